@@ -1,0 +1,203 @@
+/* mrhs.h -- C ABI of libmrhs, the multi-right-hand-side coarse-grid operator
+ * and block conjugate gradient kernels of P. Boyle, "Multiple right hand side
+ * multigrid for domain wall fermions with a multigrid preconditioned block
+ * conjugate gradient algorithm" (arXiv:2409.03904), for NVIDIA B300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: four periodic dimensions L[0..3], V = L0*L1*L2*L3 sites, site
+ *   index x = x0 + L0*(x1 + L1*(x2 + L2*x3)).
+ * Stencil: npts displacements delta_p in {-1,0,1}^4 (disp[p][4], host
+ *   memory), p = 0 must be the self term (0,0,0,0); at most 81 points
+ *   (Sec. 2.7, "Coarse operator": the full 3^4 neighbourhood).
+ * Coefficients: complex128 A[x][p][a][b], a, b < nb (row-major nb x nb
+ *   block for every site and stencil point), as (re, im) double pairs.
+ * Vectors: a block of nrhs coarse vectors is stored [x][b][r] (RHS index r
+ *   fastest), i.e. an N x nrhs row-major complex matrix with N = V*nb; the
+ *   element type is complex128 (MRHS_C128) or complex64 (MRHS_C64).
+ * Memory: every vector, matrix and coefficient pointer is caller-owned
+ *   DEVICE memory unless stated otherwise, 16-byte aligned; the library never
+ *   frees it.  Host pointers are marked "host".
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Apply-type calls are asynchronous on that stream.
+ * Errors: every call returns MRHS_OK (0) or a negative MRHS_ERR_* code and
+ *   never aborts or traps; mrhs_last_error() returns a thread-local message
+ *   for the last failure.  A CUDA failure inside a call returns MRHS_ERR_CUDA.
+ */
+#ifndef MRHS_H
+#define MRHS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MRHS_OK = 0,
+  MRHS_ERR_INVALID_ARG = -1,   /* bad size, pointer, alignment or enum */
+  MRHS_ERR_CUDA = -2,          /* a CUDA runtime call or launch failed */
+  MRHS_ERR_NOT_CONVERGED = -3, /* maxiter reached; X and info still written */
+  MRHS_ERR_BREAKDOWN = -4,     /* block Gram not positive (solve only) */
+  MRHS_ERR_NONFINITE = -5,     /* NaN/Inf met in the solve */
+  MRHS_ERR_UNSUPPORTED = -6,   /* precision not built into this operator */
+  MRHS_ERR_NO_MEMORY = -7      /* device allocation failed */
+};
+
+/* Operator precisions (coefficients and arithmetic of one application). */
+enum {
+  MRHS_PREC_FP64 = 0, /* complex128 coefficients, FP64 FMA; vectors complex128 */
+  MRHS_PREC_FP32 = 1, /* complex64 coefficients, FP32 FMA; vectors complex64 */
+  MRHS_PREC_BF16 = 2, /* bf16 codes x per-site power-of-two scale, tcgen05
+                         tensor cores, FP32 accumulation; vectors complex64 */
+  MRHS_PREC_FP16 = 3  /* as BF16 with fp16 codes */
+};
+#define MRHS_PREC_BIT(p) (1u << (p))
+
+/* Vector element types. */
+enum { MRHS_C128 = 0, MRHS_C64 = 1 };
+
+#define MRHS_MAX_RHS 64
+#define MRHS_MAX_PTS 81
+
+typedef struct mrhs_op_s* mrhs_op;
+
+/* Create a coarse operator (Sec. 2.7: "the coarse matrix coefficients are
+ * stored entirely internal to this object").
+ *   L      host int32[4], each >= 1
+ *   nb     basis size per site, 1..64
+ *   npts   stencil points, 1..81; disp host int8[npts][4] in {-1,0,1}, disp[0]=0
+ *   A      device complex128 [V][npts][nb][nb]; read during the call only
+ *   prec_mask  OR of MRHS_PREC_BIT(p): the precisions to build.  The operator
+ *          owns a packed copy of A for each (complex128, complex64, or
+ *          bf16/fp16 codes with a float scale per site); A may be freed after
+ *          the call returns.
+ * On success *out holds the handle.  Synchronises `stream`. */
+int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts,
+                   const int8_t* disp, const void* A, uint32_t prec_mask, void* stream);
+
+/* Release the operator and its device copies (after its last use is done). */
+int mrhs_op_destroy(mrhs_op op);
+
+/* Y = H X,  Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.7, "Applying the
+ * coarse operator", the per-stencil-point batched GEMM summed over p).
+ *   prec   MRHS_PREC_*; must be in the operator's prec_mask
+ *   X, Y   device [V][nb][nrhs]: complex128 for FP64, complex64 otherwise;
+ *          X and Y must not overlap
+ *   nrhs   1..MRHS_MAX_RHS */
+int coarse_op_apply(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
+                    void* stream);
+
+/* Y = H^dagger X,  Y(x) = sum_p A_p(x - delta_p)^dagger X(x - delta_p): the
+ * adjoint of the operator above (the reversed, daggered stencil).  Same
+ * arguments.  For the BF16/FP16 precisions the first call builds a packed
+ * image of the daggered coefficients inside the operator. */
+int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
+                        void* stream);
+
+/* G = X^dagger Y, the nrhs_x x nrhs_y block inner product of block CG
+ * (Fig. 2: D^dagger Z, T^dagger t, ...; Sec. 3.4's "ThinQR" Gram).
+ *   X [N][rx], Y [N][ry] of element type dtype (MRHS_C128 or MRHS_C64)
+ *   G device complex128 [rx][ry] row-major (written, not accumulated)
+ *   N >= 0 rows, 1 <= rx, ry <= MRHS_MAX_RHS
+ * Products are formed in the vectors' precision and summed in FP64 over a
+ * fixed reduction tree, so the result is bitwise reproducible.  Uses a
+ * library-owned device workspace. */
+int block_inner(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
+                int32_t dtype, void* stream);
+
+/* Y = beta*Y + X M  (Fig. 2 block updates X + D M, Q - Z M, D S^dagger, ...)
+ *   X [N][rin], Y [N][rout] of element type dtype; Y may alias X when
+ *   rin == rout (the update is done row tile by row tile)
+ *   M device complex128 [rin][rout] row-major; beta real
+ * For MRHS_C64 the arithmetic is FP32 with M rounded to complex64. */
+int block_axpy(void* Y, const void* X, const void* M, double beta, int64_t N, int32_t rin,
+               int32_t rout, int32_t dtype, void* stream);
+
+/* Factor a Hermitian block Gram G = T^dagger T (r x r, device complex128) as
+ * T = Q S (Fig. 2: "Q_{k+1} S_{k+1} = Q_k - Z_k M_k", C_0 from R_0):
+ *   S  device complex128 [r][r]: upper triangular with a positive real
+ *      diagonal (S^dagger S = G) when every pivot exceeds tau * max_i G_ii;
+ *      otherwise the diagonally pivoted factor stopped at rank k, rows k..r-1
+ *      zero (breakdown-free block CG, dropping numerically null directions)
+ *   W  device complex128 [r][r]: T W = Q (W = S^-1 at full rank; columns
+ *      k..r-1 zero otherwise)
+ *   rank  device int32[1]: k
+ * G is Hermitian-symmetrised first.  One CTA, FP64.  Asynchronous. */
+int herm_factor(const void* G, void* S, void* W, int32_t* rank, int32_t r, double tau,
+                void* stream);
+
+/* P = p(H) X with p the degree-`order` Chebyshev interpolant of 1/x on
+ * [lo, hi] (Sec. 2.3: "a Chebyshev approximation to 1/x ... coefficients
+ * at the Chebyshev interpolation points"), applied by the three-term
+ * recurrence on t(H) = (2H - (hi + lo))/(hi - lo) with the operator in
+ * precision `prec`.  X, P complex64 (FP32/BF16/FP16) or complex128 (FP64),
+ * [V][nb][nrhs]; uses operator-owned workspace; asynchronous.  0 < lo < hi. */
+int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, const void* X,
+                void* P, int32_t nrhs, void* stream);
+
+/* Solver parameters (block_cg_solve). */
+typedef struct {
+  double tol;           /* per-RHS relative true residual |b_r - H x_r| / |b_r| */
+  int32_t maxiter;      /* cap on Krylov iterations (all cycles together) */
+  int32_t mode;         /* MRHS_SOLVE_FP64 or MRHS_SOLVE_MIXED */
+  int32_t precond;      /* 0: BlockCGrQ (Fig. 2 left); 1: Chebyshev-preconditioned
+                           BlockCGrQ (Fig. 2 right) */
+  int32_t precond_prec; /* MRHS_PREC_* of the Chebyshev operator applications */
+  int32_t cheb_order;   /* polynomial degree */
+  double cheb_lo;       /* Chebyshev interval; cheb_hi <= 0: hi = 1.05 x power- */
+  double cheb_hi;       /*   method estimate; cheb_lo <= 0: lo = hi / 400 */
+  double inner_tol;     /* MIXED: residual reduction per refinement cycle */
+  int32_t max_cycles;   /* MIXED: refinement cycles */
+  int32_t check_every;  /* read the convergence flag every k iterations */
+  double breakdown_tau; /* relative Cholesky pivot threshold */
+} mrhs_solve_params;
+
+enum {
+  MRHS_SOLVE_FP64 = 0,  /* everything FP64 (plain FP64 block CG) */
+  MRHS_SOLVE_MIXED = 1  /* FP64 outer defect correction (true residual, Gram
+                           accumulation, Cholesky, solution update); inner block
+                           CG on complex64 vectors with the FP32 operator and
+                           the low-precision Chebyshev preconditioner */
+};
+
+typedef struct {
+  int32_t status;     /* same code as the return value */
+  int32_t iters;      /* Krylov iterations, all cycles */
+  int32_t cycles;     /* refinement cycles (MIXED) or 1 */
+  int32_t nrhs;
+  int64_t applies[4]; /* operator applications per precision */
+  double resid[MRHS_MAX_RHS]; /* final true relative residual per RHS (FP64) */
+  double cheb_lo, cheb_hi;    /* interval used */
+  double ms_total;            /* wall time of the call */
+} mrhs_solve_info;
+
+/* Solve H X = B for nrhs right-hand sides with block CG (Fig. 2).
+ *   B device complex128 [V][nb][nrhs] (read only); X device complex128: in,
+ *   the initial guess X_0; out, the solution.  A zero column of B gives a
+ *   zero column of X.  H must be Hermitian positive definite.
+ * Returns after termination (synchronises `stream`); on MRHS_ERR_NOT_CONVERGED
+ * X and *info hold the last iterate.  Workspace is allocated by the call. */
+int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
+                   const mrhs_solve_params* params, mrhs_solve_info* info, void* stream);
+
+/* Default parameters for `mode`. */
+void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode);
+
+/* Returns and clears the sticky error word of the tensor-core kernels: 0 if
+ * none, else a bit set by a bounded wait that expired inside a kernel (1 the
+ * TMA producer, 2 the MMA issuer, 4 the epilogue); such a kernel records the
+ * bit, drains its own copies, frees its tensor memory and returns, leaving
+ * its output undefined.  Synchronises the current device. */
+int32_t mrhs_device_error(void);
+
+/* Thread-local message describing the last error ("" if none). */
+const char* mrhs_last_error(void);
+
+/* Library version string. */
+const char* mrhs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRHS_H */

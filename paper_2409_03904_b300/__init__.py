@@ -1,0 +1,173 @@
+"""Multi-right-hand-side coarse-grid operator and block CG for NVIDIA B300.
+
+Python face of libmrhs (include/mrhs.h); every computation runs in the CUDA
+library, this package only marshals torch tensors.  Layouts: coefficients
+A[x][p][a][b] complex128; vectors [V][nb][nrhs] (RHS fastest), complex128
+for FP64 and complex64 for the FP32/BF16/FP16 operators.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import C64, C128, PREC, SOLVE_FP64, SOLVE_MIXED, MrhsError, SolveInfo, SolveParams
+
+__all__ = ["CoarseOp", "block_inner", "block_axpy", "herm_factor", "MrhsError", "PREC",
+           "SOLVE_FP64", "SOLVE_MIXED", "device_error", "version"]
+
+
+def version():
+    return _lib.lib().mrhs_version().decode()
+
+
+def device_error():
+    """Sticky error word of the tensor-core kernels (0 = none); clears it."""
+    return int(_lib.lib().mrhs_device_error())
+
+
+class CoarseOp:
+    """Coarse operator H with Y(x) = sum_p A_p(x) X(x + delta_p).
+
+    A: CUDA complex128 tensor [V][npts][nb][nb]; L: 4 lattice extents; disp:
+    int8 [npts][4] displacements (disp[0] = 0); precisions: any of "fp64",
+    "fp32", "bf16", "fp16".  The operator keeps its own packed copies.
+    """
+
+    def __init__(self, A, L, disp, precisions=("fp64", "fp32")):
+        l = _lib.lib()
+        self.L = tuple(int(v) for v in L)
+        self.V = int(np.prod(self.L))
+        disp = np.ascontiguousarray(np.asarray(disp, dtype=np.int8).reshape(-1, 4))
+        self.npts = disp.shape[0]
+        if A.dim() != 4 or A.shape[0] != self.V or A.shape[1] != self.npts or A.shape[2] != A.shape[3]:
+            raise ValueError(f"A must be [V][npts][nb][nb], got {tuple(A.shape)}")
+        self.nb = int(A.shape[2])
+        self.N = self.V * self.nb
+        self.precisions = tuple(precisions)
+        mask = 0
+        for p in self.precisions:
+            mask |= 1 << PREC[p]
+        Lc = (ctypes.c_int32 * 4)(*self.L)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(A.device):
+            _lib.check(l.mrhs_op_create(ctypes.byref(h), Lc, self.nb, self.npts,
+                                        disp.ctypes.data_as(ctypes.c_void_p),
+                                        _lib.dev_ptr(A, torch.complex128, "A"), mask,
+                                        _lib.stream_ptr()))
+        self._h = h
+        self.device = A.device
+        self.disp = disp
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().mrhs_op_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _apply(self, fn, X, prec, out):
+        dt = _lib.vec_dtype(prec)
+        if X.shape[:2] != (self.V, self.nb):
+            raise ValueError(f"X must be [V][nb][nrhs], got {tuple(X.shape)}")
+        Y = torch.empty_like(X) if out is None else out
+        fn(self._h, PREC[prec], _lib.dev_ptr(X, dt, "X"), _lib.dev_ptr(Y, dt, "Y"),
+           int(X.shape[2]), _lib.stream_ptr())
+        return Y
+
+    def apply(self, X, prec="fp64", out=None):
+        """Y = H X in precision `prec`."""
+        l = _lib.lib()
+        return self._apply(lambda *a: _lib.check(l.coarse_op_apply(*a)), X, prec, out)
+
+    def apply_dag(self, X, prec="fp64", out=None):
+        """Y = H^dagger X in precision `prec`."""
+        l = _lib.lib()
+        return self._apply(lambda *a: _lib.check(l.coarse_op_apply_dag(*a)), X, prec, out)
+
+    def cheby(self, X, lo, hi, order, prec="fp32", out=None):
+        """P = p(H) X, p the Chebyshev interpolant of 1/x on [lo, hi]."""
+        dt = _lib.vec_dtype(prec)
+        P = torch.empty_like(X) if out is None else out
+        _lib.check(_lib.lib().cheby_apply(self._h, PREC[prec], float(lo), float(hi), int(order),
+                                          _lib.dev_ptr(X, dt, "X"), _lib.dev_ptr(P, dt, "P"),
+                                          int(X.shape[2]), _lib.stream_ptr()))
+        return P
+
+    def solve(self, B, X0=None, mode="fp64", raise_on_fail=True, **kw):
+        """Block CG (Fig. 2) for H X = B; returns (X, info dict).
+
+        mode "fp64": plain FP64 BlockCGrQ (precond=1 with precond_prec "fp64"
+        for the FP64 Chebyshev-preconditioned form); mode "mixed": FP64-outer
+        defect correction around a complex64 preconditioned block CG.
+        Keyword arguments override mrhs_solve_params fields.
+        """
+        l = _lib.lib()
+        p = SolveParams()
+        l.mrhs_solve_params_default(ctypes.byref(p), SOLVE_MIXED if mode == "mixed" else SOLVE_FP64)
+        for k, v in kw.items():
+            if k == "precond_prec" and isinstance(v, str):
+                v = PREC[v]
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        X = torch.zeros_like(B) if X0 is None else X0.clone()
+        info = SolveInfo()
+        code = l.block_cg_solve(self._h, _lib.dev_ptr(B, torch.complex128, "B"),
+                                _lib.dev_ptr(X, torch.complex128, "X"), int(B.shape[2]),
+                                ctypes.byref(p), ctypes.byref(info), _lib.stream_ptr())
+        if code not in (0, -3) or (code == -3 and raise_on_fail):
+            _lib.check(code)
+        return X, info.as_dict()
+
+
+def _dtype_code(t):
+    if t.dtype == torch.complex128:
+        return C128
+    if t.dtype == torch.complex64:
+        return C64
+    raise TypeError("vectors must be complex128 or complex64")
+
+
+def block_inner(X, Y):
+    """G = X^dagger Y (complex128 [rx][ry]) for [.., rx] and [.., ry] blocks."""
+    if X.dtype != Y.dtype:
+        raise TypeError("X and Y must share a dtype")
+    rx, ry = int(X.shape[-1]), int(Y.shape[-1])
+    N = X.numel() // rx
+    if Y.numel() // ry != N:
+        raise ValueError("row counts differ")
+    G = torch.empty((rx, ry), dtype=torch.complex128, device=X.device)
+    _lib.check(_lib.lib().block_inner(_lib.dev_ptr(X, None, "X"), _lib.dev_ptr(Y, None, "Y"),
+                                      _lib.dev_ptr(G), N, rx, ry, _dtype_code(X),
+                                      _lib.stream_ptr()))
+    return G
+
+
+def block_axpy(Y, X, M, beta=0.0):
+    """Y <- beta Y + X M in place (M complex128 [rin][rout] on the device)."""
+    rin, rout = int(X.shape[-1]), int(Y.shape[-1])
+    N = X.numel() // rin
+    if X.dtype != Y.dtype:
+        raise TypeError("X and Y must share a dtype")
+    M = M.to(device=X.device, dtype=torch.complex128).contiguous()
+    _lib.check(_lib.lib().block_axpy(_lib.dev_ptr(Y, None, "Y"), _lib.dev_ptr(X, None, "X"),
+                                     _lib.dev_ptr(M), float(beta), N, rin, rout, _dtype_code(X),
+                                     _lib.stream_ptr()))
+    return Y
+
+
+def herm_factor(G, tau=1e-12):
+    """(S, W, rank) with T = Q S and T W = Q for the Gram G = T^dagger T."""
+    r = int(G.shape[0])
+    G = G.to(torch.complex128).contiguous()
+    S = torch.empty_like(G)
+    W = torch.empty_like(G)
+    rank = torch.zeros(1, dtype=torch.int32, device=G.device)
+    _lib.check(_lib.lib().herm_factor(_lib.dev_ptr(G), _lib.dev_ptr(S), _lib.dev_ptr(W),
+                                      _lib.dev_ptr(rank), r, float(tau), _lib.stream_ptr()))
+    return S, W, int(rank.item())

@@ -1,0 +1,345 @@
+// C ABI entry points of libmrhs: argument checks, operator construction and
+// dispatch to the kernels (see include/mrhs.h for the contract).
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+namespace mrhs {
+
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+namespace {
+
+__global__ void k_neighbours(int32_t* fwd, int32_t* bwd, int64_t V, int npts, int L0, int L1,
+                             int L2, int L3, const int8_t* __restrict__ disp) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (x >= V) return;
+  int c[4];
+  int64_t r = x;
+  const int L[4] = {L0, L1, L2, L3};
+  for (int mu = 0; mu < 4; ++mu) {
+    c[mu] = (int)(r % L[mu]);
+    r /= L[mu];
+  }
+  int64_t yf = 0, yb = 0;
+  for (int mu = 3; mu >= 0; --mu) {
+    const int d = disp[4 * p + mu];
+    yf = yf * L[mu] + (c[mu] + d + L[mu]) % L[mu];
+    yb = yb * L[mu] + (c[mu] - d + L[mu]) % L[mu];
+  }
+  fwd[(int64_t)p * V + x] = (int32_t)yf;
+  bwd[(int64_t)p * V + x] = (int32_t)yb;
+}
+
+__global__ void k_to_c64(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = make_float2(__double2float_rn(a[i].x), __double2float_rn(a[i].y));
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_op(const mrhs_op_s* op) {
+  if (!op) return fail(MRHS_ERR_INVALID_ARG, "null operator");
+  return MRHS_OK;
+}
+
+int check_vec(const void* p, const char* name) {
+  if (!p) return fail(MRHS_ERR_INVALID_ARG, std::string(name) + " is null");
+  if (!aligned16(p)) return fail(MRHS_ERR_INVALID_ARG, std::string(name) + " not 16-byte aligned");
+  return MRHS_OK;
+}
+
+int check_prec(const mrhs_op_s* op, int prec) {
+  if (prec < 0 || prec > 3) return fail(MRHS_ERR_INVALID_ARG, "unknown precision");
+  if (!(op->prec_mask & MRHS_PREC_BIT(prec)))
+    return fail(MRHS_ERR_UNSUPPORTED, "precision not built into this operator");
+  return MRHS_OK;
+}
+
+}  // namespace
+
+int op_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
+             cudaStream_t s) {
+  if (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_FP32)
+    return simt_apply(op, prec, dag, X, Y, nrhs, s);
+  return tc_apply(op, prec, dag, X, Y, nrhs, s);
+}
+
+}  // namespace mrhs
+
+using namespace mrhs;
+
+extern "C" {
+
+const char* mrhs_last_error(void) { return t_last_error.c_str(); }
+
+const char* mrhs_version(void) { return "mrhs 0.1 (sm_103a)"; }
+
+int32_t mrhs_device_error(void) {
+  cudaDeviceSynchronize();
+  return (int32_t)tc_read_and_clear_error();
+}
+
+int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, const int8_t* disp,
+                   const void* A, uint32_t prec_mask, void* stream) {
+  if (!out || !L || !disp || !A) return fail(MRHS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (nb < 1 || nb > 64) return fail(MRHS_ERR_INVALID_ARG, "nb must be in 1..64");
+  if (npts < 1 || npts > MRHS_MAX_PTS) return fail(MRHS_ERR_INVALID_ARG, "npts must be in 1..81");
+  if (prec_mask == 0 || (prec_mask & ~0xFu))
+    return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..3");
+  if (!aligned16(A)) return fail(MRHS_ERR_INVALID_ARG, "A not 16-byte aligned");
+  int64_t V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (L[mu] < 1) return fail(MRHS_ERR_INVALID_ARG, "lattice extents must be >= 1");
+    V *= L[mu];
+  }
+  if (V * npts > INT32_MAX) return fail(MRHS_ERR_INVALID_ARG, "lattice too large");
+  for (int p = 0; p < npts; ++p)
+    for (int mu = 0; mu < 4; ++mu)
+      if (disp[4 * p + mu] < -1 || disp[4 * p + mu] > 1)
+        return fail(MRHS_ERR_INVALID_ARG, "displacements must lie in {-1,0,1}");
+  for (int mu = 0; mu < 4; ++mu)
+    if (disp[mu] != 0) return fail(MRHS_ERR_INVALID_ARG, "disp[0] must be the self term");
+  cudaStream_t s = (cudaStream_t)stream;
+  mrhs_op_s* op = new mrhs_op_s();
+  for (int mu = 0; mu < 4; ++mu) op->L[mu] = L[mu];
+  op->nb = nb;
+  op->npts = npts;
+  op->V = V;
+  std::memcpy(op->disp, disp, 4 * (size_t)npts);
+  op->prec_mask = prec_mask;
+  cudaGetDevice(&op->device);
+  auto bail = [&](int code) {
+    mrhs_op_destroy(op);
+    return code;
+  };
+  const size_t nA = (size_t)V * npts * nb * nb;
+  int8_t* d_disp = nullptr;
+  if (cudaMalloc(&op->nbr_fwd, sizeof(int32_t) * V * npts) != cudaSuccess ||
+      cudaMalloc(&op->nbr_bwd, sizeof(int32_t) * V * npts) != cudaSuccess ||
+      cudaMalloc(&d_disp, 4 * (size_t)npts) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_disp) cudaFree(d_disp);
+    return bail(fail(MRHS_ERR_NO_MEMORY, "neighbour tables"));
+  }
+  if (cudaMemcpyAsync(d_disp, disp, 4 * (size_t)npts, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaFree(d_disp);
+    return bail(fail(MRHS_ERR_CUDA, "disp upload"));
+  }
+  {
+    dim3 grid((unsigned)((V + 255) / 256), (unsigned)npts);
+    k_neighbours<<<grid, 256, 0, s>>>(op->nbr_fwd, op->nbr_bwd, V, npts, L[0], L[1], L[2], L[3],
+                                      d_disp);
+  }
+  if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)) {
+    if (cudaMalloc(&op->a64, sizeof(double2) * nA) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d_disp);
+      return bail(fail(MRHS_ERR_NO_MEMORY, "FP64 coefficients"));
+    }
+    cudaMemcpyAsync(op->a64, A, sizeof(double2) * nA, cudaMemcpyDeviceToDevice, s);
+  }
+  if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP32)) {
+    if (cudaMalloc(&op->a32, sizeof(float2) * nA) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d_disp);
+      return bail(fail(MRHS_ERR_NO_MEMORY, "FP32 coefficients"));
+    }
+    k_to_c64<<<num_sms() * 8, 256, 0, s>>>((const double2*)A, op->a32, (int64_t)nA);
+  }
+  for (int prec = MRHS_PREC_BF16; prec <= MRHS_PREC_FP16; ++prec)
+    if (prec_mask & MRHS_PREC_BIT(prec)) {
+      int st = tc_build(op, prec, false, (const double2*)A, s);
+      if (st != MRHS_OK) {
+        cudaFree(d_disp);
+        return bail(st);
+      }
+    }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(d_disp);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(fail(MRHS_ERR_CUDA, std::string("op create: ") + cudaGetErrorString(e)));
+  *out = op;
+  return MRHS_OK;
+}
+
+int mrhs_op_destroy(mrhs_op op) {
+  if (!op) return MRHS_OK;
+  cudaFree(op->nbr_fwd);
+  cudaFree(op->nbr_bwd);
+  cudaFree(op->a64);
+  cudaFree(op->a32);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(op->tc[i].codes);
+    cudaFree(op->tc[i].scale);
+    cudaFree(op->tc[i].diag);
+    cudaFree(op->tc_dag[i].codes);
+    cudaFree(op->tc_dag[i].scale);
+    cudaFree(op->tc_dag[i].diag);
+  }
+  op->ws_xpack.release();
+  op->ws_cheb.release();
+  op->ws_small.release();
+  op->ws_solve.release();
+  delete op;
+  return MRHS_OK;
+}
+
+static int apply_common(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
+                        void* stream, bool dag) {
+  MRHS_TRY(check_op(op));
+  MRHS_TRY(check_prec(op, prec));
+  MRHS_TRY(check_vec(X, "X"));
+  MRHS_TRY(check_vec(Y, "Y"));
+  if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
+  const size_t es = prec == MRHS_PREC_FP64 ? 16 : 8;
+  const size_t bytes = es * (size_t)op->V * op->nb * nrhs;
+  const char* x = (const char*)X;
+  const char* y = (const char*)Y;
+  if (x < y + bytes && y < x + bytes) return fail(MRHS_ERR_INVALID_ARG, "X and Y overlap");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != op->device) return fail(MRHS_ERR_INVALID_ARG, "operator lives on another device");
+  return op_apply(op, prec, dag, X, Y, nrhs, (cudaStream_t)stream);
+}
+
+int coarse_op_apply(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
+                    void* stream) {
+  return apply_common(op, prec, X, Y, nrhs, stream, false);
+}
+
+int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
+                        void* stream) {
+  return apply_common(op, prec, X, Y, nrhs, stream, true);
+}
+
+int block_inner(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
+                int32_t dtype, void* stream) {
+  if (N < 0 || rx < 1 || ry < 1 || rx > MRHS_MAX_RHS || ry > MRHS_MAX_RHS)
+    return fail(MRHS_ERR_INVALID_ARG, "block_inner: sizes");
+  if (dtype != MRHS_C128 && dtype != MRHS_C64) return fail(MRHS_ERR_INVALID_ARG, "dtype");
+  MRHS_TRY(check_vec(G, "G"));
+  if (N > 0) {
+    MRHS_TRY(check_vec(X, "X"));
+    MRHS_TRY(check_vec(Y, "Y"));
+  }
+  return gram(X, Y, (double2*)G, N, rx, ry, dtype, (cudaStream_t)stream);
+}
+
+int block_axpy(void* Y, const void* X, const void* M, double beta, int64_t N, int32_t rin,
+               int32_t rout, int32_t dtype, void* stream) {
+  if (N < 0 || rin < 1 || rout < 1 || rin > MRHS_MAX_RHS || rout > MRHS_MAX_RHS)
+    return fail(MRHS_ERR_INVALID_ARG, "block_axpy: sizes");
+  if (dtype != MRHS_C128 && dtype != MRHS_C64) return fail(MRHS_ERR_INVALID_ARG, "dtype");
+  MRHS_TRY(check_vec(M, "M"));
+  if (N > 0) {
+    MRHS_TRY(check_vec(X, "X"));
+    MRHS_TRY(check_vec(Y, "Y"));
+    if (X == Y && rin != rout)
+      return fail(MRHS_ERR_INVALID_ARG, "block_axpy: in-place needs rin == rout");
+    const size_t es = dtype == MRHS_C128 ? 16 : 8;
+    const char* x = (const char*)X;
+    const char* y = (const char*)Y;
+    if (X != Y && x < y + es * N * rout && y < x + es * N * rin)
+      return fail(MRHS_ERR_INVALID_ARG, "block_axpy: X and Y partially overlap");
+  }
+  return axpy(Y, X, (const double2*)M, beta, N, rin, rout, dtype, (cudaStream_t)stream);
+}
+
+int herm_factor(const void* G, void* S, void* W, int32_t* rank, int32_t r, double tau,
+                void* stream) {
+  if (r < 1 || r > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "herm_factor: r");
+  if (!(tau >= 0.0)) return fail(MRHS_ERR_INVALID_ARG, "herm_factor: tau");
+  MRHS_TRY(check_vec(G, "G"));
+  MRHS_TRY(check_vec(S, "S"));
+  MRHS_TRY(check_vec(W, "W"));
+  if (!rank) return fail(MRHS_ERR_INVALID_ARG, "rank is null");
+  return factor((const double2*)G, (double2*)S, (double2*)W, rank, r, tau, (cudaStream_t)stream);
+}
+
+int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, const void* X,
+                void* P, int32_t nrhs, void* stream) {
+  MRHS_TRY(check_op(op));
+  MRHS_TRY(check_prec(op, prec));
+  MRHS_TRY(check_vec(X, "X"));
+  MRHS_TRY(check_vec(P, "P"));
+  if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
+  if (!(lo > 0.0 && lo < hi)) return fail(MRHS_ERR_INVALID_ARG, "need 0 < lo < hi");
+  if (order < 0 || order > 10000) return fail(MRHS_ERR_INVALID_ARG, "order");
+  if (X == P) return fail(MRHS_ERR_INVALID_ARG, "X and P must differ");
+  return cheby(op, prec, lo, hi, order, X, P, nrhs, (cudaStream_t)stream);
+}
+
+int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
+                   const mrhs_solve_params* params, mrhs_solve_info* info, void* stream) {
+  MRHS_TRY(check_op(op));
+  if (!params) return fail(MRHS_ERR_INVALID_ARG, "params is null");
+  MRHS_TRY(check_vec(B, "B"));
+  MRHS_TRY(check_vec(X, "X"));
+  if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
+  const mrhs_solve_params& p = *params;
+  if (!(p.tol > 0.0) || p.maxiter < 1) return fail(MRHS_ERR_INVALID_ARG, "tol / maxiter");
+  if (p.mode != MRHS_SOLVE_FP64 && p.mode != MRHS_SOLVE_MIXED)
+    return fail(MRHS_ERR_INVALID_ARG, "mode");
+  if (!(op->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)))
+    return fail(MRHS_ERR_UNSUPPORTED, "block_cg_solve needs the FP64 operator");
+  if (p.mode == MRHS_SOLVE_MIXED && !(op->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP32)))
+    return fail(MRHS_ERR_UNSUPPORTED, "mixed mode needs the FP32 operator");
+  if (p.precond) {
+    if (p.precond_prec < 0 || p.precond_prec > 3) return fail(MRHS_ERR_INVALID_ARG, "precond_prec");
+    if (!(op->prec_mask & MRHS_PREC_BIT(p.precond_prec)))
+      return fail(MRHS_ERR_UNSUPPORTED, "preconditioner precision not built");
+    if (p.mode == MRHS_SOLVE_FP64 && p.precond_prec != MRHS_PREC_FP64)
+      return fail(MRHS_ERR_INVALID_ARG, "FP64 mode takes an FP64 preconditioner");
+    if (p.mode == MRHS_SOLVE_MIXED && p.precond_prec == MRHS_PREC_FP64)
+      return fail(MRHS_ERR_INVALID_ARG, "mixed mode takes a FP32/BF16/FP16 preconditioner");
+    if (p.cheb_order < 0) return fail(MRHS_ERR_INVALID_ARG, "cheb_order");
+  }
+  if (X == B) return fail(MRHS_ERR_INVALID_ARG, "X and B must differ");
+  return solve(op, (const double2*)B, (double2*)X, nrhs, p, info, (cudaStream_t)stream);
+}
+
+void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->tol = 1e-8;
+  p->maxiter = 5000;
+  p->mode = mode;
+  p->precond = mode == MRHS_SOLVE_MIXED ? 1 : 0;
+  p->precond_prec = MRHS_PREC_BF16;
+  p->cheb_order = 16;
+  p->cheb_lo = 0.0;
+  p->cheb_hi = 0.0;
+  p->inner_tol = 1e-4;
+  p->max_cycles = 12;
+  p->check_every = 4;
+  p->breakdown_tau = 1e-12;
+}
+
+}  // extern "C"

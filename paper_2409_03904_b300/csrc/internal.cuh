@@ -1,0 +1,126 @@
+// Internal declarations of libmrhs (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mrhs.h"
+
+namespace mrhs {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define MRHS_CUDA_TRY(expr)                                                        \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess)                                                         \
+      return ::mrhs::fail(MRHS_ERR_CUDA, std::string(#expr) + ": " +              \
+                                             cudaGetErrorString(_e));             \
+  } while (0)
+
+#define MRHS_TRY(expr)          \
+  do {                          \
+    int _s = (expr);            \
+    if (_s != MRHS_OK) return _s; \
+  } while (0)
+
+// ---------------------------------------------------------------- complex
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__host__ __device__ inline double2 cfma_conj(double2 a, double2 b, double2 c) {  // conj(a)*b + c
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__host__ __device__ inline float2 cfma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__host__ __device__ inline float2 cfma_conj(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+template <typename C> struct real_of;
+template <> struct real_of<double2> { using type = double; };
+template <> struct real_of<float2> { using type = float; };
+template <typename C> __host__ __device__ inline C czero();
+template <> __host__ __device__ inline double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __host__ __device__ inline float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+// ---------------------------------------------------------------- operator
+struct TcImage {             // tensor-core packed coefficients (BF16/FP16)
+  void* codes = nullptr;     // see op_tc.cu for the layout
+  float* scale = nullptr;    // [V] power-of-two site scales
+  float* diag = nullptr;     // [V] mean real self diagonal d_x (FP32)
+  size_t bytes = 0;
+};
+
+struct Workspace {           // grow-only device scratch
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need);
+  void release();
+};
+
+}  // namespace mrhs
+
+struct mrhs_op_s {
+  int32_t L[4];
+  int32_t nb, npts;
+  int64_t V;
+  int8_t disp[MRHS_MAX_PTS][4];
+  int device;
+  uint32_t prec_mask;
+  int32_t* nbr_fwd = nullptr;   // [npts][V]  x + delta_p
+  int32_t* nbr_bwd = nullptr;   // [npts][V]  x - delta_p
+  double2* a64 = nullptr;       // [V][npts][nb][nb]
+  float2* a32 = nullptr;        // [V][npts][nb][nb]
+  mrhs::TcImage tc[2];          // BF16, FP16: forward stencil
+  mrhs::TcImage tc_dag[2];      // BF16, FP16: daggered stencil (built on demand)
+  mrhs::Workspace ws_xpack;     // packed input vectors for the tensor path
+  mrhs::Workspace ws_cheb;      // Chebyshev recurrence vectors
+  mrhs::Workspace ws_small;     // column scales etc.
+  mrhs::Workspace ws_solve;     // block CG vectors and state
+};
+
+namespace mrhs {
+
+// op_simt.cu
+int simt_apply(const mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
+               cudaStream_t s);
+// op_tc.cu
+int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s);
+unsigned tc_read_and_clear_error();
+int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
+             cudaStream_t s);
+int tc_supported(const mrhs_op_s* op, int nrhs);
+// blas.cu
+int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
+         cudaStream_t s);
+int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int rin, int rout,
+         int dtype, cudaStream_t s);
+// small.cu
+int factor(const double2* G, double2* S, double2* W, int32_t* rank, int r, double tau,
+           cudaStream_t s);
+int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
+            double2* part, cudaStream_t s);
+size_t gram_workspace_bytes(int64_t N, int rx, int ry);
+
+// solver.cu
+int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
+          mrhs_solve_info* info, cudaStream_t s);
+int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* X, void* P,
+          int R, cudaStream_t s);
+
+// generic apply dispatch (api.cu)
+int op_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
+             cudaStream_t s);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+int num_sms();
+
+}  // namespace mrhs

@@ -1,0 +1,482 @@
+// BF16 / FP16 coarse operator on the 5th-generation tensor cores (tcgen05).
+//
+// Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.7, "Applying the coarse
+// operator"), in the quantised form: the mean real diagonal d_x of the self
+// block is carried exactly in FP32, the remainder of the site's coefficient
+// block is stored as bf16/fp16 codes times a power-of-two site scale s_x,
+// every RHS column of the input as codes times a power-of-two sigma_r, and
+//   Y(x) = s_x sigma_r sum_p Ahat_p(x) Xhat(x + delta_p) + d_x X(x),
+// with the sum accumulated in FP32 in tensor memory.
+//
+// Complex GEMM by real splitting.  For one site and stencil point the
+// complex product A (nb x nb) X (nb x R) is the real product
+//     D (2R x nb) = XB (2R x 2nb) . AB^T,   AB = [Re A | Im A]   (nb x 2nb)
+//     XB rows r < R:  [Re X[:,r] | -Im X[:,r]]  -> D[r][a]   = Re Y[a][r]
+//     XB rows R + r:  [Im X[:,r] |  Re X[:,r]]  -> D[R+r][a] = Im Y[a][r]
+// so the streamed coefficient block enters unexpanded (its bytes are the HBM
+// traffic that bounds the kernel) and the sign/duplication goes to the small
+// X operand, which is packed once per call and re-read from L2 by the 9 or
+// 81 sites that neighbour it.  M = 128 (rows >= 2R ignored), N = nb rounded
+// up to 16, K = 2 nb, summed over all stencil points into one accumulator.
+//
+// Both operands are pre-packed in global memory in the canonical K-major
+// no-swizzle tcgen05 layout (8 x 16-byte core matrices, K groups 128 bytes
+// apart, 8-row groups K/8*128 bytes apart), so a single 1-D bulk TMA copy
+// per tile lands it ready for the MMA.  Element (row, k) of a tile with K
+// columns sits at byte (row/8)*(K/8)*128 + (k/8)*128 + (row%8)*16 + (k%8)*2.
+//
+// Kernel: persistent, one CTA per SM, warp-specialised:
+//   warp 0      TMA producer: per (site, p) one coefficient tile (read once
+//               per application, L2 evict-first) and the neighbour's packed
+//               X tile (L2 evict-last), into an nstage ring of shared memory
+//   warp 1      allocates TMEM, issues tcgen05.mma (one elected thread) into
+//               two alternating accumulators, commits stage releases
+//   warps 2-5   epilogue: tcgen05.ld of their 32-lane quarter, scales, adds
+//               d_x X(x), stores complex64 Y
+// Every mbarrier wait is bounded (1 s); on expiry the kernel records an
+// error, drains its own copies, frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace mrhs {
+
+__device__ unsigned int g_tc_error = 0;
+
+namespace {
+
+constexpr int kThreadsTc = 192;
+constexpr int kAccCols = 64;     // TMEM columns per accumulator
+constexpr int kTmemCols = 128;   // two accumulators
+constexpr int kM = 128;
+
+struct Geom {
+  int nb, nbp8, K, n_mma;   // K = 2 nbp8
+  int R, rows8;             // rows8 = round_up(2R, 8)
+  uint32_t coef_bytes, xb_bytes, sbo;
+};
+
+Geom make_geom(int nb, int R) {
+  Geom g;
+  g.nb = nb;
+  g.nbp8 = (nb + 7) / 8 * 8;
+  g.K = 2 * g.nbp8;
+  g.n_mma = (nb + 15) / 16 * 16;
+  g.R = R;
+  g.rows8 = (2 * R + 7) / 8 * 8;
+  g.coef_bytes = (uint32_t)g.nbp8 * g.K * 2;
+  g.xb_bytes = (uint32_t)g.rows8 * g.K * 2;
+  g.sbo = (uint32_t)(g.K / 8) * 128;
+  return g;
+}
+
+__host__ __device__ inline uint32_t canon_off(int row, int k, int K) {
+  return (uint32_t)(row >> 3) * (uint32_t)(K >> 3) * 128u + (uint32_t)(k >> 3) * 128u +
+         (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+__device__ inline double pow2_ceil(double m) {
+  if (!(m > 0.0)) return 1.0;
+  int e;
+  const double f = frexp(m, &e);
+  if (f == 0.5) e -= 1;
+  return ldexp(1.0, e);
+}
+
+template <bool BF16>
+__device__ inline uint16_t code16(float v) {
+  if (BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  return __half_as_ushort(__float2half_rn(v));
+}
+
+// One CTA per site: d_x, s_x and the codes of the site's coefficient tiles.
+// dag: the block of stencil point p at site x is A_p(x - delta_p)^dagger.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_pack_coef(const double2* __restrict__ A, uint8_t* codes,
+                                                   float* scale, float* diag,
+                                                   const int32_t* __restrict__ nbr_bwd, int64_t V,
+                                                   int npts, int nb, Geom g, int dag) {
+  const int64_t x = blockIdx.x;
+  if (x >= V) return;
+  __shared__ double s_red[256];
+  __shared__ float s_d;
+  __shared__ double s_scale;
+  const int nn = nb * nb;
+  auto src = [&](int p, int a, int b) -> double2 {
+    if (!dag) return A[((x * npts + p) * (int64_t)nb) * nb + a * nb + b];
+    const int64_t y = nbr_bwd[(int64_t)p * V + x];
+    const double2 v = A[((y * npts + p) * (int64_t)nb) * nb + b * nb + a];
+    return make_double2(v.x, -v.y);
+  };
+  // d_x: mean real diagonal of the self block, rounded to FP32
+  double acc = 0.0;
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) acc += src(0, a, a).x;
+  s_red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += s_red[i];
+    s_d = __double2float_rn(t / nb);
+  }
+  __syncthreads();
+  const double d = (double)s_d;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < npts * nn; i += blockDim.x) {
+    const int p = i / nn, a = (i % nn) / nb, b = i % nb;
+    double2 v = src(p, a, b);
+    if (p == 0 && a == b) v.x -= d;
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  s_red[threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t = fmax(t, s_red[i]);
+    s_scale = pow2_ceil(t);
+    scale[x] = (float)s_scale;
+    diag[x] = s_d;
+  }
+  __syncthreads();
+  const double inv = 1.0 / s_scale;   // exact: power of two
+  const int tile_elems = g.nbp8 * g.K;
+  for (int p = 0; p < npts; ++p) {
+    uint8_t* tile = codes + ((uint64_t)x * npts + p) * g.coef_bytes;
+    for (int i = threadIdx.x; i < tile_elems; i += blockDim.x) {
+      const int a = i / g.K, k = i % g.K;
+      const int b = k < g.nbp8 ? k : k - g.nbp8;
+      float v = 0.f;
+      if (a < nb && b < nb) {
+        double2 c = src(p, a, b);
+        if (p == 0 && a == b) c.x -= d;
+        v = __double2float_rn((k < g.nbp8 ? c.x : c.y) * inv);
+      }
+      *reinterpret_cast<uint16_t*>(tile + canon_off(a, k, g.K)) = code16<BF16>(v);
+    }
+  }
+}
+
+// Per-column max |Re|, |Im| of a complex64 [N][R] block (as float bits).
+__global__ void k_colmax(const float2* __restrict__ X, int64_t N, int R, unsigned* out) {
+  __shared__ unsigned s_m[MRHS_MAX_RHS];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) s_m[i] = 0u;
+  __syncthreads();
+  const int64_t total = N * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = X[i];
+    const float m = fmaxf(fabsf(v.x), fabsf(v.y));
+    atomicMax(&s_m[i % R], __float_as_uint(m));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < R; i += blockDim.x) atomicMax(&out[i], s_m[i]);
+}
+
+// sigma_r = 2^e >= column max (1 for a zero column); stored as float.
+__global__ void k_colscale(const unsigned* __restrict__ colmax, float* sigma, int R) {
+  const int r = threadIdx.x;
+  if (r < R) sigma[r] = (float)pow2_ceil((double)__uint_as_float(colmax[r]));
+}
+
+// Packed real-split input tiles, one [rows8][K] canonical tile per site.
+template <bool BF16>
+__global__ void k_pack_xb(const float2* __restrict__ X, const float* __restrict__ sigma,
+                          uint8_t* xb, int64_t V, int nb, Geom g) {
+  const int units = g.rows8 * (g.K / 8);   // 16-byte units per site
+  const int64_t total = V * units;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = u / units;
+    const int w = (int)(u % units);
+    const int kc = w / g.rows8, m = w % g.rows8;
+    const int R = g.R;
+    uint16_t h[8];
+    const bool re_row = m < R;
+    const int r = re_row ? m : m - R;
+    const float inv = (m < 2 * R) ? 1.0f / sigma[r] : 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = kc * 8 + e;
+      const bool first = k < g.nbp8;
+      const int b = first ? k : k - g.nbp8;
+      float v = 0.f;
+      if (m < 2 * R && b < nb) {
+        const float2 xv = X[(x * nb + b) * R + r];
+        if (re_row) v = first ? xv.x : -xv.y;
+        else v = first ? xv.y : xv.x;
+        v *= inv;
+      }
+      h[e] = code16<BF16>(v);
+    }
+    uint4 pk;
+    pk.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    pk.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+    pk.z = (uint32_t)h[4] | ((uint32_t)h[5] << 16);
+    pk.w = (uint32_t)h[6] | ((uint32_t)h[7] << 16);
+    *reinterpret_cast<uint4*>(xb + (uint64_t)x * g.xb_bytes + canon_off(m, kc * 8, g.K)) = pk;
+  }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    k_op_tc(const uint8_t* __restrict__ coef, const uint8_t* __restrict__ xb,
+            const float* __restrict__ sscale, const float* __restrict__ sdiag,
+            const float* __restrict__ sigma, const float2* __restrict__ X, float2* __restrict__ Y,
+            const int32_t* __restrict__ nbr, int64_t V, int npts, Geom g, int nstages) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + nstages;
+  uint64_t* acc_full = empty + nstages;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint8_t* stages = smem + 1024;
+  const uint32_t stage_bytes = g.coef_bytes + g.xb_bytes;
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&acc_full[i], 1);
+      ptx::mbar_init(&acc_empty[i], 4);
+    }
+    ptx::fence_mbar_init();
+    s_abort = 0;
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_slot, kTmemCols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer
+      const uint64_t pol_stream = ptx::policy_evict_first();
+      const uint64_t pol_keep = ptx::policy_evict_last();
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t issued = 0;
+      bool ok = true;
+      for (int64_t x = blockIdx.x; x < V && ok; x += gridDim.x) {
+        for (int p = 0; p < npts; ++p) {
+          if (!ptx::mbar_wait(&empty[s], ph ^ 1u, &s_abort)) { ok = false; break; }
+          uint8_t* st = stages + (size_t)s * stage_bytes;
+          ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
+          ptx::bulk_g2s(st, coef + ((uint64_t)x * npts + p) * g.coef_bytes, g.coef_bytes, &full[s],
+                        pol_stream);
+          const int64_t y = nbr[(int64_t)p * V + x];
+          ptx::bulk_g2s(st + g.coef_bytes, xb + (uint64_t)y * g.xb_bytes, g.xb_bytes, &full[s],
+                        pol_keep);
+          ++issued;
+          if (++s == nstages) { s = 0; ph ^= 1u; }
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicOr(&g_tc_error, 1u);
+      }
+      // drain: every copy this thread issued has landed before the CTA exits
+      const int64_t last = issued < nstages ? issued : nstages;
+      for (int64_t i = 0; i < last; ++i) {
+        const int64_t n = issued - 1 - i;           // issue index
+        const int ss = (int)(n % nstages);
+        const uint32_t par = (uint32_t)((n / nstages) & 1);
+        volatile int never = 0;
+        ptx::mbar_wait(&full[ss], par, &never);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = ptx::idesc_f16(kM, g.n_mma, BF16);
+      int s = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      const int nk = g.K / 16;
+      bool ok = true;
+      for (int64_t x = blockIdx.x; x < V && ok; x += gridDim.x) {
+        if (!ptx::mbar_wait(&acc_empty[acc], aph ^ 1u, &s_abort)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t tmem_d = tmem_base + (uint32_t)(acc * kAccCols);
+        for (int p = 0; p < npts; ++p) {
+          if (!ptx::mbar_wait(&full[s], ph, &s_abort)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t sb = ptx::smem_u32(stages + (size_t)s * stage_bytes);
+          for (int j = 0; j < nk; ++j) {
+            const uint64_t adesc = ptx::smem_desc(sb + g.coef_bytes + (uint32_t)j * 256u, 128u, g.sbo);
+            const uint64_t bdesc = ptx::smem_desc(sb + (uint32_t)j * 256u, 128u, g.sbo);
+            ptx::mma_f16(tmem_d, adesc, bdesc, idesc, (p > 0 || j > 0) ? 1u : 0u);
+          }
+          ptx::mma_commit(&empty[s]);
+          if (++s == nstages) { s = 0; ph ^= 1u; }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&acc_full[acc]);
+        if (++acc == 2) { acc = 0; aph ^= 1u; }
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicOr(&g_tc_error, 2u);
+      }
+    }
+  } else {
+    // ---------------- epilogue, warps 2..5 -> TMEM lane quarters 2,3,0,1
+    const int q = warp & 3;
+    const int m = 32 * q + lane;          // D row
+    const int R = g.R, nb = g.nb;
+    const bool valid = m < 2 * R;
+    const int r = valid ? (m < R ? m : m - R) : 0;
+    const int part = m < R ? 0 : 1;
+    const float sig = valid ? sigma[r] : 0.f;
+    float* Yf = reinterpret_cast<float*>(Y);
+    const float* Xf = reinterpret_cast<const float*>(X);
+    int acc = 0;
+    uint32_t aph = 0;
+    for (int64_t x = blockIdx.x; x < V; x += gridDim.x) {
+      const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort);
+      if (!__all_sync(0xffffffffu, got)) {   // warp-uniform: tcgen05.ld below is .aligned
+        s_abort = 1;
+        atomicOr(&g_tc_error, 4u);
+        break;
+      }
+      ptx::tc_fence_after();
+      float v[kAccCols];
+      const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols);
+      ptx::tmem_ld32_sync(taddr, v);
+      if (g.n_mma > 32) ptx::tmem_ld32_sync(taddr + 32u, v + 32);
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
+      if (valid) {
+        const float sc = sscale[x] * sig;
+        const float dx = sdiag[x];
+#pragma unroll
+        for (int a = 0; a < kAccCols; ++a) {
+          if (a < nb) {
+            const int64_t idx = (((int64_t)x * nb + a) * R + r) * 2 + part;
+            Yf[idx] = fmaf(sc, v[a], dx * Xf[idx]);
+          }
+        }
+      }
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+int tc_stages(const Geom& g, size_t* smem_out) {
+  const size_t stage = g.coef_bytes + g.xb_bytes;
+  // the M = 128 operand read runs past a 2R-row input tile, and the N = n_mma
+  // read past an nbp8-row coefficient tile: keep that much slack at the end
+  const size_t row_bytes = (size_t)g.K * 2;
+  const size_t slack = (size_t)(kM - g.rows8) * row_bytes + (size_t)(g.n_mma) * row_bytes + 1024;
+  const size_t budget = 220 * 1024;
+  int n = (int)((budget - 1024 - slack) / stage);
+  if (n > 16) n = 16;
+  if (n < 2) return 0;
+  *smem_out = 1024 + (size_t)n * stage + slack;
+  return n;
+}
+
+}  // namespace
+
+int tc_supported(const mrhs_op_s* op, int nrhs) {
+  if (op->nb > 64 || nrhs > 64 || nrhs < 1) return 0;
+  size_t smem;
+  return tc_stages(make_geom(op->nb, nrhs), &smem) > 0;
+}
+
+int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s) {
+  const int i = prec - MRHS_PREC_BF16;
+  if (i < 0 || i > 1) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
+  TcImage& img = dag ? op->tc_dag[i] : op->tc[i];
+  if (img.codes) return MRHS_OK;
+  const Geom g = make_geom(op->nb, 1);
+  if (!A) return fail(MRHS_ERR_INVALID_ARG, "no source coefficients for the packed image");
+  img.bytes = (size_t)op->V * op->npts * g.coef_bytes;
+  if (cudaMalloc(&img.codes, img.bytes) != cudaSuccess ||
+      cudaMalloc(&img.scale, sizeof(float) * op->V) != cudaSuccess ||
+      cudaMalloc(&img.diag, sizeof(float) * op->V) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MRHS_ERR_NO_MEMORY, "tensor-core coefficient image");
+  }
+  if (prec == MRHS_PREC_BF16)
+    k_pack_coef<true><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
+                                                     op->nbr_bwd, op->V, op->npts, op->nb, g,
+                                                     dag ? 1 : 0);
+  else
+    k_pack_coef<false><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale,
+                                                      img.diag, op->nbr_bwd, op->V, op->npts,
+                                                      op->nb, g, dag ? 1 : 0);
+  MRHS_CUDA_TRY(cudaGetLastError());
+  return MRHS_OK;
+}
+
+int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
+             cudaStream_t s) {
+  const int i = prec - MRHS_PREC_BF16;
+  if (i < 0 || i > 1) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
+  if (!tc_supported(op, nrhs)) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core shape");
+  if (dag && !op->tc_dag[i].codes) {
+    if (!op->a64) return fail(MRHS_ERR_UNSUPPORTED, "daggered low-precision image needs FP64 coefficients");
+    MRHS_TRY(tc_build(op, prec, true, op->a64, s));
+  }
+  const TcImage& img = dag ? op->tc_dag[i] : op->tc[i];
+  const Geom g = make_geom(op->nb, nrhs);
+  const size_t xb_bytes = (size_t)op->V * g.xb_bytes;
+  const size_t small = 256 * sizeof(unsigned);
+  MRHS_TRY(op->ws_xpack.ensure(xb_bytes + small));
+  uint8_t* xb = (uint8_t*)op->ws_xpack.ptr;
+  unsigned* colmax = (unsigned*)(xb + xb_bytes);
+  float* sigma = (float*)(colmax + MRHS_MAX_RHS);
+  const int sms = num_sms();
+  MRHS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned) * MRHS_MAX_RHS, s));
+  k_colmax<<<sms * 4, 256, 0, s>>>((const float2*)X, op->V * op->nb, nrhs, colmax);
+  k_colscale<<<1, 64, 0, s>>>(colmax, sigma, nrhs);
+  if (prec == MRHS_PREC_BF16)
+    k_pack_xb<true><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g);
+  else
+    k_pack_xb<false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g);
+  MRHS_CUDA_TRY(cudaGetLastError());
+  size_t smem = 0;
+  const int nst = tc_stages(g, &smem);
+  const int32_t* nbr = dag ? op->nbr_bwd : op->nbr_fwd;
+  const int64_t grid = op->V < sms ? op->V : sms;
+  if (prec == MRHS_PREC_BF16) {
+    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    k_op_tc<true><<<(unsigned)grid, kThreadsTc, smem, s>>>(
+        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float2*)X, (float2*)Y,
+        nbr, op->V, op->npts, g, nst);
+  } else {
+    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    k_op_tc<false><<<(unsigned)grid, kThreadsTc, smem, s>>>(
+        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float2*)X, (float2*)Y,
+        nbr, op->V, op->npts, g, nst);
+  }
+  MRHS_CUDA_TRY(cudaGetLastError());
+  return MRHS_OK;
+}
+
+unsigned tc_read_and_clear_error() {
+  unsigned v = 0, z = 0;
+  cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(v));
+  cudaMemcpyToSymbol(g_tc_error, &z, sizeof(z));
+  return v;
+}
+
+}  // namespace mrhs

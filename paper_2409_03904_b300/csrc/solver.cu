@@ -1,0 +1,675 @@
+// Block conjugate gradient solvers (Fig. 2) and the Chebyshev preconditioner
+// (Sec. 2.3) on the device.
+//
+// BlockCGrQ (Fig. 2 left) and Preconditioned BlockCGrQ (Fig. 2 right) run
+// as a host loop of stream-ordered launches: operator applications, Gram
+// products, one-CTA FP64 kernels for the nrhs x nrhs algebra (Cholesky,
+// inverse, C updates, stopping test) and fused row-wise block rotations.
+// Nothing returns to the host inside the loop except a convergence word read
+// every `check_every` iterations.  Readings of the figure taken here (the
+// CPU reference takes the same ones): the solution update carries C_k (X += D M C), one Cholesky factor
+// per iteration, Grams Hermitian-symmetrised, numerically null directions
+// dropped by a pivoted factor (the block narrows; W and S carry zero
+// columns/rows for the dropped directions, so every block keeps nrhs
+// columns in memory).
+//
+// MRHS_SOLVE_MIXED is FP64-outer defect correction (the paper's observation
+// that the preconditioner tolerates single precision while the outer solver
+// keeps double, Sec. 4): r = B - H x with the FP64 operator, per-column
+// scaling to complex64, an inner preconditioned block CG on complex64 vectors
+// with the FP32 operator and a BF16/FP16 (or FP32) Chebyshev preconditioner,
+// Grams accumulated in FP64 and factorised in FP64, and x += rho e in FP64.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+#include "small.cuh"
+
+namespace mrhs {
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kThreads = 256;
+
+template <typename C>
+__device__ inline C to_c(double2 v);
+template <>
+__device__ inline double2 to_c<double2>(double2 v) { return v; }
+template <>
+__device__ inline float2 to_c<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// ---------------------------------------------------------- elementwise
+template <typename C>
+__global__ void k_sub(C* out, const C* a, const C* b, int64_t n) {   // out = a - b
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const C x = a[i], y = b[i];
+    C r;
+    r.x = x.x - y.x;
+    r.y = x.y - y.y;
+    out[i] = r;
+  }
+}
+
+// r32[n][j] = complex64(r[n][j] / rho[j]) (0 where rho[j] == 0)
+__global__ void k_scale_to_c64(float2* out, const double2* r, const double* rho, int64_t N,
+                               int R) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N * R;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double p = rho[i % R];
+    const double2 v = r[i];
+    out[i] = p > 0.0 ? make_float2((float)(v.x / p), (float)(v.y / p)) : make_float2(0.f, 0.f);
+  }
+}
+
+// x[n][j] += rho[j] * e[n][j]  (FP64 solution update)
+__global__ void k_update_x(double2* x, const float2* e, const double* rho, int64_t N, int R) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N * R;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double p = rho[i % R];
+    const float2 v = e[i];
+    double2 xv = x[i];
+    xv.x = fma(p, (double)v.x, xv.x);
+    xv.y = fma(p, (double)v.y, xv.y);
+    x[i] = xv;
+  }
+}
+
+template <typename C>
+__global__ void k_zero_cols(C* x, const double* bnorm, int64_t N, int R) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N * R;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!(bnorm[i % R] > 0.0)) x[i] = C{};
+}
+
+// Chebyshev recurrence, first step: T1 = a W + b X, P = c0 X + c1 T1
+template <typename C>
+__global__ void k_cheb_first(C* T1, C* P, const C* W, const C* X, double a, double b, double c0,
+                             double c1, int64_t n) {
+  using Rl = typename real_of<C>::type;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const C w = W[i], x = X[i];
+    C t;
+    t.x = (Rl)a * w.x + (Rl)b * x.x;
+    t.y = (Rl)a * w.y + (Rl)b * x.y;
+    T1[i] = t;
+    C p;
+    p.x = (Rl)c0 * x.x + (Rl)c1 * t.x;
+    p.y = (Rl)c0 * x.y + (Rl)c1 * t.y;
+    P[i] = p;
+  }
+}
+// T_{j+1} = 2 (a W + b T_j) - T_{j-1} -> out (may alias Tp), P += c T_{j+1}
+template <typename C>
+__global__ void k_cheb_step(C* out, C* P, const C* W, const C* Tc, const C* Tp, double a,
+                            double b, double c, int64_t n) {
+  using Rl = typename real_of<C>::type;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const C w = W[i], tc = Tc[i], tp = Tp[i];
+    C t;
+    t.x = (Rl)2 * ((Rl)a * w.x + (Rl)b * tc.x) - tp.x;
+    t.y = (Rl)2 * ((Rl)a * w.y + (Rl)b * tc.y) - tp.y;
+    out[i] = t;
+    C p = P[i];
+    p.x += (Rl)c * t.x;
+    p.y += (Rl)c * t.y;
+    P[i] = p;
+  }
+}
+
+// ---------------------------------------------------------- column norms
+template <typename C>
+__global__ void k_colnorm_partial(const C* X, double* part, int64_t N, int R,
+                                  int64_t rows_per_block) {
+  __shared__ double s[kThreads];
+  const int64_t n0 = (int64_t)blockIdx.x * rows_per_block;
+  int64_t n1 = n0 + rows_per_block;
+  if (n1 > N) n1 = N;
+  for (int j = 0; j < R; ++j) {
+    double acc = 0.0;
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+      const C v = X[n * R + j];
+      acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * R + j] = s[0];
+    __syncthreads();
+  }
+}
+__global__ void k_colnorm_final(const double* part, double* out, int nblk, int R) {
+  const int j = threadIdx.x;
+  if (j >= R) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * R + j];
+  out[j] = sqrt(s);
+}
+
+// ---------------------------------------------------------- row rotations
+// P1 <- P1 W; (P2 <- P2 W); D <- (P2 ? P2 : P1) + D S^dagger.  W, S: R x R.
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_rotate(C* P1, C* P2, C* D, const double2* __restrict__ Wm, const double2* __restrict__ Sm,
+             int64_t N, int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sW = reinterpret_cast<C*>(smem_raw);
+  C* sSh = sW + R * R;          // S^dagger
+  C* sP1 = sSh + R * R;
+  C* sP2 = sP1 + kTile * R;
+  C* sD = sP2 + kTile * R;
+  for (int i = threadIdx.x; i < R * R; i += kThreads) {
+    sW[i] = to_c<C>(Wm[i]);
+    const int a = i / R, b = i % R;   // S^dagger[a][b] = conj(S[b][a])
+    const double2 v = Sm[b * R + a];
+    sSh[i] = to_c<C>(make_double2(v.x, -v.y));
+  }
+  for (int64_t t0 = (int64_t)blockIdx.x * kTile; t0 < N; t0 += (int64_t)gridDim.x * kTile) {
+    const int rows = (int)((N - t0) < kTile ? (N - t0) : kTile);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * R; i += kThreads) {
+      sP1[i] = P1[t0 * R + i];
+      if (P2) sP2[i] = P2[t0 * R + i];
+      sD[i] = D[t0 * R + i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * R; e += kThreads) {
+      const int n = e / R, j = e % R;
+      C a1 = czero<C>(), a2 = czero<C>(), dd = czero<C>();
+      for (int i = 0; i < R; ++i) {
+        a1 = cfma(sP1[n * R + i], sW[i * R + j], a1);
+        if (P2) a2 = cfma(sP2[n * R + i], sW[i * R + j], a2);
+        dd = cfma(sD[n * R + i], sSh[i * R + j], dd);
+      }
+      P1[t0 * R + e] = a1;
+      if (P2) P2[t0 * R + e] = a2;
+      const C base = P2 ? a2 : a1;
+      dd.x += base.x;
+      dd.y += base.y;
+      D[t0 * R + e] = dd;
+    }
+  }
+}
+
+// ---------------------------------------------------------- small algebra
+struct Small {           // device-resident solver state (R <= 64)
+  double2 C[64 * 64];    // k x R (rows >= k zero)
+  double2 S[64 * 64];
+  double2 W[64 * 64];
+  double2 M[64 * 64];    // inverse of D^dagger Z on the active block
+  double2 MC[64 * 64];   // M C
+  double2 negM[64 * 64];
+  double2 G[64 * 64];    // Gram workspace (filled by gram kernels)
+  double2 G2[64 * 64];   // second Gram (t^dagger t)
+  double est[64];        // per-column residual estimate (relative)
+  double target[64];     // per-column stopping level (absolute, same units)
+  int32_t rank;
+  int32_t flag;          // bit 0 converged, bit 1 breakdown, bit 2 non-finite
+};
+
+// Start: factor G = Gram of the initial residual block -> C = S, W (q <- q W).
+__global__ void k_small_start(Small* st, int R, double tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sA = reinterpret_cast<double2*>(smem_raw);
+  double2* sS = sA + R * R;
+  double2* sW = sS + R * R;
+  __shared__ int perm[64];
+  const int k = factor_block(st->G, R, R, R, tau, sA, sS, sW, perm, st->C, st->W);
+  for (int i = threadIdx.x; i < R * R; i += blockDim.x) st->S[i] = st->C[i];
+  if (threadIdx.x == 0) {
+    st->rank = k;
+    st->flag = 0;
+    for (int i = 0; i < R * R; ++i)
+      if (!isfinite(st->G[i].x) || !isfinite(st->G[i].y)) st->flag |= 4;
+  }
+}
+
+// M = (G_kk)^-1, MC = M C, negM = -M.
+__global__ void k_small_M(Small* st, int R, double tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sA = reinterpret_cast<double2*>(smem_raw);
+  double2* sS = sA + R * R;
+  double2* sW = sS + R * R;
+  __shared__ int perm[64];
+  const int k_in = st->rank;
+  const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, nullptr, st->W);
+  // st->W now holds the inverse factor in caller order: M = W W^dagger
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, j = e % R;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < R; ++l) {
+      const double2 a = st->W[i * R + l], b = st->W[j * R + l];
+      acc = cfma(a, make_double2(b.x, -b.y), acc);
+    }
+    st->M[e] = acc;
+    st->negM[e] = make_double2(-acc.x, -acc.y);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, j = e % R;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < R; ++l) acc = cfma(st->M[i * R + l], st->C[l * R + j], acc);
+    st->MC[e] = acc;
+  }
+  if (threadIdx.x == 0 && k < k_in) st->flag |= 2;   // D^dagger H D lost rank
+}
+
+// After the second Gram: factor -> S, W, new rank; estimate; C <- S C; test.
+// precond: est_j^2 = (C^dagger G2 C)_jj with G2 = t^dagger t (old C);
+// otherwise est_j = |(S C) e_j| (Q orthonormal).
+__global__ void k_small_S(Small* st, int R, double tau, int precond) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sA = reinterpret_cast<double2*>(smem_raw);
+  double2* sS = sA + R * R;
+  double2* sW = sS + R * R;
+  __shared__ int perm[64];
+  double2* sC = sA;   // the elimination scratch is free once the factor is written
+  const int k_in = st->rank;
+  if (precond) {
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+      double s = 0.0;
+      for (int a = 0; a < R; ++a) {
+        double2 v = make_double2(0.0, 0.0);        // (G2 C)[a][j]
+        for (int b = 0; b < R; ++b) v = cfma(st->G2[a * R + b], st->C[b * R + j], v);
+        const double2 c = st->C[a * R + j];
+        s += c.x * v.x + c.y * v.y;                 // Re(conj(C_aj) v)
+      }
+      st->est[j] = sqrt(fmax(s, 0.0));
+    }
+  }
+  __syncthreads();
+  const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, st->S, st->W);
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, j = e % R;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < R; ++l) acc = cfma(st->S[i * R + l], st->C[l * R + j], acc);
+    sC[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) st->C[e] = sC[e];
+  __syncthreads();
+  if (!precond)
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+      double s = 0.0;
+      for (int a = 0; a < R; ++a) s += sC[a * R + j].x * sC[a * R + j].x + sC[a * R + j].y * sC[a * R + j].y;
+      st->est[j] = sqrt(s);
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->rank = k;
+    int conv = 1;
+    for (int j = 0; j < R; ++j) {
+      if (!isfinite(st->est[j])) st->flag |= 4;
+      if (!(st->est[j] <= st->target[j])) conv = 0;
+    }
+    if (k == 0) conv = 1;
+    if (conv) st->flag |= 1;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// ---------------------------------------------------------- host driver
+struct Ctx {
+  mrhs_op_s* op;
+  cudaStream_t s;
+  int R;
+  int64_t N;
+  double tau;
+  Small* st = nullptr;        // device
+  double2* gpart = nullptr;   // Gram partials
+  double* npart = nullptr;    // column-norm partials
+  int64_t applies[4] = {0, 0, 0, 0};
+  // bump allocation from one grow-only operator-owned workspace: a first
+  // pass with base == nullptr only sums the sizes
+  char* base = nullptr;
+  size_t used = 0;
+  template <typename T>
+  int alloc(T** p, size_t count) {
+    const size_t off = (used + 255) / 256 * 256;
+    used = off + sizeof(T) * count;
+    *p = base ? (T*)(base + off) : nullptr;
+    return MRHS_OK;
+  }
+  int apply(int prec, const void* X, void* Y) {
+    applies[prec]++;
+    return op_apply(op, prec, false, X, Y, R, s);
+  }
+  template <typename C>
+  int gram(const C* X, const C* Y, double2* G) {
+    return gram_ws(X, Y, G, N, R, R, sizeof(C) == 16 ? MRHS_C128 : MRHS_C64, gpart, s);
+  }
+  template <typename C>
+  int colnorms(const C* X, double* out) {
+    int nblk = num_sms() * 2;
+    int64_t per = (N + nblk - 1) / nblk;
+    if (per < 1) per = 1;
+    nblk = (int)((N + per - 1) / per);
+    if (nblk < 1) nblk = 1;
+    k_colnorm_partial<C><<<nblk, kThreads, 0, s>>>(X, npart, N, R, per);
+    k_colnorm_final<<<1, 64, 0, s>>>(npart, out, nblk, R);
+    MRHS_CUDA_TRY(cudaGetLastError());
+    return MRHS_OK;
+  }
+  int small_launch(int which, int precond = 0) {
+    const size_t smem = factor_smem_bytes(R);
+    if (which == 0) {
+      MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_small_start<<<1, 256, smem, s>>>(st, R, tau);
+    } else if (which == 1) {
+      MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_small_M<<<1, 256, smem, s>>>(st, R, tau);
+    } else {
+      MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_small_S<<<1, 256, smem, s>>>(st, R, tau, precond);
+    }
+    MRHS_CUDA_TRY(cudaGetLastError());
+    return MRHS_OK;
+  }
+  template <typename C>
+  int rotate(C* P1, C* P2, C* D) {
+    const size_t smem = sizeof(C) * (2 * (size_t)R * R + 3 * (size_t)kTile * R);
+    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_rotate<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t grid = (N + kTile - 1) / kTile;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (grid > cap) grid = cap;
+    k_rotate<C><<<(unsigned)grid, kThreads, smem, s>>>(P1, P2, D, st->W, st->S, N, R);
+    MRHS_CUDA_TRY(cudaGetLastError());
+    return MRHS_OK;
+  }
+};
+
+void cheb_coeffs(double lo, double hi, int order, std::vector<double>& c) {
+  const int m1 = order + 1;
+  c.assign(m1, 0.0);
+  for (int j = 0; j < m1; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < m1; ++k) {
+      const double th = M_PI * (k + 0.5) / m1;
+      const double x = 0.5 * ((hi - lo) * std::cos(th) + hi + lo);
+      s += std::cos(j * th) / x;
+    }
+    c[j] = 2.0 * s / m1;
+  }
+  c[0] *= 0.5;
+}
+
+// P = p(H) X, recurrence buffers W, T1, T2 (each N x R of type C).
+template <typename C>
+int cheb_run(Ctx& cx, int prec, double lo, double hi, int order, const C* X, C* P, C* W, C* T1,
+             C* T2) {
+  std::vector<double> c;
+  cheb_coeffs(lo, hi, order, c);
+  const double a = 2.0 / (hi - lo), b = -(hi + lo) / (hi - lo);
+  const int64_t n = cx.N * cx.R;
+  const int g = grid_for(n);
+  if (order == 0) {
+    k_cheb_first<C><<<g, kThreads, 0, cx.s>>>(T1, P, X, X, 0.0, 0.0, c[0], 0.0, n);
+    MRHS_CUDA_TRY(cudaGetLastError());
+    return MRHS_OK;
+  }
+  MRHS_TRY(cx.apply(prec, X, W));
+  k_cheb_first<C><<<g, kThreads, 0, cx.s>>>(T1, P, W, X, a, b, c[0], c[1], n);
+  MRHS_CUDA_TRY(cudaGetLastError());
+  const C* Tprev = X;   // T_{j-1}
+  C* Tcur = T1;         // T_j
+  for (int j = 2; j <= order; ++j) {
+    MRHS_TRY(cx.apply(prec, Tcur, W));
+    // T_{j+1} goes over T_{j-1}, except that the input X is never written
+    C* dst = (Tprev == X) ? T2 : const_cast<C*>(Tprev);
+    k_cheb_step<C><<<g, kThreads, 0, cx.s>>>(dst, P, W, Tcur, Tprev, a, b, c[j], n);
+    MRHS_CUDA_TRY(cudaGetLastError());
+    Tprev = Tcur;
+    Tcur = dst;
+  }
+  return MRHS_OK;
+}
+
+template <typename C>
+struct BcgBufs {
+  C *q = nullptr, *Q = nullptr, *D = nullptr, *z = nullptr, *Zz = nullptr;
+  C *cw = nullptr, *c1 = nullptr, *c2 = nullptr;
+  void carve(Ctx& cx, int64_t n, bool precond) {
+    cx.alloc(&q, n);
+    cx.alloc(&D, n);
+    cx.alloc(&z, n);
+    if (precond) {
+      cx.alloc(&Q, n);
+      cx.alloc(&Zz, n);
+      cx.alloc(&cw, n);
+      cx.alloc(&c1, n);
+      cx.alloc(&c2, n);
+    } else {
+      Q = q;
+    }
+  }
+};
+
+// One block-CG run on H E = F (type C), E in/out. target[j]: absolute
+// stopping level of column j (estimates are in the units of F).
+template <typename C>
+int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* target_host,
+            bool precond, int pprec, double lo, double hi, int order, int maxiter,
+            int check_every, int* iters, int* flag_out) {
+  const int64_t n = cx.N * cx.R;
+  const int g = grid_for(n);
+  const int dt = sizeof(C) == 16 ? MRHS_C128 : MRHS_C64;
+  C *q = b.q, *Q = b.Q, *D = b.D, *z = b.z;
+  MRHS_CUDA_TRY(cudaMemcpyAsync(cx.st->target, target_host, sizeof(double) * cx.R,
+                                cudaMemcpyHostToDevice, cx.s));
+  MRHS_CUDA_TRY(cudaMemsetAsync(&cx.st->flag, 0, sizeof(int), cx.s));
+  // r0 = F - H E
+  MRHS_TRY(cx.apply(prec, E, z));
+  k_sub<C><<<g, kThreads, 0, cx.s>>>(q, F, z, n);
+  MRHS_CUDA_TRY(cudaGetLastError());
+  if (precond) {
+    MRHS_TRY(cheb_run<C>(cx, pprec, lo, hi, order, q, Q, b.cw, b.c1, b.c2));   // Z0 = M^-1 r0
+    MRHS_TRY(cx.gram<C>(Q, q, cx.st->G));                                      // Z0^dag r0
+  } else {
+    MRHS_TRY(cx.gram<C>(q, q, cx.st->G));                                      // R0^dag R0
+  }
+  MRHS_TRY(cx.small_launch(0));
+  // q <- q W (Q <- Q W), D <- Q: rotate with D = 0 and S = 0
+  MRHS_CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(C) * n, cx.s));
+  MRHS_CUDA_TRY(cudaMemsetAsync(cx.st->S, 0, sizeof(double2) * 64 * 64, cx.s));
+  MRHS_TRY(cx.rotate<C>(q, precond ? Q : nullptr, D));
+  int it = 0, flag = 0;
+  for (it = 1; it <= maxiter; ++it) {
+    MRHS_TRY(cx.apply(prec, D, z));                                            // z = H D
+    if (precond) MRHS_TRY(cheb_run<C>(cx, pprec, lo, hi, order, z, b.Zz, b.cw, b.c1, b.c2));
+    MRHS_TRY(cx.gram<C>(D, z, cx.st->G));                                      // D^dag z
+    MRHS_TRY(cx.small_launch(1));                                              // M, MC, -M
+    MRHS_TRY(axpy(E, D, cx.st->MC, 1.0, cx.N, cx.R, cx.R, dt, cx.s));          // E += D M C
+    MRHS_TRY(axpy(q, z, cx.st->negM, 1.0, cx.N, cx.R, cx.R, dt, cx.s));        // t = q - z M
+    if (precond) {
+      MRHS_TRY(axpy(Q, b.Zz, cx.st->negM, 1.0, cx.N, cx.R, cx.R, dt, cx.s));   // T = Q - Z M
+      MRHS_TRY(cx.gram<C>(Q, q, cx.st->G));                                    // T^dag t
+      MRHS_TRY(cx.gram<C>(q, q, cx.st->G2));                                   // t^dag t
+    } else {
+      MRHS_TRY(cx.gram<C>(q, q, cx.st->G));                                    // T^dag T
+    }
+    MRHS_TRY(cx.small_launch(2, precond ? 1 : 0));                             // S, W, C = S C
+    MRHS_TRY(cx.rotate<C>(q, precond ? Q : nullptr, D));                       // q, Q, D
+    if (it % check_every == 0 || it == maxiter) {
+      MRHS_CUDA_TRY(cudaMemcpyAsync(&flag, &cx.st->flag, sizeof(int), cudaMemcpyDeviceToHost, cx.s));
+      MRHS_CUDA_TRY(cudaStreamSynchronize(cx.s));
+      if (flag & (1 | 4)) break;
+    }
+  }
+  if (it > maxiter) it = maxiter;
+  *iters = it;
+  *flag_out = flag;
+  return MRHS_OK;
+}
+
+struct SolveBufs {
+  double *bnorm_d = nullptr, *rnorm_d = nullptr, *rho_d = nullptr;
+  double2* r64 = nullptr;
+  float2 *f32 = nullptr, *e32 = nullptr;
+  BcgBufs<double2> b64;
+  BcgBufs<float2> b32;
+  void carve(Ctx& cx, int R, int64_t n, bool mixed, bool precond) {
+    const int nblk = num_sms() * 4;
+    cx.alloc(&cx.st, 1);
+    cx.alloc(&cx.gpart, gram_workspace_bytes(cx.N, R, R) / sizeof(double2) + 1);
+    cx.alloc(&cx.npart, (size_t)nblk * R + R);
+    cx.alloc(&bnorm_d, R);
+    cx.alloc(&rnorm_d, R);
+    cx.alloc(&rho_d, R);
+    cx.alloc(&r64, n);
+    if (mixed) {
+      cx.alloc(&f32, n);
+      cx.alloc(&e32, n);
+      b32.carve(cx, n, precond);
+    } else {
+      b64.carve(cx, n, precond);
+    }
+  }
+};
+
+}  // namespace
+
+int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
+          mrhs_solve_info* info, cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  Ctx cx;
+  cx.op = op;
+  cx.s = s;
+  cx.R = R;
+  cx.N = op->V * op->nb;
+  cx.tau = p.breakdown_tau > 0 ? p.breakdown_tau : 1e-12;
+  const int64_t n = cx.N * R;
+  const int g = grid_for(n);
+  const bool mixed = p.mode == MRHS_SOLVE_MIXED;
+  SolveBufs sb;
+  sb.carve(cx, R, n, mixed, p.precond != 0);          // sizing pass
+  MRHS_TRY(op->ws_solve.ensure(cx.used));
+  cx.base = (char*)op->ws_solve.ptr;
+  cx.used = 0;
+  sb.carve(cx, R, n, mixed, p.precond != 0);          // assignment pass
+  MRHS_CUDA_TRY(cudaMemsetAsync(cx.st, 0, sizeof(Small), s));
+
+  double lo = p.cheb_lo, hi = p.cheb_hi;
+  if (p.precond && hi <= 0.0) return fail(MRHS_ERR_INVALID_ARG, "cheb_hi must be given (> 0)");
+  if (p.precond && lo <= 0.0) lo = hi / 400.0;
+  if (p.precond && !(lo < hi)) return fail(MRHS_ERR_INVALID_ARG, "cheb_lo must be < cheb_hi");
+
+  MRHS_TRY(cx.colnorms<double2>(B, sb.bnorm_d));
+  k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, sb.bnorm_d, cx.N, R);
+  std::vector<double> bnorm(R), rnorm(R), target(R);
+  MRHS_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), sb.bnorm_d, sizeof(double) * R,
+                                cudaMemcpyDeviceToHost, s));
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  int total_iters = 0, cycles = 0, status = MRHS_OK, flag = 0;
+
+  auto true_residual = [&]() -> int {   // r64 = B - H X (FP64), rnorm
+    MRHS_TRY(cx.apply(MRHS_PREC_FP64, X, sb.r64));
+    k_sub<double2><<<g, kThreads, 0, s>>>(sb.r64, B, sb.r64, n);
+    MRHS_CUDA_TRY(cudaGetLastError());
+    MRHS_TRY(cx.colnorms<double2>(sb.r64, sb.rnorm_d));
+    MRHS_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), sb.rnorm_d, sizeof(double) * R,
+                                  cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    return MRHS_OK;
+  };
+  auto all_done = [&]() {
+    for (int j = 0; j < R; ++j)
+      if (bnorm[j] > 0 && !(rnorm[j] <= p.tol * bnorm[j])) return false;
+    return true;
+  };
+  const int every = p.check_every > 0 ? p.check_every : 1;
+
+  if (!mixed) {
+    for (int j = 0; j < R; ++j) target[j] = p.tol * bnorm[j];
+    int it = 0;
+    MRHS_TRY(run_bcg<double2>(cx, sb.b64, MRHS_PREC_FP64, B, X, target.data(), p.precond != 0,
+                              p.precond_prec, lo, hi, p.cheb_order, p.maxiter, every, &it, &flag));
+    total_iters = it;
+    cycles = 1;
+    MRHS_TRY(true_residual());
+  } else {
+    MRHS_TRY(true_residual());
+    for (cycles = 0; cycles < p.max_cycles && !all_done() && total_iters < p.maxiter; ++cycles) {
+      // scale each residual column to unit norm; inner target relative to 1
+      std::vector<double> rho(R);
+      for (int j = 0; j < R; ++j) {
+        rho[j] = (bnorm[j] > 0 && rnorm[j] > p.tol * bnorm[j]) ? rnorm[j] : 0.0;
+        const double want = rho[j] > 0 ? 0.5 * p.tol * bnorm[j] / rho[j] : 1.0;
+        target[j] = std::fmax(p.inner_tol, want);
+      }
+      MRHS_CUDA_TRY(cudaMemcpyAsync(sb.rho_d, rho.data(), sizeof(double) * R,
+                                    cudaMemcpyHostToDevice, s));
+      k_scale_to_c64<<<g, kThreads, 0, s>>>(sb.f32, sb.r64, sb.rho_d, cx.N, R);
+      MRHS_CUDA_TRY(cudaMemsetAsync(sb.e32, 0, sizeof(float2) * n, s));
+      MRHS_CUDA_TRY(cudaGetLastError());
+      int it = 0;
+      MRHS_TRY(run_bcg<float2>(cx, sb.b32, MRHS_PREC_FP32, sb.f32, sb.e32, target.data(),
+                               p.precond != 0, p.precond_prec, lo, hi, p.cheb_order,
+                               p.maxiter - total_iters, every, &it, &flag));
+      total_iters += it;
+      k_update_x<<<g, kThreads, 0, s>>>(X, sb.e32, sb.rho_d, cx.N, R);
+      MRHS_CUDA_TRY(cudaGetLastError());
+      MRHS_TRY(true_residual());
+      if (flag & 4) break;
+    }
+  }
+  if (flag & 4) status = MRHS_ERR_NONFINITE;
+  else if (!all_done()) status = MRHS_ERR_NOT_CONVERGED;
+  if (info) {
+    info->status = status;
+    info->iters = total_iters;
+    info->cycles = cycles;
+    info->nrhs = R;
+    for (int i = 0; i < 4; ++i) info->applies[i] = cx.applies[i];
+    for (int j = 0; j < MRHS_MAX_RHS; ++j)
+      info->resid[j] = j < R ? (bnorm[j] > 0 ? rnorm[j] / bnorm[j] : 0.0) : 0.0;
+    info->cheb_lo = lo;
+    info->cheb_hi = hi;
+  }
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info)
+    info->ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (status != MRHS_OK)
+    set_error(status == MRHS_ERR_NONFINITE ? "non-finite value in block CG" : "not converged");
+  return status;
+}
+
+// standalone Chebyshev application (entry point cheby_apply); recurrence
+// buffers come from the operator's grow-only workspace, so calls on one
+// operator must not overlap on the GPU.
+int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* X, void* P,
+          int R, cudaStream_t s) {
+  Ctx cx;
+  cx.op = op;
+  cx.s = s;
+  cx.R = R;
+  cx.N = op->V * op->nb;
+  const int64_t n = cx.N * R;
+  const size_t es = prec == MRHS_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  MRHS_TRY(op->ws_cheb.ensure(3 * (n * es + 256)));
+  char* base = (char*)op->ws_cheb.ptr;
+  const size_t stride = (n * es + 255) / 256 * 256;
+  if (prec == MRHS_PREC_FP64)
+    return cheb_run<double2>(cx, prec, lo, hi, order, (const double2*)X, (double2*)P,
+                             (double2*)base, (double2*)(base + stride),
+                             (double2*)(base + 2 * stride));
+  return cheb_run<float2>(cx, prec, lo, hi, order, (const float2*)X, (float2*)P, (float2*)base,
+                          (float2*)(base + stride), (float2*)(base + 2 * stride));
+}
+
+}  // namespace mrhs

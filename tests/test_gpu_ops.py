@@ -1,0 +1,285 @@
+"""GPU parity: every kernel through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 per right-hand side): FP64 operator 1e-12; FP32 and
+BF16/FP16 operators 1e-5 against the oracle's exact value of the same
+quantised operator (oracle.lowprec), i.e. what remains is FP32 accumulation.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.chol import chol_upper
+from oracle.lowprec import lowprec_apply
+from oracle.ops import coarse_op_apply, coarse_op_apply_dag
+from oracle.solvers import cheby_apply as oracle_cheby
+from synth import coarse_op, load_shift, stencil, vectors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrhs():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2409_03904_b300 as m
+    return m
+
+
+def rel_per_rhs(Y, ref):
+    Y = np.asarray(Y).reshape(-1, ref.shape[-1])
+    ref = ref.reshape(-1, ref.shape[-1])
+    num = np.linalg.norm(Y - ref, axis=0)
+    den = np.maximum(np.linalg.norm(ref, axis=0), 1e-300)
+    return np.max(num / den)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+SHAPES = [((4, 3, 2, 3), 16, 81, 8), ((2, 2, 2, 2), 3, 9, 1), ((3, 3, 3, 3), 24, 9, 4),
+          ((1, 1, 1, 1), 8, 81, 2), ((3, 2, 2, 2), 48, 81, 32), ((2, 3, 2, 2), 32, 9, 64),
+          ((2, 2, 3, 2), 5, 81, 13)]
+
+
+@pytest.mark.parametrize("L,nb,npts,R", SHAPES)
+def test_fp64_fp32_op_and_dag(mrhs, L, nb, npts, R):
+    disp, _ = stencil(npts)
+    rng = np.random.default_rng(nb * 1000 + R)
+    V = int(np.prod(L))
+    A = rng.standard_normal((V, npts, nb, nb)) + 1j * rng.standard_normal((V, npts, nb, nb))
+    X = vectors(L, nb, R, 99)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32"))
+    Y = op.apply(dev(X), "fp64").cpu().numpy()
+    assert rel_per_rhs(Y, coarse_op_apply(A, X, L, disp)) <= 1e-12
+    Yd = op.apply_dag(dev(X), "fp64").cpu().numpy()
+    assert rel_per_rhs(Yd, coarse_op_apply_dag(A, X, L, disp)) <= 1e-12
+    Y32 = op.apply(dev(X.astype(np.complex64)), "fp32").cpu().numpy()
+    assert rel_per_rhs(Y32, lowprec_apply(A, X, L, disp, "fp32")) <= 1e-5
+    Yd32 = op.apply_dag(dev(X.astype(np.complex64)), "fp32").cpu().numpy()
+    from oracle.lowprec import quantise_op, quantise_vec
+    refd = coarse_op_apply_dag(quantise_op(A, "fp32"), quantise_vec(X, "fp32"), L, disp)
+    assert rel_per_rhs(Yd32, refd) <= 1e-5
+
+
+TC_SHAPES = [((4, 3, 2, 3), 16, 81, 8), ((2, 2, 2, 2), 3, 9, 1), ((3, 3, 3, 3), 24, 9, 4),
+             ((3, 2, 2, 2), 48, 81, 32), ((2, 3, 2, 2), 32, 9, 64), ((2, 2, 3, 2), 5, 81, 13),
+             ((3, 3, 2, 2), 48, 81, 12), ((2, 2, 2, 2), 64, 9, 16), ((5, 1, 1, 1), 8, 9, 3)]
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp16"])
+@pytest.mark.parametrize("L,nb,npts,R", TC_SHAPES)
+def test_tensor_core_op(mrhs, kind, L, nb, npts, R):
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 4242 + nb, 12.0)
+    X = vectors(L, nb, R, 4243)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", kind))
+    Y = op.apply(dev(X.astype(np.complex64)), kind).cpu().numpy()
+    assert mrhs.device_error() == 0
+    ref = lowprec_apply(A, X, L, disp, kind)
+    assert rel_per_rhs(Y, ref) <= 1e-5
+    # against the unquantised FP64 operator: the quantisation error itself
+    exact = coarse_op_apply(A, X, L, disp)
+    bound = 2.0 ** -6 if kind == "bf16" else 2.0 ** -9
+    assert rel_per_rhs(Y, exact) <= bound
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp16"])
+def test_tensor_core_dag(mrhs, kind):
+    L, nb, npts, R = (3, 2, 3, 2), 16, 81, 8
+    disp, _ = stencil(npts)
+    rng = np.random.default_rng(7)
+    V = int(np.prod(L))
+    A = rng.standard_normal((V, npts, nb, nb)) + 1j * rng.standard_normal((V, npts, nb, nb))
+    X = vectors(L, nb, R, 7)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", kind))
+    Y = op.apply_dag(dev(X.astype(np.complex64)), kind).cpu().numpy()
+    # the daggered operator's own coefficient field, quantised by the same rule
+    from oracle.ops import neighbour_table
+    back = neighbour_table(L, -disp.astype(np.int64))
+    Ad = np.empty_like(A)
+    for p in range(npts):
+        Ad[:, p] = np.conj(np.swapaxes(A[back[p], p], -1, -2))
+    ref = lowprec_apply(Ad, X, L, -disp.astype(np.int64), kind)
+    assert rel_per_rhs(Y, ref) <= 1e-5
+
+
+def test_tc_repeat_and_large_nrhs_stream(mrhs):
+    """Many sites per CTA (persistent loop, both accumulators, ring wrap)."""
+    L, nb, npts, R = (6, 6, 4, 4), 32, 81, 16
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 5150, 18.0)
+    X = vectors(L, nb, R, 5151)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("bf16",))
+    Xd = dev(X.astype(np.complex64))
+    Y1 = op.apply(Xd, "bf16")
+    Y2 = op.apply(Xd, "bf16")
+    assert torch.equal(Y1, Y2)          # deterministic
+    ref = lowprec_apply(A, X, L, disp, "bf16")
+    assert rel_per_rhs(Y1.cpu().numpy(), ref) <= 1e-5
+    assert mrhs.device_error() == 0
+
+
+@pytest.mark.parametrize("N,rx,ry", [(1, 1, 1), (1000, 4, 4), (33333, 12, 7), (200000, 32, 32),
+                                     (5, 64, 64), (0, 3, 3)])
+def test_block_inner(mrhs, N, rx, ry):
+    rng = np.random.default_rng(N + rx)
+    X = rng.standard_normal((N, rx)) + 1j * rng.standard_normal((N, rx))
+    Y = rng.standard_normal((N, ry)) + 1j * rng.standard_normal((N, ry))
+    G = mrhs.block_inner(dev(X), dev(Y)).cpu().numpy()
+    ref = np.conj(X).T @ Y
+    scale = max(np.linalg.norm(X) * np.linalg.norm(Y), 1e-300)
+    assert np.linalg.norm(G - ref) <= 1e-13 * scale
+    X32, Y32 = X.astype(np.complex64), Y.astype(np.complex64)
+    G32 = mrhs.block_inner(dev(X32), dev(Y32)).cpu().numpy()
+    ref32 = np.conj(X32.astype(np.complex128)).T @ Y32.astype(np.complex128)
+    assert np.linalg.norm(G32 - ref32) <= 1e-6 * scale
+    G2 = mrhs.block_inner(dev(X), dev(Y)).cpu().numpy()
+    assert np.array_equal(G, G2)        # fixed reduction order
+
+
+@pytest.mark.parametrize("N,rin,rout,beta", [(1, 1, 1, 0.0), (1000, 4, 4, 1.0),
+                                             (33333, 12, 7, -0.5), (70001, 32, 32, 0.0),
+                                             (7, 64, 64, 2.0)])
+def test_block_axpy(mrhs, N, rin, rout, beta):
+    rng = np.random.default_rng(N + rin)
+    X = rng.standard_normal((N, rin)) + 1j * rng.standard_normal((N, rin))
+    Y = rng.standard_normal((N, rout)) + 1j * rng.standard_normal((N, rout))
+    M = rng.standard_normal((rin, rout)) + 1j * rng.standard_normal((rin, rout))
+    ref = beta * Y + X @ M
+    out = mrhs.block_axpy(dev(Y), dev(X), dev(M), beta).cpu().numpy()
+    assert np.linalg.norm(out - ref) <= 1e-13 * np.linalg.norm(ref)
+    out32 = mrhs.block_axpy(dev(Y.astype(np.complex64)), dev(X.astype(np.complex64)), dev(M),
+                            beta).cpu().numpy()
+    assert np.linalg.norm(out32 - ref) <= 1e-5 * np.linalg.norm(ref)
+    if rin == rout:   # in place: X aliases Y
+        Xd = dev(X)
+        mrhs.block_axpy(Xd, Xd, dev(M), beta)
+        ref2 = beta * X + X @ M
+        assert np.linalg.norm(Xd.cpu().numpy() - ref2) <= 1e-13 * np.linalg.norm(ref2)
+
+
+@pytest.mark.parametrize("r", [1, 4, 12, 32, 64])
+def test_herm_factor(mrhs, r):
+    rng = np.random.default_rng(r)
+    T = rng.standard_normal((200, r)) + 1j * rng.standard_normal((200, r))
+    G = np.conj(T).T @ T
+    S, W, k = mrhs.herm_factor(dev(G))
+    S, W = S.cpu().numpy(), W.cpu().numpy()
+    assert k == r
+    assert np.allclose(S, chol_upper(G), atol=1e-10 * np.sqrt(np.max(np.diag(G).real)))
+    assert np.allclose(S @ W, np.eye(r), atol=1e-9)
+    if r >= 4:   # rank deficient: duplicated and dependent columns
+        T[:, 1] = T[:, 0]
+        T[:, 3] = 2 * T[:, 2] - 1j * T[:, 0]
+        G = np.conj(T).T @ T
+        S, W, k = mrhs.herm_factor(dev(G), 1e-12)
+        S, W = S.cpu().numpy(), W.cpu().numpy()
+        assert k == r - 2
+        Q = T @ W
+        assert np.allclose(np.conj(Q).T @ Q, np.diag([1.0] * k + [0.0] * (r - k)), atol=1e-8)
+        assert np.allclose(Q @ S, T, atol=1e-8 * np.linalg.norm(T))
+
+
+@pytest.mark.parametrize("kind", ["fp64", "fp32", "bf16"])
+def test_cheby_apply(mrhs, kind):
+    L, nb, npts, R = (3, 3, 2, 2), 16, 81, 4
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 61, 18.0)
+    X = vectors(L, nb, R, 62)
+    lo, hi, m = 0.5, 40.0, 8
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "bf16"))
+    if kind == "fp64":
+        P = op.cheby(dev(X), lo, hi, m, "fp64").cpu().numpy()
+        ref = oracle_cheby(lambda V: coarse_op_apply(A, V, L, disp), X, lo, hi, m)
+        assert rel_per_rhs(P, ref) <= 1e-11
+    else:
+        P = op.cheby(dev(X.astype(np.complex64)), lo, hi, m, kind).cpu().numpy()
+        ref = oracle_cheby(lambda V: lowprec_apply(A, V, L, disp, kind), X, lo, hi, m)
+        assert rel_per_rhs(P, ref) <= 1e-4
+
+
+def test_solve_fp64_small(mrhs):
+    from tests.test_oracle_ops import dense_matrix
+    L, nb, npts, R = (2, 3, 2, 2), 8, 81, 4
+    disp, _ = stencil(npts)
+    A0 = coarse_op(L, nb, npts, 77, 0.0)
+    ev = np.linalg.eigvalsh(dense_matrix(A0, L, disp))
+    c = (ev[-1] - 1e3 * ev[0]) / (1e3 - 1)
+    A = coarse_op(L, nb, npts, 77, c)
+    B = vectors(L, nb, R, 78)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "bf16"))
+    X, info = op.solve(dev(B), tol=1e-10, maxiter=1000)
+    X = X.cpu().numpy()
+    H = dense_matrix(A, L, disp)
+    ref = np.linalg.solve(H, B.reshape(-1, R))
+    assert max(info["resid"]) <= 1e-10
+    assert np.linalg.norm(X.reshape(-1, R) - ref) <= 1e3 * 1e-9 * np.linalg.norm(ref)
+    res = np.linalg.norm(B.reshape(-1, R) - H @ X.reshape(-1, R), axis=0) / np.linalg.norm(
+        B.reshape(-1, R), axis=0)
+    assert np.all(res <= 1e-10 * 1.01)
+    # preconditioned FP64 and mixed precision reach the same solution
+    Xp, ip = op.solve(dev(B), tol=1e-10, precond=1, precond_prec="fp64", cheb_hi=1.1 * ev[-1] + c,
+                      cheb_lo=0.1, cheb_order=8)
+    assert max(ip["resid"]) <= 1e-10 and ip["iters"] < info["iters"]
+    Xm, im = op.solve(dev(B), mode="mixed", tol=1e-10, precond=1, precond_prec="bf16",
+                      cheb_hi=1.1 * ev[-1] + c, cheb_lo=0.2, cheb_order=8)
+    assert max(im["resid"]) <= 1e-10, im
+    assert np.linalg.norm(Xm.cpu().numpy().reshape(-1, R) - ref) <= 1e3 * 1e-9 * np.linalg.norm(ref)
+    assert mrhs.device_error() == 0
+
+
+def test_solve_edge_cases(mrhs):
+    L, nb, npts = (2, 2, 2, 2), 4, 9
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 88, 6.0)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "fp16"))
+    B = vectors(L, nb, 4, 89)
+    B[:, :, 1] = 0.0                  # zero column
+    B[:, :, 3] = B[:, :, 0]           # duplicated column
+    for mode, kw in (("fp64", {}), ("mixed", dict(precond=1, precond_prec="fp16", cheb_hi=14.0,
+                                                  cheb_lo=0.5, cheb_order=6))):
+        X, info = op.solve(dev(B), mode=mode, tol=1e-9, maxiter=500, **kw)
+        X = X.cpu().numpy()
+        assert np.all(X[:, :, 1] == 0)
+        assert max(info["resid"]) <= 1e-9, (mode, info)
+        assert np.allclose(X[:, :, 3], X[:, :, 0], atol=1e-8 * np.abs(X).max())
+    # single right-hand side and an initial guess that is already the answer
+    B1 = B[:, :, :1].copy()
+    X1, i1 = op.solve(dev(B1), tol=1e-11)
+    X2, i2 = op.solve(dev(B1), X0=X1, tol=1e-9)
+    assert i2["iters"] <= 1 and max(i2["resid"]) <= 1e-9
+
+
+def test_invalid_arguments(mrhs):
+    L, nb, npts = (2, 2, 2, 2), 4, 9
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 1, 6.0)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64",))
+    X = dev(vectors(L, nb, 2, 1))
+    with pytest.raises(mrhs.MrhsError):
+        op.apply(X.to(torch.complex64), "bf16")            # precision not built
+    with pytest.raises(mrhs.MrhsError):
+        op.apply(X, "fp64", out=X)                         # aliasing
+    with pytest.raises(mrhs.MrhsError):
+        mrhs.CoarseOp(dev(A), L, np.roll(disp, 1, axis=0), ("fp64",))   # p = 0 not self
+    with pytest.raises(TypeError):
+        op.apply(X.cpu(), "fp64")
+
+
+def test_named_workload_solve(mrhs):
+    """4^4, nb 24, 9-point, kappa 1e3, 4 RHS, FP64 block CG to 1e-10 against
+    the dense 6144 x 6144 LU solve of the same operator."""
+    name = "L4_nb24_9pt_r4"
+    from synth import WORKLOADS
+    w = WORKLOADS[name]
+    disp, _ = stencil(w["npts"])
+    A = coarse_op(w["L"], w["nb"], w["npts"], w["seed"], load_shift(name))
+    B = vectors(w["L"], w["nb"], w["nrhs"], w["seed"])
+    op = mrhs.CoarseOp(dev(A), w["L"], disp, ("fp64",))
+    X, info = op.solve(dev(B), tol=w["tol"], maxiter=2000)
+    assert max(info["resid"]) <= w["tol"]
+    from tests.test_oracle_ops import dense_matrix
+    H = dense_matrix(A, w["L"], disp)
+    ref = np.linalg.solve(H, B.reshape(-1, w["nrhs"]))
+    err = np.linalg.norm(X.cpu().numpy().reshape(-1, w["nrhs"]) - ref) / np.linalg.norm(ref)
+    assert err <= w["kappa"] * w["tol"]
