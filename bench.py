@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark: block-CG time to a 1e-8 residual per right-hand side (mixed
+precision vs plain FP64) and the coarse operator's TFLOP/s at 32 RHS.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+Workload (default): 12^4 coarse lattice, nb = 48, 81-point stencil, 32
+right-hand sides, condition ~1e4, synthetic seeded operator and sources
+(see synth/).  One step = one complete mixed-precision solve to a true FP64
+relative residual of 1e-8 on every RHS: FP64 outer defect correction (true
+residual, Gram accumulation, Cholesky, solution update), complex64 inner
+Chebyshev-preconditioned block CG with the FP32 operator, FP16 tensor-core
+Chebyshev preconditioner.  value = ms per RHS (lower is better).
+
+Multi-GPU (torchrun): the solve does not shard in this build; every rank
+solves its own independent batch of right-hand sides against its own copy of
+the operator (replicas, weak scaling), value = max time / all RHS.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("coarse-op TFLOP/s at Nrhs=32; block-CG time-to-1e-8 per RHS, mixed vs FP64")
+DEFAULT_WORKLOAD = "L12_nb48_81pt_r32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precond", default="fp16", choices=["fp16", "bf16", "fp32"])
+    ap.add_argument("--cheb-order", type=int, default=16)
+    ap.add_argument("--cheb-ratio", type=float, default=400.0, help="hi / lo")
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--fp64-iters", type=int, default=3,
+                    help="FP64 block-CG iterations timed for the plain-FP64 comparison")
+    ap.add_argument("--fp64-full", action="store_true",
+                    help="run the plain FP64 solve to convergence (slow)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the standalone operator, FP64 and e2e measurements")
+    ap.add_argument("--cpu-sites", type=int, default=96, help="oracle sample size (sites)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d.get("bf16_tflops"), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, 1800.0, "fallback"
+
+
+def op_flops(w, R):
+    V = int(np.prod(w["L"]))
+    return 8.0 * w["nb"] ** 2 * R * w["npts"] * V
+
+
+def op_bytes(w, R, prec):
+    """Algorithmic bytes of one application: coefficients once, input and
+    output vectors once (neighbour re-reads not counted)."""
+    V = int(np.prod(w["L"]))
+    coef = {"fp64": 16, "fp32": 8, "bf16": 4, "fp16": 4}[prec]
+    vec = 16 if prec == "fp64" else 8
+    extra = 8 * V if prec in ("bf16", "fp16") else 0          # site scale + diagonal
+    return w["npts"] * V * w["nb"] ** 2 * coef + extra + 2 * V * w["nb"] * R * vec
+
+
+# ---------------------------------------------------------------- oracle leg
+class OracleSample:
+    """Oracle (plain C + OpenMP, FP64) coarse operator on a sample of sites.
+
+    The timed quantity is one application on the sampled sites, scaled to
+    the whole lattice and multiplied by the FP64 block-CG application count
+    (iterations + 2 residual evaluations), per RHS: the oracle's own
+    time-to-solution for the plain FP64 method on this workload."""
+
+    def __init__(self, w, shift, sites):
+        from synth import coarse_op, stencil
+        self.w = w
+        self.disp, _ = stencil(w["npts"])
+        self.V = int(np.prod(w["L"]))
+        rng = np.random.default_rng(0)
+        self.idx = np.sort(rng.choice(self.V, size=min(sites, self.V), replace=False))
+        self.A_s = coarse_op(w["L"], w["nb"], w["npts"], w["seed"], shift, sites=self.idx)
+
+    def ms_per_rhs(self, B_host, fp64_iters):
+        from oracle import native
+        w = self.w
+        native.coarse_op_apply_sites(self.A_s[:2], B_host, w["L"], self.disp, self.idx[:2])
+        t0 = time.perf_counter()
+        native.coarse_op_apply_sites(self.A_s, B_host, w["L"], self.disp, self.idx)
+        dt = time.perf_counter() - t0
+        full_ms = dt * 1e3 * self.V / len(self.idx)
+        R = B_host.shape[-1]
+        return full_ms * (fp64_iters + 2) / R, dict(
+            sample=f"FP64 oracle operator on {len(self.idx)} of {self.V} sites ({dt:.2f} s), "
+                   f"scaled x{self.V / len(self.idx):.0f} to one application, x{fp64_iters + 2} "
+                   "applications (FP64 block-CG iterations + 2)",
+            full_apply_ms=full_ms,
+            cores=int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+
+
+def fp64_iteration_count(name):
+    """Iterations the plain FP64 block CG needs on this workload, as measured
+    on the GPU and recorded in profiles/fp64_block_cg_iterations.txt."""
+    p = os.path.join(ROOT, "profiles", "fp64_block_cg_iterations.txt")
+    try:
+        with open(p) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 2 and parts[0] == name and parts[1].isdigit():
+                    return int(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+def run_reference(a, w, shift):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch  # noqa: F401  (only to match the environment of the other arm)
+    from synth import vectors
+    R = w["nrhs"]
+    B = vectors(w["L"], w["nb"], R, w["seed"])
+    iters = fp64_iteration_count(w["name"]) or 0
+    sample = OracleSample(w, shift, a.cpu_sites)
+    vals = []
+    for i in range(a.warmup + a.steps):
+        v, meta = sample.ms_per_rhs(B, iters)
+        if i >= a.warmup:
+            vals.append(v)
+    val = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "ms/RHS",
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": val * R,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": w["name"], "nrhs": R, "tol": 1e-8},
+           "cpu_baseline": {"value": val, "unit": "ms/RHS", "cores": meta["cores"],
+                            "kind": "oracle", "sample": meta["sample"]},
+           "e2e": {"value": val, "unit": "ms/RHS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "fp64_iterations": iters}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    a = parse()
+    from synth import WORKLOADS, load_shift
+    w = WORKLOADS[a.workload]
+    shift = load_shift(a.workload)
+    if a.impl == "reference":
+        return run_reference(a, w, shift)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import paper_2409_03904_b300 as mrhs
+    import synth.device as sdev
+    from synth import stencil
+    dev = torch.device("cuda", local)
+    R, V, nb = w["nrhs"], int(np.prod(w["L"])), w["nb"]
+    disp, _ = stencil(w["npts"])
+
+    t0 = time.time()
+    A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
+    op = mrhs.CoarseOp(A, w["L"], disp, ("fp64", "fp32", "bf16", "fp16"))
+    del A
+    torch.cuda.empty_cache()
+    B = sdev.vectors(w["L"], nb, R, w["seed"] + 7919 * rank, device=dev)
+    setup_s = time.time() - t0
+    lam = op.lambda_max(a.precond, 40)
+    hi = 1.08 * lam
+    params = dict(mode="mixed", tol=1e-8, precond=1, precond_prec=a.precond,
+                  cheb_order=a.cheb_order, cheb_hi=hi, cheb_lo=hi / a.cheb_ratio,
+                  inner_tol=a.inner_tol, maxiter=20000, max_cycles=20, check_every=4)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        X, info = op.solve(B, **params)
+    # ---------------- timed region: K complete solves
+    op.kernel_timing(True)
+    launches0 = mrhs.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            X, info = op.solve(B, **params)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = mrhs.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    kt = {p: op.kernel_time(p) for p in ("fp16", "bf16", "fp32", "fp64")}
+    op.kernel_timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / a.steps
+    value = ms_step / (R * world)
+    resid = max(max(i["resid"]) for i in infos)
+
+    # ---------------- dominant kernel roofline (live, from the timed region)
+    hbm, bf16_peak, peak_kind = peaks()
+    n16, ms16 = kt[a.precond]
+    roof = None
+    if n16:
+        per = ms16 / n16
+        byts = op_bytes(w, R, a.precond)
+        ach = byts / (per * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "kernel": f"tcgen05 {a.precond} coarse operator",
+                "algorithmic_bytes": byts, "launch_ms": per, "launches": n16,
+                "peak_kind": f"{peak_kind} copy bandwidth"}
+
+    extras = {}
+    if not a.no_extras and rank == 0:
+        # standalone coarse-operator throughput at this RHS count, per precision
+        cop = {}
+        for p in ("fp16", "bf16", "fp32", "fp64"):
+            Xp = B if p == "fp64" else B.to(torch.complex64)
+            reps = 2 if p == "fp64" else 10
+            op.apply(Xp, p)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                op.apply(Xp, p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps
+            cop[p] = {"ms": t, "tflops": op_flops(w, R) / (t * 1e-3) / 1e12,
+                      "gbs": op_bytes(w, R, p) / (t * 1e-3) / 1e9}
+        extras["coarse_op"] = cop
+        # plain FP64 block CG: time per iteration, extrapolated when not run to the end
+        if a.fp64_full:
+            Xf, fi = op.solve(B, tol=1e-8, maxiter=20000, raise_on_fail=False)
+            fp64 = {"iters": fi["iters"], "ms": fi["ms_total"], "resid": max(fi["resid"]),
+                    "ms_per_rhs": fi["ms_total"] / R, "extrapolated": False}
+        else:
+            Xf, fi = op.solve(B, tol=1e-30, maxiter=a.fp64_iters, raise_on_fail=False)
+            per_it = (fi["ms_total"] - 2 * cop["fp64"]["ms"]) / max(fi["iters"], 1)
+            n_it = fp64_iteration_count(w["name"])
+            fp64 = {"ms_per_iter": per_it, "iters_to_tol": n_it, "extrapolated": True,
+                    "ms_per_rhs": (per_it * n_it + 2 * cop["fp64"]["ms"]) / R if n_it else None}
+        extras["fp64_solve"] = fp64
+        if fp64.get("ms_per_rhs"):
+            extras["mixed_speedup_vs_fp64"] = fp64["ms_per_rhs"] / value
+        # end to end through the public API with host buffers
+        Bh = B.cpu().pin_memory()
+        Xh = torch.empty_like(Bh).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            Bd = Bh.to(dev, non_blocking=True)
+            Xd, _i = op.solve(Bd, **params)
+            Xh.copy_(Xd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / a.steps
+        extras["e2e"] = {"value": e2e_ms / R, "unit": "ms/RHS",
+                         "h2d_bytes_per_step": Bh.numel() * 16, "d2h_bytes_per_step": Xh.numel() * 16}
+        # CPU oracle on a bounded sample of the same workload
+        n_it = fp64_iteration_count(w["name"])
+        cpu_v, meta = OracleSample(w, shift, a.cpu_sites).ms_per_rhs(Bh.numpy(), n_it or 0)
+        extras["cpu_baseline"] = {"value": cpu_v if n_it else None, "unit": "ms/RHS",
+                                  "cores": meta["cores"], "kind": "oracle",
+                                  "sample": meta["sample"] + ("" if n_it else
+                                                              "; FP64 iteration count unknown"),
+                                  "full_apply_ms": meta["full_apply_ms"]}
+
+    if rank == 0:
+        inf = infos[-1]
+        out = {"metric": METRIC, "value": value, "unit": "ms/RHS", "n_gpus": world,
+               "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step,
+               "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64+f32+" + a.precond, "data": "synthetic",
+               "config": {"workload": w["name"], "L": list(w["L"]), "nb": nb, "npts": w["npts"],
+                          "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
+                          "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
+                                     f"[{hi / a.cheb_ratio:.4g}, {hi:.4g}]",
+                          "inner_tol": a.inner_tol, "parallelism": f"replicas x{world}",
+                          "l2": "inputs larger than L2 (coefficients "
+                                f"{op_bytes(w, R, a.precond) / 1e9:.1f} GB per application)"},
+               "solve": {"iters": inf["iters"], "cycles": inf["cycles"], "applies": inf["applies"],
+                         "max_true_resid": resid, "lambda_max_est": lam, "setup_s": setup_s},
+               "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
+        out.update(extras)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,15 @@ int herm_factor(const void* G, void* S, void* W, int32_t* rank, int32_t r, doubl
 int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, const void* X,
                 void* P, int32_t nrhs, void* stream);
 
+/* Largest-eigenvalue estimate of a Hermitian positive operator by the power
+ * method (Sec. 2.3: the upper end of the Chebyshev interval is obtained
+ * "with a cheap application of the power method"): Rayleigh quotient after
+ * `iters` applications in precision `prec` to one deterministic start vector.
+ * The estimate lies below the true maximum; it is cached on the operator and
+ * block_cg_solve uses 1.08 x the cached value when cheb_hi <= 0.  Uses
+ * operator-owned workspace; synchronises `stream`. */
+int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, void* stream);
+
 /* Solver parameters (block_cg_solve). */
 typedef struct {
   double tol;           /* per-RHS relative true residual |b_r - H x_r| / |b_r| */
@@ -143,11 +152,15 @@ typedef struct {
   int32_t mode;         /* MRHS_SOLVE_FP64 or MRHS_SOLVE_MIXED */
   int32_t precond;      /* 0: BlockCGrQ (Fig. 2 left); 1: Chebyshev-preconditioned
                            BlockCGrQ (Fig. 2 right) */
-  int32_t precond_prec; /* MRHS_PREC_* of the Chebyshev operator applications */
+  int32_t precond_prec; /* MRHS_PREC_* of the Chebyshev operator applications
+                           (default MRHS_PREC_FP16) */
   int32_t cheb_order;   /* polynomial degree */
-  double cheb_lo;       /* Chebyshev interval; cheb_hi <= 0: hi = 1.05 x power- */
+  double cheb_lo;       /* Chebyshev interval; cheb_hi <= 0: hi = 1.08 x power- */
   double cheb_hi;       /*   method estimate; cheb_lo <= 0: lo = hi / 400 */
-  double inner_tol;     /* MIXED: residual reduction per refinement cycle */
+  double inner_tol;     /* MIXED: residual reduction per refinement cycle; a
+                           cycle also ends when the recurrence estimate has not
+                           improved by 30% over 32 iterations (a low-precision
+                           preconditioner is not exactly linear) */
   int32_t max_cycles;   /* MIXED: refinement cycles */
   int32_t check_every;  /* read the convergence flag every k iterations */
   double breakdown_tau; /* relative Cholesky pivot threshold */
@@ -190,6 +203,18 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode);
  * bit, drains its own copies, frees its tensor memory and returns, leaving
  * its output undefined.  Synchronises the current device. */
 int32_t mrhs_device_error(void);
+
+/* Measurement hooks.  mrhs_op_kernel_timing(op, 1) makes every following
+ * application of `op` record a CUDA event pair on its stream around the
+ * operator's main kernel (the tcgen05 kernel for BF16/FP16, the FMA kernel
+ * for FP64/FP32; input packing excluded); mrhs_op_kernel_time returns the
+ * number of such launches for precision `prec` and their summed device time
+ * in ms, then clears the record (it synchronises on the last event).
+ * mrhs_launch_count returns the number of kernels this library has launched
+ * in the process so far. */
+int mrhs_op_kernel_timing(mrhs_op op, int32_t enable);
+int mrhs_op_kernel_time(mrhs_op op, int32_t prec, int64_t* launches, double* ms);
+int64_t mrhs_launch_count(void);
 
 /* Thread-local message describing the last error ("" if none). */
 const char* mrhs_last_error(void);

@@ -54,32 +54,44 @@ def generate_half(L, nb, npts, seed, procs):
     shape = (V, len(points), nb, nb)
     nbytes = int(np.prod(shape)) * 16
     shm = shared_memory.SharedMemory(create=True, size=nbytes)
-    try:
-        chunk = max(1, V // (procs * 8))
-        jobs = [(shm.name, shape, L, nb, npts, seed, points, s, min(V, s + chunk))
-                for s in range(0, V, chunk)]
-        if procs > 1:
-            with mp.get_context("spawn").Pool(procs) as pool:
-                for _ in pool.imap_unordered(_gen_chunk, jobs):
-                    pass
-        else:
-            for j in jobs:
-                _gen_chunk(j)
-        out = np.ndarray(shape, dtype=np.complex128, buffer=shm.buf).copy()
-    finally:
+    chunk = max(1, V // (procs * 8))
+    jobs = [(shm.name, shape, L, nb, npts, seed, points, s, min(V, s + chunk))
+            for s in range(0, V, chunk)]
+    if procs > 1:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            for _ in pool.imap_unordered(_gen_chunk, jobs):
+                pass
+    else:
+        for j in jobs:
+            _gen_chunk(j)
+    # no copy: the largest lattice fills half of the host memory on its own;
+    # the caller releases the block with release_half()
+    out = np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+    _LIVE[id(out)] = shm
+    return out, disp[pos]
+
+
+_LIVE = {}
+
+
+def release_half(arr):
+    shm = _LIVE.pop(id(arr), None)
+    del arr
+    if shm is not None:
         shm.close()
         shm.unlink()
-    return out, disp[pos]
 
 
 def gershgorin_radius(Ahalf):
     """max_x,a sum_b |row| over all blocks of a row (each hop block appears
     once as A_p(x) and once as a conjugate-transposed partner in some row;
     the bound uses 2x the positive blocks' row sums, an upper bound)."""
-    self_rows = np.sum(np.abs(Ahalf[:, 0]), axis=-1)
-    hop_rows = np.sum(np.abs(Ahalf[:, 1:]), axis=(1, 3))
-    hop_cols = np.sum(np.abs(Ahalf[:, 1:]), axis=(1, 2))
-    return float(np.max(self_rows + hop_rows + hop_cols))
+    best = 0.0
+    for s0 in range(0, Ahalf.shape[0], 1024):     # site chunks: bounded temporaries
+        blk = np.abs(Ahalf[s0:s0 + 1024])
+        rows = blk[:, 0].sum(axis=-1) + blk[:, 1:].sum(axis=(1, 3)) + blk[:, 1:].sum(axis=(1, 2))
+        best = max(best, float(rows.max()))
+    return best
 
 
 def estimate(w, steps, procs):
@@ -109,6 +121,8 @@ def estimate(w, steps, procs):
                shift=c, lambda_min=lmin + c, lambda_max=lmax + c,
                gershgorin_radius_H0=gershgorin_radius(Ahalf),
                seconds=round(time.time() - t0, 1))
+    op = None
+    release_half(Ahalf)
     return rec
 
 

@@ -17,6 +17,11 @@ __all__ = ["CoarseOp", "block_inner", "block_axpy", "herm_factor", "MrhsError", 
            "SOLVE_FP64", "SOLVE_MIXED", "device_error", "version"]
 
 
+def launch_count():
+    """Kernels launched by the library in this process so far."""
+    return int(_lib.lib().mrhs_launch_count())
+
+
 def version():
     return _lib.lib().mrhs_version().decode()
 
@@ -88,6 +93,24 @@ class CoarseOp:
         """Y = H^dagger X in precision `prec`."""
         l = _lib.lib()
         return self._apply(lambda *a: _lib.check(l.coarse_op_apply_dag(*a)), X, prec, out)
+
+    def lambda_max(self, prec="fp32", iters=40):
+        """Power-method estimate of the largest eigenvalue (cached on the op)."""
+        lam = ctypes.c_double()
+        _lib.check(_lib.lib().mrhs_op_lambda_max(self._h, PREC[prec], int(iters),
+                                                 ctypes.byref(lam), _lib.stream_ptr()))
+        return float(lam.value)
+
+    def kernel_timing(self, enable=True):
+        """Record CUDA events around every main operator kernel of this op."""
+        _lib.check(_lib.lib().mrhs_op_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self, prec):
+        """(launches, summed ms) of the recorded main-kernel launches; clears."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        _lib.check(_lib.lib().mrhs_op_kernel_time(self._h, PREC[prec], ctypes.byref(n),
+                                                  ctypes.byref(ms)))
+        return int(n.value), float(ms.value)
 
     def cheby(self, X, lo, hi, order, prec="fp32", out=None):
         """P = p(H) X, p the Chebyshev interpolant of 1/x on [lo, hi]."""

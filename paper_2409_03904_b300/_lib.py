@@ -67,6 +67,10 @@ SIGNATURES = {
     "mrhs_last_error": [],
     "mrhs_version": [],
     "mrhs_device_error": [],
+    "mrhs_op_kernel_timing": [P, I32],
+    "mrhs_op_kernel_time": [P, I32, P, P],
+    "mrhs_launch_count": [],
+    "mrhs_op_lambda_max": [P, I32, I32, P, P],
 }
 
 
@@ -84,6 +88,7 @@ def lib():
         l.mrhs_last_error.restype = ctypes.c_char_p
         l.mrhs_version.restype = ctypes.c_char_p
         l.mrhs_solve_params_default.restype = None
+        l.mrhs_launch_count.restype = ctypes.c_int64
         _lib = l
     return _lib
 

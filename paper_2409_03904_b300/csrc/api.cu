@@ -1,5 +1,6 @@
 // C ABI entry points of libmrhs: argument checks, operator construction and
 // dispatch to the kernels (see include/mrhs.h for the contract).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -15,6 +16,23 @@ void set_error(const std::string& msg) { t_last_error = msg; }
 int fail(int code, const std::string& msg) {
   set_error(msg);
   return code;
+}
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void timer_mark(mrhs_op_s* op, int prec, cudaStream_t s) {
+  KernelTimer& t = op->timer[prec];
+  if (!t.on) return;
+  if (t.used >= t.ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    t.ev.push_back(e);
+  }
+  cudaEventRecord(t.ev[t.used++], s);
 }
 
 int num_sms() {
@@ -154,8 +172,8 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   }
   {
     dim3 grid((unsigned)((V + 255) / 256), (unsigned)npts);
-    k_neighbours<<<grid, 256, 0, s>>>(op->nbr_fwd, op->nbr_bwd, V, npts, L[0], L[1], L[2], L[3],
-                                      d_disp);
+    { k_neighbours<<<grid, 256, 0, s>>>(op->nbr_fwd, op->nbr_bwd, V, npts, L[0], L[1], L[2], L[3],
+                                      d_disp); ::mrhs::count_launch(); }
   }
   if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)) {
     if (cudaMalloc(&op->a64, sizeof(double2) * nA) != cudaSuccess) {
@@ -171,7 +189,7 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
       cudaFree(d_disp);
       return bail(fail(MRHS_ERR_NO_MEMORY, "FP32 coefficients"));
     }
-    k_to_c64<<<num_sms() * 8, 256, 0, s>>>((const double2*)A, op->a32, (int64_t)nA);
+    { k_to_c64<<<num_sms() * 8, 256, 0, s>>>((const double2*)A, op->a32, (int64_t)nA); ::mrhs::count_launch(); }
   }
   for (int prec = MRHS_PREC_BF16; prec <= MRHS_PREC_FP16; ++prec)
     if (prec_mask & MRHS_PREC_BIT(prec)) {
@@ -189,8 +207,48 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   return MRHS_OK;
 }
 
+int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, void* stream) {
+  MRHS_TRY(check_op(op));
+  MRHS_TRY(check_prec(op, prec));
+  if (!lam || iters < 1) return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_lambda_max: arguments");
+  MRHS_TRY(lambda_max(op, prec, iters, (cudaStream_t)stream, lam));
+  op->lam_max[prec] = *lam;
+  return MRHS_OK;
+}
+
+int64_t mrhs_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int mrhs_op_kernel_timing(mrhs_op op, int32_t enable) {
+  if (!op) return fail(MRHS_ERR_INVALID_ARG, "null operator");
+  for (auto& t : op->timer) {
+    t.on = enable != 0;
+    t.used = 0;
+  }
+  return MRHS_OK;
+}
+
+int mrhs_op_kernel_time(mrhs_op op, int32_t prec, int64_t* launches, double* ms) {
+  if (!op || !launches || !ms || prec < 0 || prec > 3)
+    return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_kernel_time: arguments");
+  KernelTimer& t = op->timer[prec];
+  double total = 0.0;
+  const size_t pairs = t.used / 2;
+  if (pairs) MRHS_CUDA_TRY(cudaEventSynchronize(t.ev[2 * pairs - 1]));
+  for (size_t i = 0; i < pairs; ++i) {
+    float v = 0.f;
+    MRHS_CUDA_TRY(cudaEventElapsedTime(&v, t.ev[2 * i], t.ev[2 * i + 1]));
+    total += v;
+  }
+  *launches = (int64_t)pairs;
+  *ms = total;
+  t.used = 0;
+  return MRHS_OK;
+}
+
 int mrhs_op_destroy(mrhs_op op) {
   if (!op) return MRHS_OK;
+  for (auto& t : op->timer)
+    for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
   cudaFree(op->nbr_fwd);
   cudaFree(op->nbr_bwd);
   cudaFree(op->a64);
@@ -332,7 +390,7 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->maxiter = 5000;
   p->mode = mode;
   p->precond = mode == MRHS_SOLVE_MIXED ? 1 : 0;
-  p->precond_prec = MRHS_PREC_BF16;
+  p->precond_prec = MRHS_PREC_FP16;
   p->cheb_order = 16;
   p->cheb_lo = 0.0;
   p->cheb_hi = 0.0;

@@ -173,15 +173,19 @@ int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry,
   }
   if (dtype == MRHS_C128) {
     const size_t smem = sizeof(double2) * kTile * (rx + ry);
-    k_gram_partial<double2><<<nblk, kThreads, smem, s>>>((const double2*)X, (const double2*)Y,
-                                                          part, N, rx, ry, per);
+    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<double2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    { k_gram_partial<double2><<<nblk, kThreads, smem, s>>>((const double2*)X, (const double2*)Y,
+                                                          part, N, rx, ry, per); ::mrhs::count_launch(); }
   } else {
     const size_t smem = sizeof(float2) * kTile * (rx + ry);
-    k_gram_partial<float2><<<nblk, kThreads, smem, s>>>((const float2*)X, (const float2*)Y, part,
-                                                         N, rx, ry, per);
+    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<float2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    { k_gram_partial<float2><<<nblk, kThreads, smem, s>>>((const float2*)X, (const float2*)Y, part,
+                                                         N, rx, ry, per); ::mrhs::count_launch(); }
   }
   MRHS_CUDA_TRY(cudaGetLastError());
-  k_gram_final<<<(ne + 127) / 128, 128, 0, s>>>(part, G, nblk, ne);
+  { k_gram_final<<<(ne + 127) / 128, 128, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }
@@ -206,12 +210,12 @@ int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int r
     const size_t smem = sizeof(double2) * ((size_t)rin * rout + (size_t)kTile * rin);
     MRHS_CUDA_TRY(cudaFuncSetAttribute(k_axpy<double2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_axpy<double2><<<(unsigned)grid, kThreads, smem, s>>>((double2*)Y, (const double2*)X, M, beta,
-                                                            N, rin, rout);
+    { k_axpy<double2><<<(unsigned)grid, kThreads, smem, s>>>((double2*)Y, (const double2*)X, M, beta,
+                                                            N, rin, rout); ::mrhs::count_launch(); }
   } else {
     const size_t smem = sizeof(float2) * ((size_t)rin * rout + (size_t)kTile * rin);
-    k_axpy<float2><<<(unsigned)grid, kThreads, smem, s>>>((float2*)Y, (const float2*)X, M, beta, N,
-                                                          rin, rout);
+    { k_axpy<float2><<<(unsigned)grid, kThreads, smem, s>>>((float2*)Y, (const float2*)X, M, beta, N,
+                                                          rin, rout); ::mrhs::count_launch(); }
   }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "mrhs.h"
 
@@ -59,6 +60,14 @@ struct TcImage {             // tensor-core packed coefficients (BF16/FP16)
   size_t bytes = 0;
 };
 
+// CUDA-event timing of an operator's main kernel, one (start, stop) pair per
+// launch while enabled; read and cleared by mrhs_op_kernel_time.
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+};
+
 struct Workspace {           // grow-only device scratch
   void* ptr = nullptr;
   size_t bytes = 0;
@@ -85,12 +94,17 @@ struct mrhs_op_s {
   mrhs::Workspace ws_cheb;      // Chebyshev recurrence vectors
   mrhs::Workspace ws_small;     // column scales etc.
   mrhs::Workspace ws_solve;     // block CG vectors and state
+  mrhs::KernelTimer timer[4];   // per precision
+  double lam_max[4] = {0, 0, 0, 0};  // cached power-method estimates
 };
 
 namespace mrhs {
 
+void count_launch();
+void timer_mark(mrhs_op_s* op, int prec, cudaStream_t s);   // call before and after
+
 // op_simt.cu
-int simt_apply(const mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
+int simt_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
                cudaStream_t s);
 // op_tc.cu
 int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s);
@@ -115,6 +129,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
           mrhs_solve_info* info, cudaStream_t s);
 int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* X, void* P,
           int R, cudaStream_t s);
+int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam);
 
 // generic apply dispatch (api.cu)
 int op_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,

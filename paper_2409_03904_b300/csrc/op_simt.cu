@@ -81,7 +81,7 @@ int launch(const C* A, const C* X, C* Y, const int32_t* nbr, int64_t V, int nb, 
   auto kern = k_op_simt<C, OPT>;
   MRHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t grid = V < 1048576 ? V : 1048576;
-  kern<<<(unsigned)grid, threads, smem, s>>>(A, X, Y, nbr, V, nb, npts, R, dag);
+  { kern<<<(unsigned)grid, threads, smem, s>>>(A, X, Y, nbr, V, nb, npts, R, dag); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }
@@ -104,16 +104,20 @@ int dispatch(const C* A, const C* X, C* Y, const int32_t* nbr, int64_t V, int nb
 
 }  // namespace
 
-int simt_apply(const mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
+int simt_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
                cudaStream_t s) {
   const int32_t* nbr = dag ? op->nbr_bwd : op->nbr_fwd;
+  int st = MRHS_ERR_UNSUPPORTED;
+  timer_mark(op, prec, s);
   if (prec == MRHS_PREC_FP64)
-    return dispatch<double2>(op->a64, (const double2*)X, (double2*)Y, nbr, op->V, op->nb, op->npts,
-                             nrhs, dag ? 1 : 0, s);
-  if (prec == MRHS_PREC_FP32)
-    return dispatch<float2>(op->a32, (const float2*)X, (float2*)Y, nbr, op->V, op->nb, op->npts,
-                            nrhs, dag ? 1 : 0, s);
-  return fail(MRHS_ERR_UNSUPPORTED, "simt apply: precision");
+    st = dispatch<double2>(op->a64, (const double2*)X, (double2*)Y, nbr, op->V, op->nb, op->npts,
+                           nrhs, dag ? 1 : 0, s);
+  else if (prec == MRHS_PREC_FP32)
+    st = dispatch<float2>(op->a32, (const float2*)X, (float2*)Y, nbr, op->V, op->nb, op->npts,
+                          nrhs, dag ? 1 : 0, s);
+  timer_mark(op, prec, s);
+  if (st == MRHS_ERR_UNSUPPORTED) return fail(st, "simt apply: precision");
+  return st;
 }
 
 }  // namespace mrhs

@@ -414,13 +414,13 @@ int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s
     return fail(MRHS_ERR_NO_MEMORY, "tensor-core coefficient image");
   }
   if (prec == MRHS_PREC_BF16)
-    k_pack_coef<true><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
+    { k_pack_coef<true><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
                                                      op->nbr_bwd, op->V, op->npts, op->nb, g,
-                                                     dag ? 1 : 0);
+                                                     dag ? 1 : 0); ::mrhs::count_launch(); }
   else
-    k_pack_coef<false><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale,
+    { k_pack_coef<false><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale,
                                                       img.diag, op->nbr_bwd, op->V, op->npts,
-                                                      op->nb, g, dag ? 1 : 0);
+                                                      op->nb, g, dag ? 1 : 0); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }
@@ -444,30 +444,32 @@ int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs
   float* sigma = (float*)(colmax + MRHS_MAX_RHS);
   const int sms = num_sms();
   MRHS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned) * MRHS_MAX_RHS, s));
-  k_colmax<<<sms * 4, 256, 0, s>>>((const float2*)X, op->V * op->nb, nrhs, colmax);
-  k_colscale<<<1, 64, 0, s>>>(colmax, sigma, nrhs);
+  { k_colmax<<<sms * 4, 256, 0, s>>>((const float2*)X, op->V * op->nb, nrhs, colmax); ::mrhs::count_launch(); }
+  { k_colscale<<<1, 64, 0, s>>>(colmax, sigma, nrhs); ::mrhs::count_launch(); }
   if (prec == MRHS_PREC_BF16)
-    k_pack_xb<true><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g);
+    { k_pack_xb<true><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
   else
-    k_pack_xb<false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g);
+    { k_pack_xb<false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   size_t smem = 0;
   const int nst = tc_stages(g, &smem);
   const int32_t* nbr = dag ? op->nbr_bwd : op->nbr_fwd;
   const int64_t grid = op->V < sms ? op->V : sms;
+  timer_mark(op, prec, s);
   if (prec == MRHS_PREC_BF16) {
     MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_op_tc<true><<<(unsigned)grid, kThreadsTc, smem, s>>>(
+    { k_op_tc<true><<<(unsigned)grid, kThreadsTc, smem, s>>>(
         (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float2*)X, (float2*)Y,
-        nbr, op->V, op->npts, g, nst);
+        nbr, op->V, op->npts, g, nst); ::mrhs::count_launch(); }
   } else {
     MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_op_tc<false><<<(unsigned)grid, kThreadsTc, smem, s>>>(
+    { k_op_tc<false><<<(unsigned)grid, kThreadsTc, smem, s>>>(
         (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float2*)X, (float2*)Y,
-        nbr, op->V, op->npts, g, nst);
+        nbr, op->V, op->npts, g, nst); ::mrhs::count_launch(); }
   }
+  timer_mark(op, prec, s);
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }

@@ -37,7 +37,7 @@ int factor(const double2* G, double2* S, double2* W, int32_t* rank, int r, doubl
   const size_t smem = factor_smem_bytes(r);
   MRHS_CUDA_TRY(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-  k_factor<<<1, 256, smem, s>>>(G, S, W, rank, r, tau);
+  { k_factor<<<1, 256, smem, s>>>(G, S, W, rank, r, tau); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }

@@ -315,6 +315,32 @@ __global__ void k_small_S(Small* st, int R, double tau, int precond) {
   }
 }
 
+// deterministic start vector in [-1, 1] (an integer hash of the index)
+template <typename C>
+__global__ void k_init_vec(C* v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    C c;
+    c.x = (typename real_of<C>::type)((double)(h & 0xFFFFFF) / 8388608.0 - 1.0);
+    c.y = (typename real_of<C>::type)((double)((h >> 24) & 0xFFFFFF) / 8388608.0 - 1.0);
+    v[i] = c;
+  }
+}
+template <typename C>
+__global__ void k_scale_vec(C* out, const C* in, double f, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    C c = in[i];
+    c.x = (typename real_of<C>::type)(c.x * f);
+    c.y = (typename real_of<C>::type)(c.y * f);
+    out[i] = c;
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)num_sms() * 16;
@@ -360,8 +386,8 @@ struct Ctx {
     if (per < 1) per = 1;
     nblk = (int)((N + per - 1) / per);
     if (nblk < 1) nblk = 1;
-    k_colnorm_partial<C><<<nblk, kThreads, 0, s>>>(X, npart, N, R, per);
-    k_colnorm_final<<<1, 64, 0, s>>>(npart, out, nblk, R);
+    { k_colnorm_partial<C><<<nblk, kThreads, 0, s>>>(X, npart, N, R, per); ::mrhs::count_launch(); }
+    { k_colnorm_final<<<1, 64, 0, s>>>(npart, out, nblk, R); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaGetLastError());
     return MRHS_OK;
   }
@@ -369,13 +395,13 @@ struct Ctx {
     const size_t smem = factor_smem_bytes(R);
     if (which == 0) {
       MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_small_start<<<1, 256, smem, s>>>(st, R, tau);
+      { k_small_start<<<1, 256, smem, s>>>(st, R, tau); ::mrhs::count_launch(); }
     } else if (which == 1) {
       MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_small_M<<<1, 256, smem, s>>>(st, R, tau);
+      { k_small_M<<<1, 256, smem, s>>>(st, R, tau); ::mrhs::count_launch(); }
     } else {
       MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_small_S<<<1, 256, smem, s>>>(st, R, tau, precond);
+      { k_small_S<<<1, 256, smem, s>>>(st, R, tau, precond); ::mrhs::count_launch(); }
     }
     MRHS_CUDA_TRY(cudaGetLastError());
     return MRHS_OK;
@@ -387,7 +413,7 @@ struct Ctx {
     int64_t grid = (N + kTile - 1) / kTile;
     const int64_t cap = (int64_t)num_sms() * 16;
     if (grid > cap) grid = cap;
-    k_rotate<C><<<(unsigned)grid, kThreads, smem, s>>>(P1, P2, D, st->W, st->S, N, R);
+    { k_rotate<C><<<(unsigned)grid, kThreads, smem, s>>>(P1, P2, D, st->W, st->S, N, R); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaGetLastError());
     return MRHS_OK;
   }
@@ -418,12 +444,12 @@ int cheb_run(Ctx& cx, int prec, double lo, double hi, int order, const C* X, C* 
   const int64_t n = cx.N * cx.R;
   const int g = grid_for(n);
   if (order == 0) {
-    k_cheb_first<C><<<g, kThreads, 0, cx.s>>>(T1, P, X, X, 0.0, 0.0, c[0], 0.0, n);
+    { k_cheb_first<C><<<g, kThreads, 0, cx.s>>>(T1, P, X, X, 0.0, 0.0, c[0], 0.0, n); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaGetLastError());
     return MRHS_OK;
   }
   MRHS_TRY(cx.apply(prec, X, W));
-  k_cheb_first<C><<<g, kThreads, 0, cx.s>>>(T1, P, W, X, a, b, c[0], c[1], n);
+  { k_cheb_first<C><<<g, kThreads, 0, cx.s>>>(T1, P, W, X, a, b, c[0], c[1], n); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   const C* Tprev = X;   // T_{j-1}
   C* Tcur = T1;         // T_j
@@ -431,7 +457,7 @@ int cheb_run(Ctx& cx, int prec, double lo, double hi, int order, const C* X, C* 
     MRHS_TRY(cx.apply(prec, Tcur, W));
     // T_{j+1} goes over T_{j-1}, except that the input X is never written
     C* dst = (Tprev == X) ? T2 : const_cast<C*>(Tprev);
-    k_cheb_step<C><<<g, kThreads, 0, cx.s>>>(dst, P, W, Tcur, Tprev, a, b, c[j], n);
+    { k_cheb_step<C><<<g, kThreads, 0, cx.s>>>(dst, P, W, Tcur, Tprev, a, b, c[j], n); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaGetLastError());
     Tprev = Tcur;
     Tcur = dst;
@@ -474,7 +500,7 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
   MRHS_CUDA_TRY(cudaMemsetAsync(&cx.st->flag, 0, sizeof(int), cx.s));
   // r0 = F - H E
   MRHS_TRY(cx.apply(prec, E, z));
-  k_sub<C><<<g, kThreads, 0, cx.s>>>(q, F, z, n);
+  { k_sub<C><<<g, kThreads, 0, cx.s>>>(q, F, z, n); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   if (precond) {
     MRHS_TRY(cheb_run<C>(cx, pprec, lo, hi, order, q, Q, b.cw, b.c1, b.c2));   // Z0 = M^-1 r0
@@ -487,7 +513,10 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
   MRHS_CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(C) * n, cx.s));
   MRHS_CUDA_TRY(cudaMemsetAsync(cx.st->S, 0, sizeof(double2) * 64 * 64, cx.s));
   MRHS_TRY(cx.rotate<C>(q, precond ? Q : nullptr, D));
-  int it = 0, flag = 0;
+  int it = 0, flag = 0, stalled = 0;
+  double best = 1e300;
+  std::vector<double> est(cx.R);
+  const int stall_checks = check_every > 0 ? (32 + check_every - 1) / check_every : 0;
   for (it = 1; it <= maxiter; ++it) {
     MRHS_TRY(cx.apply(prec, D, z));                                            // z = H D
     if (precond) MRHS_TRY(cheb_run<C>(cx, pprec, lo, hi, order, z, b.Zz, b.cw, b.c1, b.c2));
@@ -506,8 +535,24 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
     MRHS_TRY(cx.rotate<C>(q, precond ? Q : nullptr, D));                       // q, Q, D
     if (it % check_every == 0 || it == maxiter) {
       MRHS_CUDA_TRY(cudaMemcpyAsync(&flag, &cx.st->flag, sizeof(int), cudaMemcpyDeviceToHost, cx.s));
+      MRHS_CUDA_TRY(cudaMemcpyAsync(est.data(), cx.st->est, sizeof(double) * cx.R,
+                                    cudaMemcpyDeviceToHost, cx.s));
       MRHS_CUDA_TRY(cudaStreamSynchronize(cx.s));
       if (flag & (1 | 4)) break;
+      // stagnation: the worst column's distance to its target has not shrunk
+      // by 30% over `stall_checks` reads (a low-precision preconditioner is
+      // not exactly linear, so the recurrences can plateau above the target;
+      // the caller then restarts from the true residual)
+      double worst = 0.0;
+      for (int j = 0; j < cx.R; ++j)
+        if (target_host[j] > 0.0) worst = std::fmax(worst, est[j] / target_host[j]);
+      if (worst < 0.7 * best) {
+        best = worst;
+        stalled = 0;
+      } else if (stall_checks > 0 && ++stalled >= stall_checks) {
+        flag |= 8;
+        break;
+      }
     }
   }
   if (it > maxiter) it = maxiter;
@@ -541,7 +586,50 @@ struct SolveBufs {
   }
 };
 
+template <typename C>
+int power_run(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
+  const int64_t n = op->V * op->nb;
+  const size_t vb = (sizeof(C) * n + 255) / 256 * 256;
+  const size_t part = gram_workspace_bytes(n, 1, 1);
+  MRHS_TRY(op->ws_small.ensure(2 * vb + part + 256));
+  char* base = (char*)op->ws_small.ptr;
+  C* v = (C*)base;
+  C* w = (C*)(base + vb);
+  double2* G = (double2*)(base + 2 * vb);           // two 1 x 1 Grams
+  double2* gp = G + 2;
+  const int g = grid_for(n);
+  const int dt = sizeof(C) == 16 ? MRHS_C128 : MRHS_C64;
+  { k_init_vec<C><<<g, kThreads, 0, s>>>(v, n); ::mrhs::count_launch(); }
+  double2 h[2];
+  MRHS_TRY(gram_ws(v, v, G, n, 1, 1, dt, gp, s));
+  MRHS_CUDA_TRY(cudaMemcpyAsync(h, G, sizeof(double2), cudaMemcpyDeviceToHost, s));
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  { k_scale_vec<C><<<g, kThreads, 0, s>>>(v, v, 1.0 / std::sqrt(h[0].x), n); ::mrhs::count_launch(); }
+  double est = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    MRHS_TRY(op_apply(op, prec, false, v, w, 1, s));
+    MRHS_TRY(gram_ws(v, w, G, n, 1, 1, dt, gp, s));       // v^dag H v (|v| = 1)
+    MRHS_TRY(gram_ws(w, w, G + 1, n, 1, 1, dt, gp, s));   // |H v|^2
+    MRHS_CUDA_TRY(cudaMemcpyAsync(h, G, 2 * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    est = h[0].x;
+    if (!(h[1].x > 0.0) || !std::isfinite(h[1].x)) break;
+    { k_scale_vec<C><<<g, kThreads, 0, s>>>(v, w, 1.0 / std::sqrt(h[1].x), n); ::mrhs::count_launch(); }
+  }
+  MRHS_CUDA_TRY(cudaGetLastError());
+  *lam = est;
+  return MRHS_OK;
+}
+
 }  // namespace
+
+// Largest-eigenvalue estimate by the power method (Sec. 2.3 obtains the
+// Chebyshev upper bound "with a cheap application of the power method"):
+// Rayleigh quotient of H^k v0, one right-hand side, operator in `prec`.
+int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
+  if (prec == MRHS_PREC_FP64) return power_run<double2>(op, prec, iters, s, lam);
+  return power_run<float2>(op, prec, iters, s, lam);
+}
 
 int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
           mrhs_solve_info* info, cudaStream_t s) {
@@ -564,12 +652,18 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
   MRHS_CUDA_TRY(cudaMemsetAsync(cx.st, 0, sizeof(Small), s));
 
   double lo = p.cheb_lo, hi = p.cheb_hi;
-  if (p.precond && hi <= 0.0) return fail(MRHS_ERR_INVALID_ARG, "cheb_hi must be given (> 0)");
+  if (p.precond && hi <= 0.0) {
+    // cached power-method estimate in the preconditioner's precision, with
+    // a margin: p(x) must not see eigenvalues above hi
+    double& cached = op->lam_max[p.precond_prec];
+    if (!(cached > 0.0)) MRHS_TRY(lambda_max(op, p.precond_prec, 40, s, &cached));
+    hi = 1.08 * cached;
+  }
   if (p.precond && lo <= 0.0) lo = hi / 400.0;
   if (p.precond && !(lo < hi)) return fail(MRHS_ERR_INVALID_ARG, "cheb_lo must be < cheb_hi");
 
   MRHS_TRY(cx.colnorms<double2>(B, sb.bnorm_d));
-  k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, sb.bnorm_d, cx.N, R);
+  { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, sb.bnorm_d, cx.N, R); ::mrhs::count_launch(); }
   std::vector<double> bnorm(R), rnorm(R), target(R);
   MRHS_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), sb.bnorm_d, sizeof(double) * R,
                                 cudaMemcpyDeviceToHost, s));
@@ -578,7 +672,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
 
   auto true_residual = [&]() -> int {   // r64 = B - H X (FP64), rnorm
     MRHS_TRY(cx.apply(MRHS_PREC_FP64, X, sb.r64));
-    k_sub<double2><<<g, kThreads, 0, s>>>(sb.r64, B, sb.r64, n);
+    { k_sub<double2><<<g, kThreads, 0, s>>>(sb.r64, B, sb.r64, n); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaGetLastError());
     MRHS_TRY(cx.colnorms<double2>(sb.r64, sb.rnorm_d));
     MRHS_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), sb.rnorm_d, sizeof(double) * R,
@@ -595,12 +689,17 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
 
   if (!mixed) {
     for (int j = 0; j < R; ++j) target[j] = p.tol * bnorm[j];
-    int it = 0;
-    MRHS_TRY(run_bcg<double2>(cx, sb.b64, MRHS_PREC_FP64, B, X, target.data(), p.precond != 0,
-                              p.precond_prec, lo, hi, p.cheb_order, p.maxiter, every, &it, &flag));
-    total_iters = it;
-    cycles = 1;
     MRHS_TRY(true_residual());
+    cycles = 0;
+    if (!all_done()) {
+      int it = 0;
+      MRHS_TRY(run_bcg<double2>(cx, sb.b64, MRHS_PREC_FP64, B, X, target.data(), p.precond != 0,
+                                p.precond_prec, lo, hi, p.cheb_order, p.maxiter, every, &it,
+                                &flag));
+      total_iters = it;
+      cycles = 1;
+      MRHS_TRY(true_residual());
+    }
   } else {
     MRHS_TRY(true_residual());
     for (cycles = 0; cycles < p.max_cycles && !all_done() && total_iters < p.maxiter; ++cycles) {
@@ -613,7 +712,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       }
       MRHS_CUDA_TRY(cudaMemcpyAsync(sb.rho_d, rho.data(), sizeof(double) * R,
                                     cudaMemcpyHostToDevice, s));
-      k_scale_to_c64<<<g, kThreads, 0, s>>>(sb.f32, sb.r64, sb.rho_d, cx.N, R);
+      { k_scale_to_c64<<<g, kThreads, 0, s>>>(sb.f32, sb.r64, sb.rho_d, cx.N, R); ::mrhs::count_launch(); }
       MRHS_CUDA_TRY(cudaMemsetAsync(sb.e32, 0, sizeof(float2) * n, s));
       MRHS_CUDA_TRY(cudaGetLastError());
       int it = 0;
@@ -621,7 +720,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
                                p.precond != 0, p.precond_prec, lo, hi, p.cheb_order,
                                p.maxiter - total_iters, every, &it, &flag));
       total_iters += it;
-      k_update_x<<<g, kThreads, 0, s>>>(X, sb.e32, sb.rho_d, cx.N, R);
+      { k_update_x<<<g, kThreads, 0, s>>>(X, sb.e32, sb.rho_d, cx.N, R); ::mrhs::count_launch(); }
       MRHS_CUDA_TRY(cudaGetLastError());
       MRHS_TRY(true_residual());
       if (flag & 4) break;

@@ -192,10 +192,17 @@ def test_cheby_apply(mrhs, kind):
         P = op.cheby(dev(X), lo, hi, m, "fp64").cpu().numpy()
         ref = oracle_cheby(lambda V: coarse_op_apply(A, V, L, disp), X, lo, hi, m)
         assert rel_per_rhs(P, ref) <= 1e-11
-    else:
+    elif kind == "fp32":
         P = op.cheby(dev(X.astype(np.complex64)), lo, hi, m, kind).cpu().numpy()
         ref = oracle_cheby(lambda V: lowprec_apply(A, V, L, disp, kind), X, lo, hi, m)
         assert rel_per_rhs(P, ref) <= 1e-4
+    else:
+        # every step re-quantises its input to bf16, and a different FP32
+        # rounding upstream can flip a code, so the recurrence is compared with
+        # the exact polynomial at the quantisation level (2^-8 per step)
+        P = op.cheby(dev(X.astype(np.complex64)), lo, hi, m, kind).cpu().numpy()
+        ref = oracle_cheby(lambda V: coarse_op_apply(A, V, L, disp), X, lo, hi, m)
+        assert rel_per_rhs(P, ref) <= 2e-2
 
 
 def test_solve_fp64_small(mrhs):
@@ -207,7 +214,7 @@ def test_solve_fp64_small(mrhs):
     c = (ev[-1] - 1e3 * ev[0]) / (1e3 - 1)
     A = coarse_op(L, nb, npts, 77, c)
     B = vectors(L, nb, R, 78)
-    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "bf16"))
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "bf16", "fp16"))
     X, info = op.solve(dev(B), tol=1e-10, maxiter=1000)
     X = X.cpu().numpy()
     H = dense_matrix(A, L, disp)
@@ -221,10 +228,11 @@ def test_solve_fp64_small(mrhs):
     Xp, ip = op.solve(dev(B), tol=1e-10, precond=1, precond_prec="fp64", cheb_hi=1.1 * ev[-1] + c,
                       cheb_lo=0.1, cheb_order=8)
     assert max(ip["resid"]) <= 1e-10 and ip["iters"] < info["iters"]
-    Xm, im = op.solve(dev(B), mode="mixed", tol=1e-10, precond=1, precond_prec="bf16",
-                      cheb_hi=1.1 * ev[-1] + c, cheb_lo=0.2, cheb_order=8)
-    assert max(im["resid"]) <= 1e-10, im
-    assert np.linalg.norm(Xm.cpu().numpy().reshape(-1, R) - ref) <= 1e3 * 1e-9 * np.linalg.norm(ref)
+    for kind in ("fp16", "bf16", "fp32"):
+        Xm, im = op.solve(dev(B), mode="mixed", tol=1e-10, precond=1, precond_prec=kind,
+                          cheb_hi=1.1 * ev[-1] + c, cheb_lo=0.2, cheb_order=8)
+        assert max(im["resid"]) <= 1e-10, (kind, im)
+        assert np.linalg.norm(Xm.cpu().numpy().reshape(-1, R) - ref) <= 1e3 * 1e-9 * np.linalg.norm(ref)
     assert mrhs.device_error() == 0
 
 
@@ -247,7 +255,7 @@ def test_solve_edge_cases(mrhs):
     B1 = B[:, :, :1].copy()
     X1, i1 = op.solve(dev(B1), tol=1e-11)
     X2, i2 = op.solve(dev(B1), X0=X1, tol=1e-9)
-    assert i2["iters"] <= 1 and max(i2["resid"]) <= 1e-9
+    assert i2["iters"] == 0 and max(i2["resid"]) <= 1e-9
 
 
 def test_invalid_arguments(mrhs):
@@ -283,3 +291,20 @@ def test_named_workload_solve(mrhs):
     ref = np.linalg.solve(H, B.reshape(-1, w["nrhs"]))
     err = np.linalg.norm(X.cpu().numpy().reshape(-1, w["nrhs"]) - ref) / np.linalg.norm(ref)
     assert err <= w["kappa"] * w["tol"]
+
+
+def test_lambda_max_and_auto_interval(mrhs):
+    """Power method below the true maximum and within a few percent; a solve
+    with cheb_hi unset uses it (with its margin) and converges."""
+    from tests.test_oracle_ops import dense_matrix
+    L, nb, npts, R = (3, 2, 2, 2), 8, 81, 3
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 313, 18.0)
+    ev = np.linalg.eigvalsh(dense_matrix(A, L, disp))
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "fp16"))
+    for prec in ("fp64", "fp32", "fp16"):
+        lam = op.lambda_max(prec, 200)
+        assert ev[-1] * 0.97 <= lam <= ev[-1] * (1 + 1e-3), (prec, lam, ev[-1])
+    B = vectors(L, nb, R, 314)
+    X, info = op.solve(dev(B), mode="mixed", tol=1e-9, precond=1, precond_prec="fp16")
+    assert max(info["resid"]) <= 1e-9 and info["cheb_hi"] >= ev[-1]
