@@ -9,7 +9,7 @@
  *   index x = x0 + L0*(x1 + L1*(x2 + L2*x3)).
  * Stencil: npts displacements delta_p in {-1,0,1}^4 (disp[p][4], host
  *   memory), p = 0 must be the self term (0,0,0,0); at most 81 points
- *   (Sec. 2.7, "Coarse operator": the full 3^4 neighbourhood).
+ *   (Sec. 2.6, "Coarse operator": the full 3^4 neighbourhood).
  * Coefficients: complex128 A[x][p][a][b], a, b < nb (row-major nb x nb
  *   block for every site and stencil point), as (re, im) double pairs.
  * Vectors: a block of nrhs coarse vectors is stored [x][b][r] (RHS index r
@@ -62,7 +62,7 @@ enum { MRHS_C128 = 0, MRHS_C64 = 1 };
 
 typedef struct mrhs_op_s* mrhs_op;
 
-/* Create a coarse operator (Sec. 2.7: "the coarse matrix coefficients are
+/* Create a coarse operator (Sec. 2.6: "the coarse matrix coefficients are
  * stored entirely internal to this object").
  *   L      host int32[4], each >= 1
  *   nb     basis size per site, 1..64
@@ -79,7 +79,7 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts,
 /* Release the operator and its device copies (after its last use is done). */
 int mrhs_op_destroy(mrhs_op op);
 
-/* Y = H X,  Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.7, "Applying the
+/* Y = H X,  Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.6, "Applying the
  * coarse operator", the per-stencil-point batched GEMM summed over p).
  *   prec   MRHS_PREC_*; must be in the operator's prec_mask
  *   X, Y   device [V][nb][nrhs]: complex128 for FP64, complex64 otherwise;
@@ -96,7 +96,7 @@ int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_
                         void* stream);
 
 /* G = X^dagger Y, the nrhs_x x nrhs_y block inner product of block CG
- * (Fig. 2: D^dagger Z, T^dagger t, ...; Sec. 3.4's "ThinQR" Gram).
+ * (Fig. 2: D^dagger Z, T^dagger t, ...; Sec. 3.5 and Table 6, the "ThinQR" Gram).
  *   X [N][rx], Y [N][ry] of element type dtype (MRHS_C128 or MRHS_C64)
  *   G device complex128 [rx][ry] row-major (written, not accumulated)
  *   N >= 0 rows, 1 <= rx, ry <= MRHS_MAX_RHS

@@ -10,7 +10,7 @@ Every function is a plain restatement of the paper (P. Boyle, "Multiple right
 hand side multigrid for domain wall fermions with a multigrid preconditioned
 block conjugate gradient algorithm", arXiv:2409.03904), in complex128:
 
-* ``ops``      coarse operator Y(x) = sum_p A_p(x) X(x+delta_p)   (Sec. 2.7,
+* ``ops``      coarse operator Y(x) = sum_p A_p(x) X(x+delta_p)   (Sec. 2.6,
                "Applying the coarse operator"), its adjoint, the Gram product
                X^dagger Y and the block update beta Y + X M (Fig. 2).
 * ``chol``     upper Cholesky S^dagger S = G and triangular inverse (Fig. 2).

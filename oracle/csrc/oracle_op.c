@@ -3,7 +3,7 @@
  * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
  * baseline leg of the benchmark; never linked into the product library.
  *
- * Y(x) = sum_p A_p(x) X(x + delta_p)       (Sec. 2.7, "Applying the coarse
+ * Y(x) = sum_p A_p(x) X(x + delta_p)       (Sec. 2.6, "Applying the coarse
  * operator"), periodic lattice, site x = x0 + L0*(x1 + L1*(x2 + L2*x3)).
  * Layouts: A[x][p][a][b], X/Y[x][b][r], complex as (re, im) double pairs.
  *

@@ -30,7 +30,7 @@ def neighbour_table(L, disp):
 
 
 def coarse_op_apply(A, X, L, disp):
-    """Y(x) = sum_p A_p(x) X(x + delta_p)  (Sec. 2.7, "Applying the coarse
+    """Y(x) = sum_p A_p(x) X(x + delta_p)  (Sec. 2.6, "Applying the coarse
     operator": one batched GEMM per stencil point, batch = coarse volume)."""
     nbr = neighbour_table(L, disp)
     Y = np.zeros(X.shape, dtype=np.complex128)

@@ -1,6 +1,6 @@
 // Block inner products and block updates of block CG (Fig. 2), N x nrhs blocks.
 //
-// Gram G = X^dagger Y: the "ThinQR" reduction of Sec. 3.4 / Table 6 (12 x 12
+// Gram G = X^dagger Y: the "ThinQR" reduction of Sec. 3.5 and Table 6 (12 x 12
 // result, K ~ 1M).  The paper splits K into batched short GEMMs and sums the
 // partial 12 x 12 matrices by hand; here one pass over the rows does the
 // same thing in one launch: every CTA reduces a contiguous row range in

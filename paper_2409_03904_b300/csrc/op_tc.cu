@@ -1,6 +1,6 @@
 // BF16 / FP16 coarse operator on the 5th-generation tensor cores (tcgen05).
 //
-// Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.7, "Applying the coarse
+// Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.6, "Applying the coarse
 // operator"), in the quantised form: the mean real diagonal d_x of the self
 // block is carried exactly in FP32, the remainder of the site's coefficient
 // block is stored as bf16/fp16 codes times a power-of-two site scale s_x,

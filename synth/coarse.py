@@ -6,7 +6,7 @@ random draws and index bookkeeping):
 
 * lattice L = (L0, L1, L2, L3), periodic, site x = x0 + L0*(x1 + L1*(x2 + L2*x3));
 * stencil: displacement list delta_p, p = 0 the self term (9-point: self and
-  +-e_mu; 81-point: all of {-1,0,1}^4, the full neighbourhood of Sec. 2.7
+  +-e_mu; 81-point: all of {-1,0,1}^4, the full neighbourhood of Sec. 2.6
   "Coarse operator");
 * hop matrices: A_p(x) = G / sqrt(nb) with G i.i.d. standard complex normal
   for every "positive" delta_p (first non-zero component +1); the partner is

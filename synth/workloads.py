@@ -1,7 +1,7 @@
 """Named synthetic workloads (lattice, basis size, stencil, RHS count, target
 condition number, tolerance, seed).  Sizes follow the coarse problems the
 paper solves: 4^4 coarse blocks of a fine lattice, n_basis 16..64, 9- or
-81-point stencils and about a dozen right-hand sides (Sec. 2.7, Table 1,
+81-point stencils and about a dozen right-hand sides (Sec. 2.6, Table 1,
 Table 6).  Seeds are BASE_SEED + index.
 """
 from .coarse import BASE_SEED
