@@ -106,6 +106,23 @@ int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_
 int block_inner(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
                 int32_t dtype, void* stream);
 
+/* Same product as block_inner, for callers that may not allocate device
+ * memory (the paper has no counterpart: this is a deployment variant).
+ * block_inner grows a library-owned cudaMalloc workspace; this call instead
+ * keeps its partial Grams in a fixed 2 MiB array compiled into the library
+ * (held by every GPU that loads it until exit) and allocates nothing.
+ *   Arguments as block_inner; rx, ry <= 64 (larger is rejected with
+ *   MRHS_ERR_INVALID_ARG); the number of row blocks is capped so the partials
+ *   fit, so the summation order (not the result beyond rounding) may differ
+ *   from block_inner's.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the array: calls that overlap
+ * on the GPU race and give wrong results.  Each call writes every partial it
+ * reads, so nothing carries over between calls. */
+int block_inner_noalloc(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
+                        int32_t dtype, void* stream);
+
 /* Y = beta*Y + X M  (Fig. 2 block updates X + D M, Q - Z M, D S^dagger, ...)
  *   X [N][rin], Y [N][rout] of element type dtype; Y may alias X when
  *   rin == rout (the update is done row tile by row tile)

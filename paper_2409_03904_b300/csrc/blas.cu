@@ -190,6 +190,40 @@ int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry,
   return MRHS_OK;
 }
 
+// Same two kernels as gram_ws, with the number of row blocks capped so that
+// the partial Grams fit a caller-provided buffer of `max_entries` complex128
+// values (used by the entry point that must not allocate).
+int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
+                   double2* part, int64_t max_entries, cudaStream_t s) {
+  const int ne = rx * ry;
+  int nblk = gram_blocks(N);
+  if ((int64_t)nblk * ne > max_entries) nblk = (int)(max_entries / ne);
+  if (nblk < 1) return fail(MRHS_ERR_INVALID_ARG, "partial-Gram buffer too small");
+  int64_t per = (N + nblk - 1) / nblk;
+  per = ((per + kTile - 1) / kTile) * kTile;
+  if (N == 0) {
+    MRHS_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double2) * ne, s));
+    return MRHS_OK;
+  }
+  if (dtype == MRHS_C128) {
+    const size_t smem = sizeof(double2) * kTile * (rx + ry);
+    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<double2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    { k_gram_partial<double2><<<nblk, kThreads, smem, s>>>((const double2*)X, (const double2*)Y,
+                                                          part, N, rx, ry, per); ::mrhs::count_launch(); }
+  } else {
+    const size_t smem = sizeof(float2) * kTile * (rx + ry);
+    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<float2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    { k_gram_partial<float2><<<nblk, kThreads, smem, s>>>((const float2*)X, (const float2*)Y, part,
+                                                         N, rx, ry, per); ::mrhs::count_launch(); }
+  }
+  MRHS_CUDA_TRY(cudaGetLastError());
+  { k_gram_final<<<(ne + 127) / 128, 128, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
+  MRHS_CUDA_TRY(cudaGetLastError());
+  return MRHS_OK;
+}
+
 int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
          cudaStream_t s) {
   int dev = 0;

@@ -123,6 +123,8 @@ int factor(const double2* G, double2* S, double2* W, int32_t* rank, int r, doubl
 int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
             double2* part, cudaStream_t s);
 size_t gram_workspace_bytes(int64_t N, int rx, int ry);
+int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
+                   double2* part, int64_t max_entries, cudaStream_t s);
 
 // solver.cu
 int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
