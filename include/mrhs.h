@@ -230,6 +230,14 @@ int32_t mrhs_device_error(void);
  * mrhs_launch_count returns the number of kernels this library has launched
  * in the process so far. */
 int mrhs_op_kernel_timing(mrhs_op op, int32_t enable);
+
+/* Launch shape of this operator's BF16/FP16 tensor-core kernel (the knobs an
+ * autotuner searches): stencil points per pipeline stage (1..16; 0 = built-in
+ * choice of >= 16 KB of coefficients per copy), CTAs per SM (1 or 2, each
+ * with its own copy/MMA ring; default 2) and the ring depth cap (2..32).  Shapes that
+ * do not fit shared memory fall back to fewer points per stage.  Results do
+ * not depend on the shape. */
+int mrhs_op_tc_tune(mrhs_op op, int32_t pts_per_stage, int32_t ctas_per_sm, int32_t max_stages);
 int mrhs_op_kernel_time(mrhs_op op, int32_t prec, int64_t* launches, double* ms);
 int64_t mrhs_launch_count(void);
 

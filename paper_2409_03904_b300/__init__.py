@@ -101,6 +101,11 @@ class CoarseOp:
                                                  ctypes.byref(lam), _lib.stream_ptr()))
         return float(lam.value)
 
+    def tc_tune(self, pts_per_stage=0, ctas_per_sm=1, max_stages=32):
+        """Launch shape of the BF16/FP16 tensor-core kernel (0 = default)."""
+        _lib.check(_lib.lib().mrhs_op_tc_tune(self._h, int(pts_per_stage), int(ctas_per_sm),
+                                              int(max_stages)))
+
     def kernel_timing(self, enable=True):
         """Record CUDA events around every main operator kernel of this op."""
         _lib.check(_lib.lib().mrhs_op_kernel_timing(self._h, 1 if enable else 0))

@@ -72,6 +72,7 @@ SIGNATURES = {
     "mrhs_op_kernel_time": [P, I32, P, P],
     "mrhs_launch_count": [],
     "mrhs_op_lambda_max": [P, I32, I32, P, P],
+    "mrhs_op_tc_tune": [P, I32, I32, I32],
 }
 
 

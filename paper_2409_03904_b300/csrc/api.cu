@@ -216,6 +216,18 @@ int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, voi
   return MRHS_OK;
 }
 
+int mrhs_op_tc_tune(mrhs_op op, int32_t pts_per_stage, int32_t ctas_per_sm, int32_t max_stages) {
+  MRHS_TRY(check_op(op));
+  if (pts_per_stage < 0 || pts_per_stage > 16 || ctas_per_sm < 1 || ctas_per_sm > 2 ||
+      max_stages < 2 || max_stages > 32)
+    return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_tc_tune: pts 0..16, ctas 1..2, stages 2..32");
+  op->tc_tune.pps = pts_per_stage;
+  op->tc_tune.ctas_per_sm = ctas_per_sm;
+  op->tc_tune.max_stages = max_stages;
+  op->tc_set = true;
+  return MRHS_OK;
+}
+
 int64_t mrhs_launch_count(void) { return (int64_t)g_launches.load(); }
 
 int mrhs_op_kernel_timing(mrhs_op op, int32_t enable) {

@@ -68,6 +68,13 @@ struct KernelTimer {
   size_t used = 0;
 };
 
+// Launch shape of the tensor-core operator (pps <= 0: built-in default).
+struct TcTune {
+  int pps = 0;           // stencil points per pipeline stage
+  int ctas_per_sm = 1;   // CTAs per SM (each with its own ring)
+  int max_stages = 32;   // ring depth cap
+};
+
 struct Workspace {           // grow-only device scratch
   void* ptr = nullptr;
   size_t bytes = 0;
@@ -96,6 +103,8 @@ struct mrhs_op_s {
   mrhs::Workspace ws_solve;     // block CG vectors and state
   mrhs::KernelTimer timer[4];   // per precision
   double lam_max[4] = {0, 0, 0, 0};  // cached power-method estimates
+  mrhs::TcTune tc_tune;              // tensor-core launch shape
+  bool tc_set = false;               // tc_tune set explicitly
 };
 
 namespace mrhs {

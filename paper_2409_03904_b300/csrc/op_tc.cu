@@ -51,6 +51,7 @@ constexpr int kThreadsTc = 192;
 constexpr int kAccCols = 64;     // TMEM columns per accumulator
 constexpr int kTmemCols = 128;   // two accumulators
 constexpr int kM = 128;
+constexpr size_t kSmemBudget = 220 * 1024;   // dynamic shared memory per SM for the ring
 
 struct Geom {
   int nb, nbp8, K, n_mma;   // K = 2 nbp8
@@ -71,6 +72,15 @@ Geom make_geom(int nb, int R) {
   g.sbo = (uint32_t)(g.K / 8) * 128;
   return g;
 }
+
+// Stencil geometry by value in the kernel parameters, so the TMA producer
+// forms x +- delta_p with a few integer operations instead of a dependent
+// global load per tile.
+struct Stencil {
+  int32_t L[4];
+  int32_t sign;            // +1: x + delta_p (forward); -1: x - delta_p (adjoint)
+  int8_t d[MRHS_MAX_PTS][4];
+};
 
 __host__ __device__ inline uint32_t canon_off(int row, int k, int K) {
   return (uint32_t)(row >> 3) * (uint32_t)(K >> 3) * 128u + (uint32_t)(k >> 3) * 128u +
@@ -222,8 +232,8 @@ template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_op_tc(const uint8_t* __restrict__ coef, const uint8_t* __restrict__ xb,
             const float* __restrict__ sscale, const float* __restrict__ sdiag,
-            const float* __restrict__ sigma, const float2* __restrict__ X, float2* __restrict__ Y,
-            const int32_t* __restrict__ nbr, int64_t V, int npts, Geom g, int nstages) {
+            const float* __restrict__ sigma, const float* __restrict__ Xf, float* __restrict__ Yf,
+            const Stencil st, int64_t V, int npts, Geom g, int nstages, int pps) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + nstages;
@@ -231,7 +241,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   uint64_t* acc_empty = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   uint8_t* stages = smem + 1024;
-  const uint32_t stage_bytes = g.coef_bytes + g.xb_bytes;
+  // a stage holds `pps` consecutive stencil points of one site: their
+  // coefficient tiles (contiguous in HBM, one bulk copy) then their pps
+  // neighbour input tiles
+  const uint32_t stage_bytes = (uint32_t)pps * (g.coef_bytes + g.xb_bytes);
+  const uint32_t xb_off = (uint32_t)pps * g.coef_bytes;
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -266,15 +280,35 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       int64_t issued = 0;
       bool ok = true;
       for (int64_t x = blockIdx.x; x < V && ok; x += gridDim.x) {
-        for (int p = 0; p < npts; ++p) {
+        int c[4];
+        {
+          int64_t r = x;
+#pragma unroll
+          for (int mu = 0; mu < 4; ++mu) {
+            c[mu] = (int)(r % st.L[mu]);
+            r /= st.L[mu];
+          }
+        }
+        for (int p0 = 0; p0 < npts; p0 += pps) {
+          const int np = (npts - p0) < pps ? (npts - p0) : pps;
           if (!ptx::mbar_wait(&empty[s], ph ^ 1u, &s_abort)) { ok = false; break; }
-          uint8_t* st = stages + (size_t)s * stage_bytes;
-          ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
-          ptx::bulk_g2s(st, coef + ((uint64_t)x * npts + p) * g.coef_bytes, g.coef_bytes, &full[s],
-                        pol_stream);
-          const int64_t y = nbr[(int64_t)p * V + x];
-          ptx::bulk_g2s(st + g.coef_bytes, xb + (uint64_t)y * g.xb_bytes, g.xb_bytes, &full[s],
-                        pol_keep);
+          uint8_t* st_smem = stages + (size_t)s * stage_bytes;
+          ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)np * (g.coef_bytes + g.xb_bytes));
+          ptx::bulk_g2s(st_smem, coef + ((uint64_t)x * npts + p0) * g.coef_bytes,
+                        (uint32_t)np * g.coef_bytes, &full[s], pol_stream);
+          for (int i = 0; i < np; ++i) {
+            const int p = p0 + i;
+            int64_t y = 0;
+#pragma unroll
+            for (int mu = 3; mu >= 0; --mu) {
+              int v = c[mu] + st.sign * (int)st.d[p][mu];
+              v += (v < 0) ? st.L[mu] : 0;
+              v -= (v >= st.L[mu]) ? st.L[mu] : 0;
+              y = y * st.L[mu] + v;
+            }
+            ptx::bulk_g2s(st_smem + xb_off + (uint32_t)i * g.xb_bytes,
+                          xb + (uint64_t)y * g.xb_bytes, g.xb_bytes, &full[s], pol_keep);
+          }
           ++issued;
           if (++s == nstages) { s = 0; ph ^= 1u; }
         }
@@ -305,14 +339,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!ptx::mbar_wait(&acc_empty[acc], aph ^ 1u, &s_abort)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t tmem_d = tmem_base + (uint32_t)(acc * kAccCols);
-        for (int p = 0; p < npts; ++p) {
+        for (int p0 = 0; p0 < npts; p0 += pps) {
+          const int np = (npts - p0) < pps ? (npts - p0) : pps;
           if (!ptx::mbar_wait(&full[s], ph, &s_abort)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint32_t sb = ptx::smem_u32(stages + (size_t)s * stage_bytes);
-          for (int j = 0; j < nk; ++j) {
-            const uint64_t adesc = ptx::smem_desc(sb + g.coef_bytes + (uint32_t)j * 256u, 128u, g.sbo);
-            const uint64_t bdesc = ptx::smem_desc(sb + (uint32_t)j * 256u, 128u, g.sbo);
-            ptx::mma_f16(tmem_d, adesc, bdesc, idesc, (p > 0 || j > 0) ? 1u : 0u);
+          for (int i = 0; i < np; ++i) {
+            const uint32_t cb = sb + (uint32_t)i * g.coef_bytes;
+            const uint32_t ab = sb + xb_off + (uint32_t)i * g.xb_bytes;
+            for (int j = 0; j < nk; ++j) {
+              const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)j * 256u, 128u, g.sbo);
+              const uint64_t bdesc = ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, g.sbo);
+              ptx::mma_f16(tmem_d, adesc, bdesc, idesc, (p0 > 0 || i > 0 || j > 0) ? 1u : 0u);
+            }
           }
           ptx::mma_commit(&empty[s]);
           if (++s == nstages) { s = 0; ph ^= 1u; }
@@ -335,11 +374,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const int r = valid ? (m < R ? m : m - R) : 0;
     const int part = m < R ? 0 : 1;
     const float sig = valid ? sigma[r] : 0.f;
-    float* Yf = reinterpret_cast<float*>(Y);
-    const float* Xf = reinterpret_cast<const float*>(X);
     int acc = 0;
     uint32_t aph = 0;
     for (int64_t x = blockIdx.x; x < V; x += gridDim.x) {
+      // the d_x X(x) term: load it before waiting, so its latency overlaps
+      // the site's MMAs
+      float xv[kAccCols];
+      float sc = 0.f, dx = 0.f;
+      if (valid) {
+        sc = __ldg(&sscale[x]) * sig;
+        dx = __ldg(&sdiag[x]);
+#pragma unroll
+        for (int a = 0; a < kAccCols; ++a)
+          xv[a] = a < nb ? __ldg(&Xf[(((int64_t)x * nb + a) * R + r) * 2 + part]) : 0.f;
+      }
       const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort);
       if (!__all_sync(0xffffffffu, got)) {   // warp-uniform: tcgen05.ld below is .aligned
         s_abort = 1;
@@ -355,13 +403,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
       if (valid) {
-        const float sc = sscale[x] * sig;
-        const float dx = sdiag[x];
 #pragma unroll
         for (int a = 0; a < kAccCols; ++a) {
           if (a < nb) {
             const int64_t idx = (((int64_t)x * nb + a) * R + r) * 2 + part;
-            Yf[idx] = fmaf(sc, v[a], dx * Xf[idx]);
+            Yf[idx] = fmaf(sc, v[a], dx * xv[a]);
           }
         }
       }
@@ -377,18 +423,32 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   }
 }
 
-int tc_stages(const Geom& g, size_t* smem_out) {
-  const size_t stage = g.coef_bytes + g.xb_bytes;
+// Ring depth and shared memory for `pps` points per stage within `budget`
+// bytes of shared memory per CTA.
+int tc_stages(const Geom& g, int pps, size_t budget, int max_stages, size_t* smem_out) {
+  const size_t stage = (size_t)pps * (g.coef_bytes + g.xb_bytes);
   // the M = 128 operand read runs past a 2R-row input tile, and the N = n_mma
   // read past an nbp8-row coefficient tile: keep that much slack at the end
   const size_t row_bytes = (size_t)g.K * 2;
   const size_t slack = (size_t)(kM - g.rows8) * row_bytes + (size_t)(g.n_mma) * row_bytes + 1024;
-  const size_t budget = 220 * 1024;
+  if (budget < 1024 + slack + 2 * stage) return 0;
   int n = (int)((budget - 1024 - slack) / stage);
-  if (n > 16) n = 16;
+  if (n > max_stages) n = max_stages;
+  if (n > 32) n = 32;                 // barrier area: 2 * 32 + 4 words < 1024 bytes
   if (n < 2) return 0;
   *smem_out = 1024 + (size_t)n * stage + slack;
   return n;
+}
+
+TcTune default_tune(const Geom& g) {
+  TcTune t;
+  // points per stage: aim for >= 16 KB of coefficients per copy
+  t.pps = (int)((16384 + g.coef_bytes - 1) / g.coef_bytes);
+  if (t.pps > 8) t.pps = 8;
+  if (t.pps < 1) t.pps = 1;
+  t.ctas_per_sm = 2;    // two independent copy/MMA rings per SM
+  t.max_stages = 32;
+  return t;
 }
 
 }  // namespace
@@ -396,7 +456,7 @@ int tc_stages(const Geom& g, size_t* smem_out) {
 int tc_supported(const mrhs_op_s* op, int nrhs) {
   if (op->nb > 64 || nrhs > 64 || nrhs < 1) return 0;
   size_t smem;
-  return tc_stages(make_geom(op->nb, nrhs), &smem) > 0;
+  return tc_stages(make_geom(op->nb, nrhs), 1, kSmemBudget, 32, &smem) > 0;
 }
 
 int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s) {
@@ -451,23 +511,44 @@ int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs
   else
     { k_pack_xb<false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
+  TcTune t = default_tune(g);
+  if (op->tc_tune.pps > 0) t.pps = op->tc_tune.pps;
+  if (op->tc_set) {
+    t.ctas_per_sm = op->tc_tune.ctas_per_sm;
+    t.max_stages = op->tc_tune.max_stages;
+  }
   size_t smem = 0;
-  const int nst = tc_stages(g, &smem);
-  const int32_t* nbr = dag ? op->nbr_bwd : op->nbr_fwd;
-  const int64_t grid = op->V < sms ? op->V : sms;
+  int nst = 0;
+  for (;;) {   // fall back to fewer points per stage if the ring does not fit
+    nst = tc_stages(g, t.pps, kSmemBudget / (size_t)t.ctas_per_sm, t.max_stages, &smem);
+    if (nst >= 2 || t.pps == 1) break;
+    t.pps = (t.pps + 1) / 2;
+  }
+  if (nst < 2 && t.ctas_per_sm > 1) {
+    t.ctas_per_sm = 1;
+    nst = tc_stages(g, t.pps, kSmemBudget, t.max_stages, &smem);
+  }
+  if (nst < 2) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core ring does not fit");
+  Stencil stn;
+  for (int mu = 0; mu < 4; ++mu) stn.L[mu] = op->L[mu];
+  stn.sign = dag ? -1 : 1;
+  for (int p = 0; p < op->npts; ++p)
+    for (int mu = 0; mu < 4; ++mu) stn.d[p][mu] = op->disp[p][mu];
+  const int64_t cap = (int64_t)sms * t.ctas_per_sm;
+  const int64_t grid = op->V < cap ? op->V : cap;
   timer_mark(op, prec, s);
   if (prec == MRHS_PREC_BF16) {
     MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     { k_op_tc<true><<<(unsigned)grid, kThreadsTc, smem, s>>>(
-        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float2*)X, (float2*)Y,
-        nbr, op->V, op->npts, g, nst); ::mrhs::count_launch(); }
+        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float*)X, (float*)Y,
+        stn, op->V, op->npts, g, nst, t.pps); ::mrhs::count_launch(); }
   } else {
     MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     { k_op_tc<false><<<(unsigned)grid, kThreadsTc, smem, s>>>(
-        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float2*)X, (float2*)Y,
-        nbr, op->V, op->npts, g, nst); ::mrhs::count_launch(); }
+        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float*)X, (float*)Y,
+        stn, op->V, op->npts, g, nst, t.pps); ::mrhs::count_launch(); }
   }
   timer_mark(op, prec, s);
   MRHS_CUDA_TRY(cudaGetLastError());
