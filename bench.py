@@ -42,10 +42,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--precond", default="fp16", choices=["fp16", "bf16", "fp32"])
-    ap.add_argument("--cheb-order", type=int, default=16)
+    ap.add_argument("--precond", default="fp16x", choices=["fp16x", "fp16", "bf16", "fp32", "tc32"])
+    ap.add_argument("--krylov", default="tc32", choices=["tc32", "fp32"])
+    ap.add_argument("--cheb-order", type=int, default=8)
     ap.add_argument("--cheb-ratio", type=float, default=400.0, help="hi / lo")
-    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--fp64-iters", type=int, default=3,
                     help="FP64 block-CG iterations timed for the plain-FP64 comparison")
     ap.add_argument("--fp64-full", action="store_true",
@@ -126,9 +127,9 @@ def op_bytes(w, R, prec):
     """Algorithmic bytes of one application: coefficients once, input and
     output vectors once (neighbour re-reads not counted)."""
     V = int(np.prod(w["L"]))
-    coef = {"fp64": 16, "fp32": 8, "bf16": 4, "fp16": 4}[prec]
+    coef = {"fp64": 16, "fp32": 8, "bf16": 4, "fp16": 4, "fp16x": 4, "tc32": 8}[prec]
     vec = 16 if prec == "fp64" else 8
-    extra = 8 * V if prec in ("bf16", "fp16") else 0          # site scale + diagonal
+    extra = 8 * V if prec not in ("fp64", "fp32") else 0      # site scale + diagonal
     return w["npts"] * V * w["nb"] ** 2 * coef + extra + 2 * V * w["nb"] * R * vec
 
 
@@ -241,7 +242,8 @@ def main():
 
     t0 = time.time()
     A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
-    op = mrhs.CoarseOp(A, w["L"], disp, ("fp64", "fp32", "bf16", "fp16"))
+    precs = tuple(dict.fromkeys(("fp64", "fp32", "fp16", a.precond, a.krylov)))
+    op = mrhs.CoarseOp(A, w["L"], disp, precs)
     del A
     torch.cuda.empty_cache()
     B = sdev.vectors(w["L"], nb, R, w["seed"] + 7919 * rank, device=dev)
@@ -249,6 +251,7 @@ def main():
     lam = op.lambda_max(a.precond, 40)
     hi = 1.08 * lam
     params = dict(mode="mixed", tol=1e-8, precond=1, precond_prec=a.precond,
+                  krylov_prec=a.krylov,
                   cheb_order=a.cheb_order, cheb_hi=hi, cheb_lo=hi / a.cheb_ratio,
                   inner_tol=a.inner_tol, maxiter=20000, max_cycles=20, check_every=4)
 
@@ -272,7 +275,7 @@ def main():
         barrier()
     launches = mrhs.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    kt = {p: op.kernel_time(p) for p in ("fp16", "bf16", "fp32", "fp64")}
+    kt = {p: op.kernel_time(p) for p in precs}
     op.kernel_timing(False)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -299,7 +302,7 @@ def main():
     if not a.no_extras and rank == 0:
         # standalone coarse-operator throughput at this RHS count, per precision
         cop = {}
-        for p in ("fp16", "bf16", "fp32", "fp64"):
+        for p in precs:
             Xp = B if p == "fp64" else B.to(torch.complex64)
             reps = 2 if p == "fp64" else 10
             op.apply(Xp, p)
@@ -320,11 +323,14 @@ def main():
             fp64 = {"iters": fi["iters"], "ms": fi["ms_total"], "resid": max(fi["resid"]),
                     "ms_per_rhs": fi["ms_total"] / R, "extrapolated": False}
         else:
-            Xf, fi = op.solve(B, tol=1e-30, maxiter=a.fp64_iters, raise_on_fail=False)
-            per_it = (fi["ms_total"] - 2 * cop["fp64"]["ms"]) / max(fi["iters"], 1)
+            # per-iteration cost as the difference of two short runs, so the
+            # fixed start-up and final residual costs cancel
+            _, f1 = op.solve(B, tol=1e-30, maxiter=2, raise_on_fail=False)
+            _, f2 = op.solve(B, tol=1e-30, maxiter=2 + a.fp64_iters, raise_on_fail=False)
+            per_it = (f2["ms_total"] - f1["ms_total"]) / max(f2["iters"] - f1["iters"], 1)
             n_it = fp64_iteration_count(w["name"])
             fp64 = {"ms_per_iter": per_it, "iters_to_tol": n_it, "extrapolated": True,
-                    "ms_per_rhs": (per_it * n_it + 2 * cop["fp64"]["ms"]) / R if n_it else None}
+                    "ms_per_rhs": (per_it * n_it + f1["ms_total"] - 2 * per_it) / R if n_it else None}
         extras["fp64_solve"] = fp64
         if fp64.get("ms_per_rhs"):
             extras["mixed_speedup_vs_fp64"] = fp64["ms_per_rhs"] / value
@@ -357,7 +363,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": "ms/RHS", "n_gpus": world,
                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step,
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64+f32+" + a.precond, "data": "synthetic",
+               "dtype": f"f64+{a.krylov}+{a.precond}", "data": "synthetic",
                "config": {"workload": w["name"], "L": list(w["L"]), "nb": nb, "npts": w["npts"],
                           "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
                           "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
@@ -366,8 +372,11 @@ def main():
                           "l2": "inputs larger than L2 (coefficients "
                                 f"{op_bytes(w, R, a.precond) / 1e9:.1f} GB per application)"},
                "solve": {"iters": inf["iters"], "cycles": inf["cycles"], "applies": inf["applies"],
+                         "cycle_iters": inf["cycle_iters"], "cycle_resid": inf["cycle_resid"],
+                         "cycle_flag": inf["cycle_flag"],
                          "max_true_resid": resid, "lambda_max_est": lam, "setup_s": setup_s},
-               "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
+               "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
+               "kernel_time_ms": {p: {"launches": n, "ms": t} for p, (n, t) in kt.items()}}
         out.update(extras)
         print(json.dumps(out), flush=True)
     if world > 1:

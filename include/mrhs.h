@@ -50,15 +50,27 @@ enum {
   MRHS_PREC_FP32 = 1, /* complex64 coefficients, FP32 FMA; vectors complex64 */
   MRHS_PREC_BF16 = 2, /* bf16 codes x per-site power-of-two scale, tcgen05
                          tensor cores, FP32 accumulation; vectors complex64 */
-  MRHS_PREC_FP16 = 3  /* as BF16 with fp16 codes */
+  MRHS_PREC_FP16 = 3, /* as BF16 with fp16 codes */
+  MRHS_PREC_FP16X = 4, /* fp16 coefficient codes, input in two fp16 terms
+                          (hi + 2^-11 lo): linear in X to ~2^-22; nrhs <= 32 */
+  MRHS_PREC_TC32 = 5  /* coefficients and input in two fp16 terms, lo x lo
+                          dropped: FP32-class accuracy on the tensor cores,
+                          8 bytes per complex coefficient; nrhs <= 32 */
 };
+#define MRHS_NUM_PREC 6
 #define MRHS_PREC_BIT(p) (1u << (p))
+
+/* The four tensor-core forms share one design (op_tc.cu): per site, the
+ * mean real self diagonal d_x in FP32, the rest as codes times a power-of-two
+ * site scale, each input column times a power-of-two scale, FP32 accumulation
+ * in tensor memory.  Two-term values are hi = fp16(u), lo = fp16((u-hi)2^11). */
 
 /* Vector element types. */
 enum { MRHS_C128 = 0, MRHS_C64 = 1 };
 
 #define MRHS_MAX_RHS 64
 #define MRHS_MAX_PTS 81
+#define MRHS_MAX_CYCLES 16
 
 typedef struct mrhs_op_s* mrhs_op;
 
@@ -70,8 +82,8 @@ typedef struct mrhs_op_s* mrhs_op;
  *   A      device complex128 [V][npts][nb][nb]; read during the call only
  *   prec_mask  OR of MRHS_PREC_BIT(p): the precisions to build.  The operator
  *          owns a packed copy of A for each (complex128, complex64, or
- *          bf16/fp16 codes with a float scale per site); A may be freed after
- *          the call returns.
+ *          16-bit codes with a float scale and diagonal per site; FP16 and
+ *          FP16X share one image); A may be freed after the call returns.
  * On success *out holds the handle.  Synchronises `stream`. */
 int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts,
                    const int8_t* disp, const void* A, uint32_t prec_mask, void* stream);
@@ -169,8 +181,9 @@ typedef struct {
   int32_t mode;         /* MRHS_SOLVE_FP64 or MRHS_SOLVE_MIXED */
   int32_t precond;      /* 0: BlockCGrQ (Fig. 2 left); 1: Chebyshev-preconditioned
                            BlockCGrQ (Fig. 2 right) */
-  int32_t precond_prec; /* MRHS_PREC_* of the Chebyshev operator applications
-                           (default MRHS_PREC_FP16) */
+  int32_t precond_prec; /* MRHS_PREC_* of the Chebyshev operator applications;
+                           -1 (default): FP16X if built and nrhs <= 32, else
+                           FP16, BF16 or FP32, the first one built */
   int32_t cheb_order;   /* polynomial degree */
   double cheb_lo;       /* Chebyshev interval; cheb_hi <= 0: hi = 1.08 x power- */
   double cheb_hi;       /*   method estimate; cheb_lo <= 0: lo = hi / 400 */
@@ -181,6 +194,9 @@ typedef struct {
   int32_t max_cycles;   /* MIXED: refinement cycles */
   int32_t check_every;  /* read the convergence flag every k iterations */
   double breakdown_tau; /* relative Cholesky pivot threshold */
+  int32_t krylov_prec;  /* MIXED: operator precision inside the inner Krylov loop,
+                           MRHS_PREC_FP32 or MRHS_PREC_TC32; -1 (default): TC32
+                           if built and nrhs <= 32, else FP32 */
 } mrhs_solve_params;
 
 enum {
@@ -196,10 +212,18 @@ typedef struct {
   int32_t iters;      /* Krylov iterations, all cycles */
   int32_t cycles;     /* refinement cycles (MIXED) or 1 */
   int32_t nrhs;
-  int64_t applies[4]; /* operator applications per precision */
+  int64_t applies[MRHS_NUM_PREC]; /* operator applications per precision */
   double resid[MRHS_MAX_RHS]; /* final true relative residual per RHS (FP64) */
   double cheb_lo, cheb_hi;    /* interval used */
   double ms_total;            /* wall time of the call */
+  int32_t krylov_prec;        /* operator precision used in the Krylov loop */
+  int32_t precond_prec;       /* operator precision used in the preconditioner (-1: none) */
+  /* MIXED, per refinement cycle (first MRHS_MAX_CYCLES): inner iterations,
+   * largest true relative residual after the cycle, and how the inner solve
+   * ended (bit 0 target reached, bit 3 estimate stalled) */
+  int32_t cycle_iters[MRHS_MAX_CYCLES];
+  double cycle_resid[MRHS_MAX_CYCLES];
+  int32_t cycle_flag[MRHS_MAX_CYCLES];
 } mrhs_solve_info;
 
 /* Solve H X = B for nrhs right-hand sides with block CG (Fig. 2).

@@ -22,6 +22,15 @@ to the order of its FP32 accumulation:
       Y(x) = s_x sigma_r sum_p Ahat_p(x) Xhat(x + delta_p) + d_x X(x).
 Both roundings use the same two-step path on both sides, so the quantised
 codes are bit-identical.
+
+Two-term (split) forms, for the tensor-core paths that need FP32-class
+accuracy from 16-bit operands (up to 32 right-hand sides):
+* a value u (an FP32 number) is held as hi = fp16(u) and
+  lo = fp16((u - hi) * 2^11), u ~ hi + 2^-11 lo to about 2^-22 relative;
+* "fp16x": FP16 coefficient codes as above, input columns in two terms:
+      Y = s_x sigma_r sum_p Ahat_p (Xhi + 2^-11 Xlo) + d_x X(x);
+* "tc32": coefficients and input in two terms, the lo x lo product dropped:
+      Y = s_x sigma_r sum_p [Ahi (Xhi + 2^-11 Xlo) + 2^-11 Alo Xhi] + d_x X(x).
 """
 import numpy as np
 import torch
@@ -102,12 +111,42 @@ def quantise_vec(X, kind):
     return round_complex(X32 / sig, kind) * sig
 
 
+def split16(u):
+    """(hi, lo) of FP32 values u: hi = fp16(u), lo = fp16((u - hi) * 2^11)."""
+    u32 = np.asarray(u, dtype=np.float64).astype(np.float32)
+    hi = u32.astype(np.float16).astype(np.float32)
+    lo = ((u32 - hi) * np.float32(2048.0)).astype(np.float16).astype(np.float32)
+    return hi.astype(np.float64), lo.astype(np.float64)
+
+
+def split16_complex(z):
+    hr, lr = split16(np.real(z))
+    hi_, li = split16(np.imag(z))
+    return hr + 1j * hi_, lr + 1j * li
+
+
 def lowprec_apply(A, X, L, disp, kind):
     """The exact value the GPU operator of precision `kind` approximates with
     FP32 accumulation (FP64 arithmetic on the quantised operands)."""
     from .ops import coarse_op_apply
     if kind in ("fp64", "fp32"):
         return coarse_op_apply(quantise_op(A, kind), quantise_vec(X, kind), L, disp)
+    if kind in ("fp16x", "tc32"):
+        s = site_scales(A)
+        u = remainder(A) / s[:, None, None, None]
+        X32 = round_complex(X, "fp32")
+        sig = column_scales(X32)
+        xh, xl = split16_complex(X32 / sig)
+        xh, xl = xh * sig, xl * sig
+        if kind == "fp16x":
+            Ah = round_complex(u, "fp16") * s[:, None, None, None]
+            Y = coarse_op_apply(Ah, xh, L, disp) + 2.0 ** -11 * coarse_op_apply(Ah, xl, L, disp)
+        else:
+            ah, al = split16_complex(round_complex(u, "fp32"))
+            ah, al = ah * s[:, None, None, None], al * s[:, None, None, None]
+            Y = (coarse_op_apply(ah, xh, L, disp) + 2.0 ** -11 * coarse_op_apply(ah, xl, L, disp)
+                 + 2.0 ** -11 * coarse_op_apply(al, xh, L, disp))
+        return Y + site_diagonal(A)[:, None, None] * X32
     s = site_scales(A)
     Ahat = round_complex(remainder(A) / s[:, None, None, None], kind) * s[:, None, None, None]
     X32 = round_complex(X, "fp32")

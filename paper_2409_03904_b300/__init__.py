@@ -138,7 +138,7 @@ class CoarseOp:
         p = SolveParams()
         l.mrhs_solve_params_default(ctypes.byref(p), SOLVE_MIXED if mode == "mixed" else SOLVE_FP64)
         for k, v in kw.items():
-            if k == "precond_prec" and isinstance(v, str):
+            if k in ("precond_prec", "krylov_prec") and isinstance(v, str):
                 v = PREC[v]
             if not hasattr(p, k):
                 raise KeyError(k)

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libmrhs.so")
 MRHS_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NOT_CONVERGED", -4: "BREAKDOWN", -5: "NONFINITE",
           -6: "UNSUPPORTED", -7: "NO_MEMORY"}
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "fp16x": 4, "tc32": 5}
+NAMES = {v: k for k, v in PREC.items()}
 C128, C64 = 0, 1
 MAX_RHS = 64
 SOLVE_FP64, SOLVE_MIXED = 0, 1
@@ -34,20 +35,27 @@ class SolveParams(ctypes.Structure):
                 ("cheb_order", ctypes.c_int32), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_cycles", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("breakdown_tau", ctypes.c_double)]
+                ("breakdown_tau", ctypes.c_double), ("krylov_prec", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
-                ("nrhs", ctypes.c_int32), ("applies", ctypes.c_int64 * 4),
+                ("nrhs", ctypes.c_int32), ("applies", ctypes.c_int64 * 6),
                 ("resid", ctypes.c_double * MAX_RHS), ("cheb_lo", ctypes.c_double),
-                ("cheb_hi", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("cheb_hi", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("krylov_prec", ctypes.c_int32), ("precond_prec", ctypes.c_int32),
+                ("cycle_iters", ctypes.c_int32 * 16), ("cycle_resid", ctypes.c_double * 16),
+                ("cycle_flag", ctypes.c_int32 * 16)]
 
     def as_dict(self):
         return dict(status=self.status, iters=self.iters, cycles=self.cycles,
                     applies={k: int(self.applies[v]) for k, v in PREC.items()},
                     resid=[self.resid[j] for j in range(self.nrhs)], cheb_lo=self.cheb_lo,
-                    cheb_hi=self.cheb_hi, ms_total=self.ms_total)
+                    cheb_hi=self.cheb_hi, ms_total=self.ms_total,
+                    krylov_prec=NAMES.get(self.krylov_prec), precond_prec=NAMES.get(self.precond_prec),
+                    cycle_iters=[self.cycle_iters[c] for c in range(min(self.cycles, 16))],
+                    cycle_resid=[self.cycle_resid[c] for c in range(min(self.cycles, 16))],
+                    cycle_flag=[self.cycle_flag[c] for c in range(min(self.cycles, 16))])
 
 
 _lib = None

@@ -93,7 +93,7 @@ int check_vec(const void* p, const char* name) {
 }
 
 int check_prec(const mrhs_op_s* op, int prec) {
-  if (prec < 0 || prec > 3) return fail(MRHS_ERR_INVALID_ARG, "unknown precision");
+  if (prec < 0 || prec >= MRHS_NUM_PREC) return fail(MRHS_ERR_INVALID_ARG, "unknown precision");
   if (!(op->prec_mask & MRHS_PREC_BIT(prec)))
     return fail(MRHS_ERR_UNSUPPORTED, "precision not built into this operator");
   return MRHS_OK;
@@ -129,8 +129,8 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   *out = nullptr;
   if (nb < 1 || nb > 64) return fail(MRHS_ERR_INVALID_ARG, "nb must be in 1..64");
   if (npts < 1 || npts > MRHS_MAX_PTS) return fail(MRHS_ERR_INVALID_ARG, "npts must be in 1..81");
-  if (prec_mask == 0 || (prec_mask & ~0xFu))
-    return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..3");
+  if (prec_mask == 0 || (prec_mask >> MRHS_NUM_PREC))
+    return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..5");
   if (!aligned16(A)) return fail(MRHS_ERR_INVALID_ARG, "A not 16-byte aligned");
   int64_t V = 1;
   for (int mu = 0; mu < 4; ++mu) {
@@ -191,7 +191,7 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
     }
     { k_to_c64<<<num_sms() * 8, 256, 0, s>>>((const double2*)A, op->a32, (int64_t)nA); ::mrhs::count_launch(); }
   }
-  for (int prec = MRHS_PREC_BF16; prec <= MRHS_PREC_FP16; ++prec)
+  for (int prec = MRHS_PREC_BF16; prec < MRHS_NUM_PREC; ++prec)
     if (prec_mask & MRHS_PREC_BIT(prec)) {
       int st = tc_build(op, prec, false, (const double2*)A, s);
       if (st != MRHS_OK) {
@@ -240,7 +240,7 @@ int mrhs_op_kernel_timing(mrhs_op op, int32_t enable) {
 }
 
 int mrhs_op_kernel_time(mrhs_op op, int32_t prec, int64_t* launches, double* ms) {
-  if (!op || !launches || !ms || prec < 0 || prec > 3)
+  if (!op || !launches || !ms || prec < 0 || prec >= MRHS_NUM_PREC)
     return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_kernel_time: arguments");
   KernelTimer& t = op->timer[prec];
   double total = 0.0;
@@ -265,7 +265,7 @@ int mrhs_op_destroy(mrhs_op op) {
   cudaFree(op->nbr_bwd);
   cudaFree(op->a64);
   cudaFree(op->a32);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     cudaFree(op->tc[i].codes);
     cudaFree(op->tc[i].scale);
     cudaFree(op->tc[i].diag);
@@ -379,20 +379,43 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
     return fail(MRHS_ERR_INVALID_ARG, "mode");
   if (!(op->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)))
     return fail(MRHS_ERR_UNSUPPORTED, "block_cg_solve needs the FP64 operator");
-  if (p.mode == MRHS_SOLVE_MIXED && !(op->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP32)))
-    return fail(MRHS_ERR_UNSUPPORTED, "mixed mode needs the FP32 operator");
-  if (p.precond) {
-    if (p.precond_prec < 0 || p.precond_prec > 3) return fail(MRHS_ERR_INVALID_ARG, "precond_prec");
-    if (!(op->prec_mask & MRHS_PREC_BIT(p.precond_prec)))
+  mrhs_solve_params q = p;   // resolve the automatic precision choices
+  auto built = [&](int pr) { return (op->prec_mask & MRHS_PREC_BIT(pr)) != 0; };
+  auto fits = [&](int pr) {
+    return !(pr == MRHS_PREC_FP16X || pr == MRHS_PREC_TC32) || nrhs <= 32;
+  };
+  if (q.mode == MRHS_SOLVE_MIXED) {
+    if (q.krylov_prec < 0)
+      q.krylov_prec = (built(MRHS_PREC_TC32) && fits(MRHS_PREC_TC32)) ? MRHS_PREC_TC32 : MRHS_PREC_FP32;
+    if (q.krylov_prec != MRHS_PREC_FP32 && q.krylov_prec != MRHS_PREC_TC32)
+      return fail(MRHS_ERR_INVALID_ARG, "krylov_prec must be FP32 or TC32");
+    if (!built(q.krylov_prec) || !fits(q.krylov_prec))
+      return fail(MRHS_ERR_UNSUPPORTED, "mixed mode needs the FP32 (or TC32, nrhs <= 32) operator");
+  }
+  if (q.precond && q.precond_prec < 0) {
+    const int order[] = {MRHS_PREC_FP16X, MRHS_PREC_FP16, MRHS_PREC_BF16, MRHS_PREC_TC32,
+                         MRHS_PREC_FP32};
+    q.precond_prec = q.mode == MRHS_SOLVE_FP64 ? MRHS_PREC_FP64 : -1;
+    if (q.mode == MRHS_SOLVE_MIXED)
+      for (int pr : order)
+        if (built(pr) && fits(pr)) { q.precond_prec = pr; break; }
+  }
+  const mrhs_solve_params& pp = q;
+  if (pp.precond) {
+    if (pp.precond_prec < 0 || pp.precond_prec >= MRHS_NUM_PREC)
+      return fail(MRHS_ERR_INVALID_ARG, "precond_prec");
+    if (!fits(pp.precond_prec))
+      return fail(MRHS_ERR_UNSUPPORTED, "FP16X/TC32 preconditioner needs nrhs <= 32");
+    if (!built(pp.precond_prec))
       return fail(MRHS_ERR_UNSUPPORTED, "preconditioner precision not built");
-    if (p.mode == MRHS_SOLVE_FP64 && p.precond_prec != MRHS_PREC_FP64)
+    if (pp.mode == MRHS_SOLVE_FP64 && pp.precond_prec != MRHS_PREC_FP64)
       return fail(MRHS_ERR_INVALID_ARG, "FP64 mode takes an FP64 preconditioner");
-    if (p.mode == MRHS_SOLVE_MIXED && p.precond_prec == MRHS_PREC_FP64)
-      return fail(MRHS_ERR_INVALID_ARG, "mixed mode takes a FP32/BF16/FP16 preconditioner");
-    if (p.cheb_order < 0) return fail(MRHS_ERR_INVALID_ARG, "cheb_order");
+    if (pp.mode == MRHS_SOLVE_MIXED && pp.precond_prec == MRHS_PREC_FP64)
+      return fail(MRHS_ERR_INVALID_ARG, "mixed mode takes a low-precision preconditioner");
+    if (pp.cheb_order < 0) return fail(MRHS_ERR_INVALID_ARG, "cheb_order");
   }
   if (X == B) return fail(MRHS_ERR_INVALID_ARG, "X and B must differ");
-  return solve(op, (const double2*)B, (double2*)X, nrhs, p, info, (cudaStream_t)stream);
+  return solve(op, (const double2*)B, (double2*)X, nrhs, pp, info, (cudaStream_t)stream);
 }
 
 void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
@@ -402,11 +425,12 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->maxiter = 5000;
   p->mode = mode;
   p->precond = mode == MRHS_SOLVE_MIXED ? 1 : 0;
-  p->precond_prec = MRHS_PREC_FP16;
-  p->cheb_order = 16;
+  p->precond_prec = -1;
+  p->krylov_prec = -1;
+  p->cheb_order = 8;
   p->cheb_lo = 0.0;
   p->cheb_hi = 0.0;
-  p->inner_tol = 1e-4;
+  p->inner_tol = 1e-3;
   p->max_cycles = 12;
   p->check_every = 4;
   p->breakdown_tau = 1e-12;

@@ -95,14 +95,14 @@ struct mrhs_op_s {
   int32_t* nbr_bwd = nullptr;   // [npts][V]  x - delta_p
   double2* a64 = nullptr;       // [V][npts][nb][nb]
   float2* a32 = nullptr;        // [V][npts][nb][nb]
-  mrhs::TcImage tc[2];          // BF16, FP16: forward stencil
-  mrhs::TcImage tc_dag[2];      // BF16, FP16: daggered stencil (built on demand)
+  mrhs::TcImage tc[3];          // BF16, FP16 (also FP16X), TC32: forward stencil
+  mrhs::TcImage tc_dag[3];      // the same for the daggered stencil (on demand)
   mrhs::Workspace ws_xpack;     // packed input vectors for the tensor path
   mrhs::Workspace ws_cheb;      // Chebyshev recurrence vectors
   mrhs::Workspace ws_small;     // column scales etc.
   mrhs::Workspace ws_solve;     // block CG vectors and state
-  mrhs::KernelTimer timer[4];   // per precision
-  double lam_max[4] = {0, 0, 0, 0};  // cached power-method estimates
+  mrhs::KernelTimer timer[MRHS_NUM_PREC];   // per precision
+  double lam_max[MRHS_NUM_PREC] = {0, 0, 0, 0, 0, 0};  // cached power-method estimates
   mrhs::TcTune tc_tune;              // tensor-core launch shape
   bool tc_set = false;               // tc_tune set explicitly
 };
@@ -120,7 +120,7 @@ int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s
 unsigned tc_read_and_clear_error();
 int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
              cudaStream_t s);
-int tc_supported(const mrhs_op_s* op, int nrhs);
+int tc_supported(const mrhs_op_s* op, int prec, int nrhs);
 // blas.cu
 int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
          cudaStream_t s);

@@ -1,10 +1,12 @@
-// BF16 / FP16 coarse operator on the 5th-generation tensor cores (tcgen05).
+// Coarse operator on the 5th-generation tensor cores (tcgen05): BF16, FP16,
+// and two split forms (FP16X, TC32) that reach FP32-class accuracy from
+// 16-bit operands.
 //
 // Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.6, "Applying the coarse
 // operator"), in the quantised form: the mean real diagonal d_x of the self
 // block is carried exactly in FP32, the remainder of the site's coefficient
-// block is stored as bf16/fp16 codes times a power-of-two site scale s_x,
-// every RHS column of the input as codes times a power-of-two sigma_r, and
+// block is stored as 16-bit codes times a power-of-two site scale s_x, every
+// RHS column of the input as codes times a power-of-two sigma_r, and
 //   Y(x) = s_x sigma_r sum_p Ahat_p(x) Xhat(x + delta_p) + d_x X(x),
 // with the sum accumulated in FP32 in tensor memory.
 //
@@ -16,8 +18,20 @@
 // so the streamed coefficient block enters unexpanded (its bytes are the HBM
 // traffic that bounds the kernel) and the sign/duplication goes to the small
 // X operand, which is packed once per call and re-read from L2 by the 9 or
-// 81 sites that neighbour it.  M = 128 (rows >= 2R ignored), N = nb rounded
-// up to 16, K = 2 nb, summed over all stencil points into one accumulator.
+// 81 sites that neighbour it.  M = 128, N = nb rounded up to 16, K = 2 nb,
+// summed over all stencil points into one accumulator.
+//
+// Split forms (up to 32 right-hand sides, so 2R <= 64): a value u is held as
+// hi = fp16(u), lo = fp16((u - hi) 2^11).  XSPLIT puts the input's lo rows in
+// rows 64..127 of the same M = 128 operand (rows that are idle otherwise),
+// so one MMA gives both Ahi Xhi (rows < 64) and Ahi Xlo (rows >= 64); ASPLIT
+// adds a second MMA per step against the coefficients' lo tile into a second
+// accumulator, whose rows < 64 are Alo Xhi.  The epilogue combines
+//   D1[m] + 2^-11 (D1[64 + m] + D2[m]),
+// fetching D1[64 + m] from the warps that own those TMEM lanes through
+// shared memory.  FP16X = FP16 coefficients with a two-term input (linear in
+// X to ~2^-22, for a stationary preconditioner); TC32 = both operands in two
+// terms (FP32-class operator, same bytes per coefficient as complex64).
 //
 // Both operands are pre-packed in global memory in the canonical K-major
 // no-swizzle tcgen05 layout (8 x 16-byte core matrices, K groups 128 bytes
@@ -25,14 +39,16 @@
 // per tile lands it ready for the MMA.  Element (row, k) of a tile with K
 // columns sits at byte (row/8)*(K/8)*128 + (k/8)*128 + (row%8)*16 + (k%8)*2.
 //
-// Kernel: persistent, one CTA per SM, warp-specialised:
-//   warp 0      TMA producer: per (site, p) one coefficient tile (read once
-//               per application, L2 evict-first) and the neighbour's packed
-//               X tile (L2 evict-last), into an nstage ring of shared memory
+// Kernel: persistent, two CTAs per SM by default (two independent rings),
+// warp-specialised:
+//   warp 0      TMA producer: per stage the coefficient tiles of `pps`
+//               consecutive stencil points of one site (contiguous, one bulk
+//               copy, L2 evict-first) and their neighbours' packed X tiles
+//               (L2 evict-last), into an nstage ring of shared memory
 //   warp 1      allocates TMEM, issues tcgen05.mma (one elected thread) into
 //               two alternating accumulators, commits stage releases
 //   warps 2-5   epilogue: tcgen05.ld of their 32-lane quarter, scales, adds
-//               d_x X(x), stores complex64 Y
+//               d_x X(x) (loaded before the wait), stores complex64 Y
 // Every mbarrier wait is bounded (1 s); on expiry the kernel records an
 // error, drains its own copies, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -48,27 +64,34 @@ __device__ unsigned int g_tc_error = 0;
 namespace {
 
 constexpr int kThreadsTc = 192;
-constexpr int kAccCols = 64;     // TMEM columns per accumulator
-constexpr int kTmemCols = 128;   // two accumulators
+constexpr int kAccCols = 64;     // TMEM columns per accumulator (n_mma <= 64)
 constexpr int kM = 128;
-constexpr size_t kSmemBudget = 220 * 1024;   // dynamic shared memory per SM for the ring
+constexpr int kLoRow = 64;       // first row of the input's lo term (XSPLIT)
+constexpr size_t kSmemBudget = 220 * 1024;   // dynamic shared memory per SM
+constexpr float kLoScale = 1.0f / 2048.0f;   // 2^-11
 
 struct Geom {
   int nb, nbp8, K, n_mma;   // K = 2 nbp8
-  int R, rows8;             // rows8 = round_up(2R, 8)
-  uint32_t coef_bytes, xb_bytes, sbo;
+  int R, xrows;             // rows of a packed input tile
+  int xsplit, asplit;
+  uint32_t coef1;           // one coefficient tile (hi or lo)
+  uint32_t coef_bytes;      // coefficient bytes per stencil point (x2 if asplit)
+  uint32_t xb_bytes, sbo;
 };
 
-Geom make_geom(int nb, int R) {
+Geom make_geom(int nb, int R, bool xsplit, bool asplit) {
   Geom g;
   g.nb = nb;
   g.nbp8 = (nb + 7) / 8 * 8;
   g.K = 2 * g.nbp8;
   g.n_mma = (nb + 15) / 16 * 16;
   g.R = R;
-  g.rows8 = (2 * R + 7) / 8 * 8;
-  g.coef_bytes = (uint32_t)g.nbp8 * g.K * 2;
-  g.xb_bytes = (uint32_t)g.rows8 * g.K * 2;
+  g.xsplit = xsplit;
+  g.asplit = asplit;
+  g.xrows = xsplit ? kM : (2 * R + 7) / 8 * 8;
+  g.coef1 = (uint32_t)g.nbp8 * g.K * 2;
+  g.coef_bytes = g.coef1 * (asplit ? 2u : 1u);
+  g.xb_bytes = (uint32_t)g.xrows * g.K * 2;
   g.sbo = (uint32_t)(g.K / 8) * 128;
   return g;
 }
@@ -100,10 +123,27 @@ __device__ inline uint16_t code16(float v) {
   if (BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
   return __half_as_ushort(__float2half_rn(v));
 }
+// two-term split of an FP32 value: hi = fp16(u), lo = fp16((u - hi) 2^11)
+__device__ inline void split16(float u, uint16_t& hi, uint16_t& lo) {
+  const __half h = __float2half_rn(u);
+  hi = __half_as_ushort(h);
+  lo = __half_as_ushort(__float2half_rn((u - __half2float(h)) * 2048.0f));
+}
+
+int image_index(int prec) {
+  switch (prec) {
+    case MRHS_PREC_BF16: return 0;
+    case MRHS_PREC_FP16:
+    case MRHS_PREC_FP16X: return 1;
+    case MRHS_PREC_TC32: return 2;
+    default: return -1;
+  }
+}
 
 // One CTA per site: d_x, s_x and the codes of the site's coefficient tiles.
 // dag: the block of stencil point p at site x is A_p(x - delta_p)^dagger.
-template <bool BF16>
+// ASPLIT: each point gets a hi tile followed by a lo tile.
+template <bool BF16, bool ASPLIT>
 __global__ void __launch_bounds__(256) k_pack_coef(const double2* __restrict__ A, uint8_t* codes,
                                                    float* scale, float* diag,
                                                    const int32_t* __restrict__ nbr_bwd, int64_t V,
@@ -162,7 +202,14 @@ __global__ void __launch_bounds__(256) k_pack_coef(const double2* __restrict__ A
         if (p == 0 && a == b) c.x -= d;
         v = __double2float_rn((k < g.nbp8 ? c.x : c.y) * inv);
       }
-      *reinterpret_cast<uint16_t*>(tile + canon_off(a, k, g.K)) = code16<BF16>(v);
+      if (ASPLIT) {
+        uint16_t hi, lo;
+        split16(v, hi, lo);
+        *reinterpret_cast<uint16_t*>(tile + canon_off(a, k, g.K)) = hi;
+        *reinterpret_cast<uint16_t*>(tile + g.coef1 + canon_off(a, k, g.K)) = lo;
+      } else {
+        *reinterpret_cast<uint16_t*>(tile + canon_off(a, k, g.K)) = code16<BF16>(v);
+      }
     }
   }
 }
@@ -189,52 +236,64 @@ __global__ void k_colscale(const unsigned* __restrict__ colmax, float* sigma, in
   if (r < R) sigma[r] = (float)pow2_ceil((double)__uint_as_float(colmax[r]));
 }
 
-// Packed real-split input tiles, one [rows8][K] canonical tile per site.
-template <bool BF16>
+// Packed real-split input tiles, one [xrows][K] canonical tile per site.
+// XSPLIT: rows < 2R hold the hi term, rows 64 + (0..2R-1) the lo term.
+template <bool BF16, bool XSPLIT>
 __global__ void k_pack_xb(const float2* __restrict__ X, const float* __restrict__ sigma,
                           uint8_t* xb, int64_t V, int nb, Geom g) {
-  const int units = g.rows8 * (g.K / 8);   // 16-byte units per site
+  const int units = g.xrows * (g.K / 8);   // 16-byte units per site
   const int64_t total = V * units;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total;
        u += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = u / units;
     const int w = (int)(u % units);
-    const int kc = w / g.rows8, m = w % g.rows8;
+    const int kc = w / g.xrows, mrow = w % g.xrows;
+    const bool lo_term = XSPLIT && mrow >= kLoRow;
+    const int m = lo_term ? mrow - kLoRow : mrow;
     const int R = g.R;
     uint16_t h[8];
     const bool re_row = m < R;
     const int r = re_row ? m : m - R;
-    const float inv = (m < 2 * R) ? 1.0f / sigma[r] : 0.f;
+    const bool live = m < 2 * R;
+    const float inv = live ? 1.0f / sigma[r] : 0.f;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = kc * 8 + e;
       const bool first = k < g.nbp8;
       const int b = first ? k : k - g.nbp8;
       float v = 0.f;
-      if (m < 2 * R && b < nb) {
+      if (live && b < nb) {
         const float2 xv = X[(x * nb + b) * R + r];
         if (re_row) v = first ? xv.x : -xv.y;
         else v = first ? xv.y : xv.x;
         v *= inv;
       }
-      h[e] = code16<BF16>(v);
+      if (XSPLIT) {
+        uint16_t hi, lo;
+        split16(v, hi, lo);
+        h[e] = lo_term ? lo : hi;
+      } else {
+        h[e] = code16<BF16>(v);
+      }
     }
     uint4 pk;
     pk.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
     pk.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
     pk.z = (uint32_t)h[4] | ((uint32_t)h[5] << 16);
     pk.w = (uint32_t)h[6] | ((uint32_t)h[7] << 16);
-    *reinterpret_cast<uint4*>(xb + (uint64_t)x * g.xb_bytes + canon_off(m, kc * 8, g.K)) = pk;
+    *reinterpret_cast<uint4*>(xb + (uint64_t)x * g.xb_bytes + canon_off(mrow, kc * 8, g.K)) = pk;
   }
 }
 
-template <bool BF16>
-__global__ void __launch_bounds__(kThreadsTc, 1)
+template <bool BF16, bool XSPLIT, bool ASPLIT>
+__global__ void __launch_bounds__(kThreadsTc, 2)
     k_op_tc(const uint8_t* __restrict__ coef, const uint8_t* __restrict__ xb,
             const float* __restrict__ sscale, const float* __restrict__ sdiag,
             const float* __restrict__ sigma, const float* __restrict__ Xf, float* __restrict__ Yf,
             const Stencil st, int64_t V, int npts, Geom g, int nstages, int pps) {
   extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int kAccStride = ASPLIT ? 2 * kAccCols : kAccCols;   // TMEM cols per buffer
+  constexpr uint32_t kTmemCols = ASPLIT ? 256u : 128u;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + nstages;
   uint64_t* acc_full = empty + nstages;
@@ -246,6 +305,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   // neighbour input tiles
   const uint32_t stage_bytes = (uint32_t)pps * (g.coef_bytes + g.xb_bytes);
   const uint32_t xb_off = (uint32_t)pps * g.coef_bytes;
+  // XSPLIT exchange buffer for the lo rows, after the ring
+  float* ex = reinterpret_cast<float*>(stages + (size_t)nstages * stage_bytes);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -338,7 +399,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       for (int64_t x = blockIdx.x; x < V && ok; x += gridDim.x) {
         if (!ptx::mbar_wait(&acc_empty[acc], aph ^ 1u, &s_abort)) { ok = false; break; }
         ptx::tc_fence_after();
-        const uint32_t tmem_d = tmem_base + (uint32_t)(acc * kAccCols);
+        const uint32_t tmem_d = tmem_base + (uint32_t)(acc * kAccStride);
         for (int p0 = 0; p0 < npts; p0 += pps) {
           const int np = (npts - p0) < pps ? (npts - p0) : pps;
           if (!ptx::mbar_wait(&full[s], ph, &s_abort)) { ok = false; break; }
@@ -347,10 +408,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           for (int i = 0; i < np; ++i) {
             const uint32_t cb = sb + (uint32_t)i * g.coef_bytes;
             const uint32_t ab = sb + xb_off + (uint32_t)i * g.xb_bytes;
+            const uint32_t first = (p0 > 0 || i > 0) ? 1u : 0u;
             for (int j = 0; j < nk; ++j) {
               const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)j * 256u, 128u, g.sbo);
               const uint64_t bdesc = ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, g.sbo);
-              ptx::mma_f16(tmem_d, adesc, bdesc, idesc, (p0 > 0 || i > 0 || j > 0) ? 1u : 0u);
+              ptx::mma_f16(tmem_d, adesc, bdesc, idesc, (first || j > 0) ? 1u : 0u);
+              if (ASPLIT) {
+                const uint64_t ldesc = ptx::smem_desc(cb + g.coef1 + (uint32_t)j * 256u, 128u, g.sbo);
+                ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc, ldesc, idesc,
+                             (first || j > 0) ? 1u : 0u);
+              }
             }
           }
           ptx::mma_commit(&empty[s]);
@@ -368,12 +435,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   } else {
     // ---------------- epilogue, warps 2..5 -> TMEM lane quarters 2,3,0,1
     const int q = warp & 3;
-    const int m = 32 * q + lane;          // D row
+    const int mrow = 32 * q + lane;              // D row = TMEM lane
+    const bool lo_thread = XSPLIT && mrow >= kLoRow;
+    const int m = lo_thread ? mrow - kLoRow : mrow;
     const int R = g.R, nb = g.nb;
     const bool valid = m < 2 * R;
+    const bool writer = valid && !lo_thread;
     const int r = valid ? (m < R ? m : m - R) : 0;
     const int part = m < R ? 0 : 1;
-    const float sig = valid ? sigma[r] : 0.f;
+    const float sig = writer ? sigma[r] : 0.f;
     int acc = 0;
     uint32_t aph = 0;
     for (int64_t x = blockIdx.x; x < V; x += gridDim.x) {
@@ -381,7 +451,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       // the site's MMAs
       float xv[kAccCols];
       float sc = 0.f, dx = 0.f;
-      if (valid) {
+      if (writer) {
         sc = __ldg(&sscale[x]) * sig;
         dx = __ldg(&sdiag[x]);
 #pragma unroll
@@ -389,20 +459,50 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           xv[a] = a < nb ? __ldg(&Xf[(((int64_t)x * nb + a) * R + r) * 2 + part]) : 0.f;
       }
       const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort);
-      if (!__all_sync(0xffffffffu, got)) {   // warp-uniform: tcgen05.ld below is .aligned
+      // give up together: tcgen05.ld below is .aligned per warp, and with
+      // XSPLIT the four epilogue warps also meet at named barriers
+      const bool all_got = XSPLIT ? ptx::epilogue_all(got) : __all_sync(0xffffffffu, got);
+      if (!all_got) {
         s_abort = 1;
         atomicOr(&g_tc_error, 4u);
         break;
       }
       ptx::tc_fence_after();
       float v[kAccCols];
-      const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols);
+      const uint32_t taddr =
+          tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccStride);
       ptx::tmem_ld32_sync(taddr, v);
       if (g.n_mma > 32) ptx::tmem_ld32_sync(taddr + 32u, v + 32);
+      if (ASPLIT && !lo_thread) {      // + 2^-11 Alo Xhi (rows < 64 only)
+        float w[32];
+        ptx::tmem_ld32_sync(taddr + (uint32_t)kAccCols, w);
+#pragma unroll
+        for (int a = 0; a < 32; ++a) v[a] = fmaf(kLoScale, w[a], v[a]);
+        if (g.n_mma > 32) {
+          ptx::tmem_ld32_sync(taddr + (uint32_t)kAccCols + 32u, w);
+#pragma unroll
+          for (int a = 0; a < 32; ++a) v[32 + a] = fmaf(kLoScale, w[a], v[32 + a]);
+        }
+      }
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
-      if (valid) {
+      if (XSPLIT) {
+        // lo rows hand 2^-11 Ahi Xlo to the thread of the matching hi row
+        if (lo_thread && valid) {
+#pragma unroll
+          for (int a = 0; a < kAccCols; ++a)
+            if (a < nb) ex[m * kAccCols + a] = kLoScale * v[a];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (writer) {
+#pragma unroll
+          for (int a = 0; a < kAccCols; ++a)
+            if (a < nb) v[a] += ex[m * kAccCols + a];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
+      if (writer) {
 #pragma unroll
         for (int a = 0; a < kAccCols; ++a) {
           if (a < nb) {
@@ -427,16 +527,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 // bytes of shared memory per CTA.
 int tc_stages(const Geom& g, int pps, size_t budget, int max_stages, size_t* smem_out) {
   const size_t stage = (size_t)pps * (g.coef_bytes + g.xb_bytes);
-  // the M = 128 operand read runs past a 2R-row input tile, and the N = n_mma
-  // read past an nbp8-row coefficient tile: keep that much slack at the end
+  // the M = 128 operand read runs past an input tile of fewer than 128 rows,
+  // and the N = n_mma read past an nbp8-row coefficient tile: keep that much
+  // slack at the end (plus the XSPLIT exchange buffer)
   const size_t row_bytes = (size_t)g.K * 2;
-  const size_t slack = (size_t)(kM - g.rows8) * row_bytes + (size_t)(g.n_mma) * row_bytes + 1024;
-  if (budget < 1024 + slack + 2 * stage) return 0;
-  int n = (int)((budget - 1024 - slack) / stage);
+  size_t tail = (size_t)(kM - g.xrows) * row_bytes + (size_t)(g.n_mma) * row_bytes + 1024;
+  if (g.xsplit) tail += (size_t)kLoRow * kAccCols * sizeof(float);
+  if (budget < 1024 + tail + 2 * stage) return 0;
+  int n = (int)((budget - 1024 - tail) / stage);
   if (n > max_stages) n = max_stages;
   if (n > 32) n = 32;                 // barrier area: 2 * 32 + 4 words < 1024 bytes
   if (n < 2) return 0;
-  *smem_out = 1024 + (size_t)n * stage + slack;
+  *smem_out = 1024 + (size_t)n * stage + tail;
   return n;
 }
 
@@ -451,20 +553,35 @@ TcTune default_tune(const Geom& g) {
   return t;
 }
 
+template <bool BF16, bool XS, bool AS>
+int launch_tc(const TcImage& img, const uint8_t* xb, const float* sigma, const void* X, void* Y,
+              const Stencil& stn, int64_t V, int npts, const Geom& g, int nst, int pps,
+              size_t smem, int64_t grid, cudaStream_t s) {
+  auto kern = k_op_tc<BF16, XS, AS>;
+  MRHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  { kern<<<(unsigned)grid, kThreadsTc, smem, s>>>((const uint8_t*)img.codes, xb, img.scale, img.diag,
+                                                  sigma, (const float*)X, (float*)Y, stn, V, npts,
+                                                  g, nst, pps); ::mrhs::count_launch(); }
+  return MRHS_OK;
+}
+
 }  // namespace
 
-int tc_supported(const mrhs_op_s* op, int nrhs) {
+int tc_supported(const mrhs_op_s* op, int prec, int nrhs) {
   if (op->nb > 64 || nrhs > 64 || nrhs < 1) return 0;
+  const bool xs = prec == MRHS_PREC_FP16X || prec == MRHS_PREC_TC32;
+  if (xs && nrhs > 32) return 0;
   size_t smem;
-  return tc_stages(make_geom(op->nb, nrhs), 1, kSmemBudget, 32, &smem) > 0;
+  return tc_stages(make_geom(op->nb, nrhs, xs, prec == MRHS_PREC_TC32), 1, kSmemBudget, 32,
+                   &smem) > 0;
 }
 
 int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s) {
-  const int i = prec - MRHS_PREC_BF16;
-  if (i < 0 || i > 1) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
+  const int i = image_index(prec);
+  if (i < 0) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
   TcImage& img = dag ? op->tc_dag[i] : op->tc[i];
   if (img.codes) return MRHS_OK;
-  const Geom g = make_geom(op->nb, 1);
+  const Geom g = make_geom(op->nb, 1, false, i == 2);
   if (!A) return fail(MRHS_ERR_INVALID_ARG, "no source coefficients for the packed image");
   img.bytes = (size_t)op->V * op->npts * g.coef_bytes;
   if (cudaMalloc(&img.codes, img.bytes) != cudaSuccess ||
@@ -473,29 +590,38 @@ int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s
     cudaGetLastError();
     return fail(MRHS_ERR_NO_MEMORY, "tensor-core coefficient image");
   }
-  if (prec == MRHS_PREC_BF16)
-    { k_pack_coef<true><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
+  const unsigned grid = (unsigned)op->V;
+  if (i == 0)
+    { k_pack_coef<true, false><<<grid, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
                                                      op->nbr_bwd, op->V, op->npts, op->nb, g,
                                                      dag ? 1 : 0); ::mrhs::count_launch(); }
+  else if (i == 1)
+    { k_pack_coef<false, false><<<grid, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
+                                                      op->nbr_bwd, op->V, op->npts, op->nb, g,
+                                                      dag ? 1 : 0); ::mrhs::count_launch(); }
   else
-    { k_pack_coef<false><<<(unsigned)op->V, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale,
-                                                      img.diag, op->nbr_bwd, op->V, op->npts,
-                                                      op->nb, g, dag ? 1 : 0); ::mrhs::count_launch(); }
+    { k_pack_coef<false, true><<<grid, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
+                                                     op->nbr_bwd, op->V, op->npts, op->nb, g,
+                                                     dag ? 1 : 0); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }
 
 int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
              cudaStream_t s) {
-  const int i = prec - MRHS_PREC_BF16;
-  if (i < 0 || i > 1) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
-  if (!tc_supported(op, nrhs)) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core shape");
+  const int i = image_index(prec);
+  if (i < 0) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
+  if (!tc_supported(op, prec, nrhs))
+    return fail(MRHS_ERR_UNSUPPORTED,
+                "tensor-core shape (nb <= 64; nrhs <= 64, or <= 32 for FP16X/TC32)");
   if (dag && !op->tc_dag[i].codes) {
     if (!op->a64) return fail(MRHS_ERR_UNSUPPORTED, "daggered low-precision image needs FP64 coefficients");
     MRHS_TRY(tc_build(op, prec, true, op->a64, s));
   }
   const TcImage& img = dag ? op->tc_dag[i] : op->tc[i];
-  const Geom g = make_geom(op->nb, nrhs);
+  const bool xs = prec == MRHS_PREC_FP16X || prec == MRHS_PREC_TC32;
+  const bool as = prec == MRHS_PREC_TC32;
+  const Geom g = make_geom(op->nb, nrhs, xs, as);
   const size_t xb_bytes = (size_t)op->V * g.xb_bytes;
   const size_t small = 256 * sizeof(unsigned);
   MRHS_TRY(op->ws_xpack.ensure(xb_bytes + small));
@@ -507,9 +633,11 @@ int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs
   { k_colmax<<<sms * 4, 256, 0, s>>>((const float2*)X, op->V * op->nb, nrhs, colmax); ::mrhs::count_launch(); }
   { k_colscale<<<1, 64, 0, s>>>(colmax, sigma, nrhs); ::mrhs::count_launch(); }
   if (prec == MRHS_PREC_BF16)
-    { k_pack_xb<true><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
+    { k_pack_xb<true, false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
+  else if (!xs)
+    { k_pack_xb<false, false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
   else
-    { k_pack_xb<false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
+    { k_pack_xb<false, true><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   TcTune t = default_tune(g);
   if (op->tc_tune.pps > 0) t.pps = op->tc_tune.pps;
@@ -537,20 +665,21 @@ int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs
   const int64_t cap = (int64_t)sms * t.ctas_per_sm;
   const int64_t grid = op->V < cap ? op->V : cap;
   timer_mark(op, prec, s);
-  if (prec == MRHS_PREC_BF16) {
-    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    { k_op_tc<true><<<(unsigned)grid, kThreadsTc, smem, s>>>(
-        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float*)X, (float*)Y,
-        stn, op->V, op->npts, g, nst, t.pps); ::mrhs::count_launch(); }
-  } else {
-    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_op_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    { k_op_tc<false><<<(unsigned)grid, kThreadsTc, smem, s>>>(
-        (const uint8_t*)img.codes, xb, img.scale, img.diag, sigma, (const float*)X, (float*)Y,
-        stn, op->V, op->npts, g, nst, t.pps); ::mrhs::count_launch(); }
-  }
+  int st = MRHS_OK;
+  if (prec == MRHS_PREC_BF16)
+    st = launch_tc<true, false, false>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
+                                       smem, grid, s);
+  else if (prec == MRHS_PREC_FP16)
+    st = launch_tc<false, false, false>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
+                                        smem, grid, s);
+  else if (prec == MRHS_PREC_FP16X)
+    st = launch_tc<false, true, false>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
+                                       smem, grid, s);
+  else
+    st = launch_tc<false, true, true>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
+                                      smem, grid, s);
   timer_mark(op, prec, s);
+  MRHS_TRY(st);
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }

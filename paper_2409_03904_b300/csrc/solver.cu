@@ -359,7 +359,7 @@ struct Ctx {
   Small* st = nullptr;        // device
   double2* gpart = nullptr;   // Gram partials
   double* npart = nullptr;    // column-norm partials
-  int64_t applies[4] = {0, 0, 0, 0};
+  int64_t applies[MRHS_NUM_PREC] = {0, 0, 0, 0, 0, 0};
   // bump allocation from one grow-only operator-owned workspace: a first
   // pass with base == nullptr only sums the sizes
   char* base = nullptr;
@@ -680,16 +680,43 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     MRHS_CUDA_TRY(cudaStreamSynchronize(s));
     return MRHS_OK;
   };
+  // a zero initial guess needs no operator application: r = B
+  auto initial_residual = [&]() -> int {
+    std::vector<double> xn(R);
+    MRHS_TRY(cx.colnorms<double2>(X, sb.rnorm_d));
+    MRHS_CUDA_TRY(cudaMemcpyAsync(xn.data(), sb.rnorm_d, sizeof(double) * R,
+                                  cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    bool zero = true;
+    for (double v : xn) zero = zero && v == 0.0;
+    if (!zero) return true_residual();
+    MRHS_CUDA_TRY(cudaMemcpyAsync(sb.r64, B, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+    rnorm = bnorm;
+    return MRHS_OK;
+  };
   auto all_done = [&]() {
     for (int j = 0; j < R; ++j)
       if (bnorm[j] > 0 && !(rnorm[j] <= p.tol * bnorm[j])) return false;
     return true;
   };
+  auto max_rel = [&]() {
+    double m = 0.0;
+    for (int j = 0; j < R; ++j)
+      if (bnorm[j] > 0) m = std::fmax(m, rnorm[j] / bnorm[j]);
+    return m;
+  };
   const int every = p.check_every > 0 ? p.check_every : 1;
+  if (info) {
+    for (int c = 0; c < MRHS_MAX_CYCLES; ++c) {
+      info->cycle_iters[c] = 0;
+      info->cycle_resid[c] = 0.0;
+      info->cycle_flag[c] = 0;
+    }
+  }
 
   if (!mixed) {
     for (int j = 0; j < R; ++j) target[j] = p.tol * bnorm[j];
-    MRHS_TRY(true_residual());
+    MRHS_TRY(initial_residual());
     cycles = 0;
     if (!all_done()) {
       int it = 0;
@@ -701,7 +728,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       MRHS_TRY(true_residual());
     }
   } else {
-    MRHS_TRY(true_residual());
+    MRHS_TRY(initial_residual());
     for (cycles = 0; cycles < p.max_cycles && !all_done() && total_iters < p.maxiter; ++cycles) {
       // scale each residual column to unit norm; inner target relative to 1
       std::vector<double> rho(R);
@@ -716,13 +743,18 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       MRHS_CUDA_TRY(cudaMemsetAsync(sb.e32, 0, sizeof(float2) * n, s));
       MRHS_CUDA_TRY(cudaGetLastError());
       int it = 0;
-      MRHS_TRY(run_bcg<float2>(cx, sb.b32, MRHS_PREC_FP32, sb.f32, sb.e32, target.data(),
+      MRHS_TRY(run_bcg<float2>(cx, sb.b32, p.krylov_prec, sb.f32, sb.e32, target.data(),
                                p.precond != 0, p.precond_prec, lo, hi, p.cheb_order,
                                p.maxiter - total_iters, every, &it, &flag));
       total_iters += it;
       { k_update_x<<<g, kThreads, 0, s>>>(X, sb.e32, sb.rho_d, cx.N, R); ::mrhs::count_launch(); }
       MRHS_CUDA_TRY(cudaGetLastError());
       MRHS_TRY(true_residual());
+      if (info && cycles < MRHS_MAX_CYCLES) {
+        info->cycle_iters[cycles] = it;
+        info->cycle_resid[cycles] = max_rel();
+        info->cycle_flag[cycles] = flag;
+      }
       if (flag & 4) break;
     }
   }
@@ -733,11 +765,13 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     info->iters = total_iters;
     info->cycles = cycles;
     info->nrhs = R;
-    for (int i = 0; i < 4; ++i) info->applies[i] = cx.applies[i];
+    for (int i = 0; i < MRHS_NUM_PREC; ++i) info->applies[i] = cx.applies[i];
     for (int j = 0; j < MRHS_MAX_RHS; ++j)
       info->resid[j] = j < R ? (bnorm[j] > 0 ? rnorm[j] / bnorm[j] : 0.0) : 0.0;
     info->cheb_lo = lo;
     info->cheb_hi = hi;
+    info->krylov_prec = mixed ? p.krylov_prec : MRHS_PREC_FP64;
+    info->precond_prec = p.precond ? p.precond_prec : -1;
   }
   MRHS_CUDA_TRY(cudaStreamSynchronize(s));
   if (info)

@@ -147,5 +147,20 @@ __device__ __forceinline__ void tmem_ld32_sync(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// AND of `pred` over the 128 threads of the four epilogue warps (named
+// barrier 1); every one of them must call it.
+__device__ __forceinline__ bool epilogue_all(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return r != 0;
+}
+
 }  // namespace ptx
 }  // namespace mrhs

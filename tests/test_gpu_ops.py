@@ -66,21 +66,43 @@ TC_SHAPES = [((4, 3, 2, 3), 16, 81, 8), ((2, 2, 2, 2), 3, 9, 1), ((3, 3, 3, 3), 
              ((3, 3, 2, 2), 48, 81, 12), ((2, 2, 2, 2), 64, 9, 16), ((5, 1, 1, 1), 8, 9, 3)]
 
 
-@pytest.mark.parametrize("kind", ["bf16", "fp16"])
+@pytest.mark.parametrize("kind", ["bf16", "fp16", "fp16x", "tc32"])
 @pytest.mark.parametrize("L,nb,npts,R", TC_SHAPES)
 def test_tensor_core_op(mrhs, kind, L, nb, npts, R):
     disp, _ = stencil(npts)
     A = coarse_op(L, nb, npts, 4242 + nb, 12.0)
     X = vectors(L, nb, R, 4243)
     op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", kind))
+    if kind in ("fp16x", "tc32") and R > 32:
+        with pytest.raises(mrhs.MrhsError):
+            op.apply(dev(X.astype(np.complex64)), kind)
+        return
     Y = op.apply(dev(X.astype(np.complex64)), kind).cpu().numpy()
     assert mrhs.device_error() == 0
     ref = lowprec_apply(A, X, L, disp, kind)
     assert rel_per_rhs(Y, ref) <= 1e-5
     # against the unquantised FP64 operator: the quantisation error itself
     exact = coarse_op_apply(A, X, L, disp)
-    bound = 2.0 ** -6 if kind == "bf16" else 2.0 ** -9
+    bound = {"bf16": 2.0 ** -6, "fp16": 2.0 ** -9, "fp16x": 2.0 ** -9, "tc32": 2.0 ** -17}[kind]
     assert rel_per_rhs(Y, exact) <= bound
+
+
+def test_fp16x_is_linear_and_tc32_is_fp32_class(mrhs):
+    L, nb, npts, R = (4, 3, 2, 2), 32, 81, 16
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 999, 18.0)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp16", "fp16x", "tc32", "fp32"))
+    X1 = dev(vectors(L, nb, R, 1).astype(np.complex64))
+    X2 = dev(vectors(L, nb, R, 2).astype(np.complex64))
+    def nonlin(kind):
+        lhs = op.apply(0.37 * X1 + X2, kind)
+        rhs = 0.37 * op.apply(X1, kind) + op.apply(X2, kind)
+        return float(torch.linalg.norm(lhs - rhs) / torch.linalg.norm(rhs))
+    assert nonlin("fp16x") < 1e-5 < nonlin("fp16")
+    exact = coarse_op_apply(A, X1.cpu().numpy().astype(np.complex128), L, disp)
+    e32 = rel_per_rhs(op.apply(X1, "tc32").cpu().numpy(), exact)
+    ef = rel_per_rhs(op.apply(X1, "fp32").cpu().numpy(), exact)
+    assert e32 <= 1e-5 and ef <= 1e-5
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp16"])
@@ -214,7 +236,7 @@ def test_solve_fp64_small(mrhs):
     c = (ev[-1] - 1e3 * ev[0]) / (1e3 - 1)
     A = coarse_op(L, nb, npts, 77, c)
     B = vectors(L, nb, R, 78)
-    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "bf16", "fp16"))
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "bf16", "fp16", "fp16x"))
     X, info = op.solve(dev(B), tol=1e-10, maxiter=1000)
     X = X.cpu().numpy()
     H = dense_matrix(A, L, disp)
@@ -228,7 +250,7 @@ def test_solve_fp64_small(mrhs):
     Xp, ip = op.solve(dev(B), tol=1e-10, precond=1, precond_prec="fp64", cheb_hi=1.1 * ev[-1] + c,
                       cheb_lo=0.1, cheb_order=8)
     assert max(ip["resid"]) <= 1e-10 and ip["iters"] < info["iters"]
-    for kind in ("fp16", "bf16", "fp32"):
+    for kind in ("fp16", "bf16", "fp32", "fp16x"):
         Xm, im = op.solve(dev(B), mode="mixed", tol=1e-10, precond=1, precond_prec=kind,
                           cheb_hi=1.1 * ev[-1] + c, cheb_lo=0.2, cheb_order=8)
         assert max(im["resid"]) <= 1e-10, (kind, im)
@@ -308,3 +330,18 @@ def test_lambda_max_and_auto_interval(mrhs):
     B = vectors(L, nb, R, 314)
     X, info = op.solve(dev(B), mode="mixed", tol=1e-9, precond=1, precond_prec="fp16")
     assert max(info["resid"]) <= 1e-9 and info["cheb_hi"] >= ev[-1]
+
+
+def test_mixed_solve_automatic_precisions(mrhs):
+    """With every form built, the mixed solve picks TC32 in the Krylov loop
+    and FP16X in the preconditioner for <= 32 RHS, FP32/FP16 above."""
+    L, nb, npts = (3, 2, 2, 2), 8, 81
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 4321, 18.0)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "fp16", "fp16x", "tc32"))
+    for R, kp, pp in ((8, "tc32", "fp16x"), (40, "fp32", "fp16")):
+        B = vectors(L, nb, R, 4322)
+        X, info = op.solve(dev(B), mode="mixed", tol=1e-9)
+        assert max(info["resid"]) <= 1e-9, info
+        assert (info["krylov_prec"], info["precond_prec"]) == (kp, pp)
+        assert info["applies"][kp] > 0 and info["applies"][pp] > 0

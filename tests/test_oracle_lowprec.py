@@ -77,3 +77,36 @@ def test_quantised_operator_error():
         assert err <= 2.0 ** -(bits - 4)
         if kind == "fp32":
             assert np.allclose(Yq, coarse_op_apply(Aq, Xq, L, disp))
+
+
+def test_split16_two_terms(rng):
+    from oracle.lowprec import split16
+    u = rng.uniform(-1, 1, 100000) * 10.0 ** rng.integers(-3, 1, 100000)
+    u32 = u.astype(np.float32).astype(np.float64)
+    hi, lo = split16(u)
+    assert np.array_equal(hi, u32.astype(np.float16).astype(np.float64))
+    rel = np.abs(hi + 2.0 ** -11 * lo - u32) / np.abs(u32)
+    assert np.max(rel[np.abs(u32) > 2.0 ** -10]) <= 2.0 ** -21
+
+
+def test_split_operators_accuracy():
+    """fp16x is linear in X to ~2^-22 (its error is the fp16 coefficients');
+    tc32 reaches FP32-class accuracy."""
+    L, nb, npts, R = (3, 2, 2, 3), 8, 81, 4
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 23, 9.0)
+    X = vectors(L, nb, R, 23)
+    Y = coarse_op_apply(A, X, L, disp)
+    e16 = np.linalg.norm(lowprec_apply(A, X, L, disp, "fp16") - Y) / np.linalg.norm(Y)
+    e16x = np.linalg.norm(lowprec_apply(A, X, L, disp, "fp16x") - Y) / np.linalg.norm(Y)
+    e32 = np.linalg.norm(lowprec_apply(A, X, L, disp, "tc32") - Y) / np.linalg.norm(Y)
+    assert e16x <= e16 and e16x <= 2.0 ** -9
+    assert e32 <= 2.0 ** -19
+    # linearity in X: fp16x(a X1 + X2) vs a fp16x(X1) + fp16x(X2)
+    X2 = vectors(L, nb, R, 24)
+    lhs = lowprec_apply(A, 0.37 * X + X2, L, disp, "fp16x")
+    rhs = 0.37 * lowprec_apply(A, X, L, disp, "fp16x") + lowprec_apply(A, X2, L, disp, "fp16x")
+    lin16 = np.linalg.norm(lowprec_apply(A, 0.37 * X + X2, L, disp, "fp16")
+                           - 0.37 * lowprec_apply(A, X, L, disp, "fp16")
+                           - lowprec_apply(A, X2, L, disp, "fp16")) / np.linalg.norm(rhs)
+    assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) <= 2.0 ** -19 < lin16
