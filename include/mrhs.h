@@ -107,6 +107,17 @@ int coarse_op_apply(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nr
 int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
                         void* stream);
 
+/* GA_p(x) = alpha * sum_r G(x)[a][r] conj(X(x + delta_p)[b][r]): the
+ * coefficient-shaped outer product that gives the adjoints of the operator
+ * (grad A = grad Y X^dagger on the stencil, alpha = 1) and of the solve
+ * (grad A = -grad B X^dagger, alpha = -1), from dY = dA X + A dX with
+ * Y(x) = sum_p A_p(x) X(x + delta_p) (Sec. 2.6).
+ *   G, X   device [V][nb][nrhs], both complex128 or both complex64 (dtype)
+ *   GA     device complex128 [V][npts][nb][nb] (written), FP64 accumulation
+ * Asynchronous. */
+int coarse_op_outer(mrhs_op op, const void* G, const void* X, void* GA, double alpha,
+                    int32_t nrhs, int32_t dtype, void* stream);
+
 /* G = X^dagger Y, the nrhs_x x nrhs_y block inner product of block CG
  * (Fig. 2: D^dagger Z, T^dagger t, ...; Sec. 3.5 and Table 6, the "ThinQR" Gram).
  *   X [N][rx], Y [N][ry] of element type dtype (MRHS_C128 or MRHS_C64)

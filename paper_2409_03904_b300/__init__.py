@@ -13,7 +13,7 @@ import torch
 from . import _lib
 from ._lib import C64, C128, PREC, SOLVE_FP64, SOLVE_MIXED, MrhsError, SolveInfo, SolveParams
 
-__all__ = ["CoarseOp", "block_inner", "block_axpy", "herm_factor", "MrhsError", "PREC",
+__all__ = ["CoarseOp", "coarse_apply", "coarse_solve", "block_inner", "block_axpy", "herm_factor", "MrhsError", "PREC",
            "SOLVE_FP64", "SOLVE_MIXED", "device_error", "version"]
 
 
@@ -93,6 +93,19 @@ class CoarseOp:
         """Y = H^dagger X in precision `prec`."""
         l = _lib.lib()
         return self._apply(lambda *a: _lib.check(l.coarse_op_apply_dag(*a)), X, prec, out)
+
+    def outer(self, G, X, alpha=1.0):
+        """alpha * G(x) X(x + delta_p)^dagger on the stencil: complex128
+        [V][npts][nb][nb] (the coefficient adjoint)."""
+        if G.dtype != X.dtype or G.shape != X.shape:
+            raise TypeError("G and X must have the same dtype and shape")
+        GA = torch.empty((self.V, self.npts, self.nb, self.nb), dtype=torch.complex128,
+                         device=G.device)
+        _lib.check(_lib.lib().coarse_op_outer(self._h, _lib.dev_ptr(G, None, "G"),
+                                              _lib.dev_ptr(X, None, "X"), _lib.dev_ptr(GA),
+                                              float(alpha), int(G.shape[2]), _dtype_code(G),
+                                              _lib.stream_ptr()))
+        return GA
 
     def lambda_max(self, prec="fp32", iters=40):
         """Power-method estimate of the largest eigenvalue (cached on the op)."""
@@ -199,3 +212,6 @@ def herm_factor(G, tau=1e-12):
     _lib.check(_lib.lib().herm_factor(_lib.dev_ptr(G), _lib.dev_ptr(S), _lib.dev_ptr(W),
                                       _lib.dev_ptr(rank), r, float(tau), _lib.stream_ptr()))
     return S, W, int(rank.item())
+
+
+from .autograd import coarse_apply, coarse_solve  # noqa: E402

@@ -67,6 +67,7 @@ SIGNATURES = {
     "coarse_op_apply": [P, I32, P, P, I32, P],
     "coarse_op_apply_dag": [P, I32, P, P, I32, P],
     "block_inner": [P, P, P, I64, I32, I32, I32, P],
+    "coarse_op_outer": [P, P, P, P, D, I32, I32, P],
     "block_inner_noalloc": [P, P, P, I64, I32, I32, I32, P],
     "block_axpy": [P, P, P, D, I64, I32, I32, I32, P],
     "herm_factor": [P, P, P, P, I32, D, P],  # rank: device int32*

@@ -309,6 +309,20 @@ int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_
   return apply_common(op, prec, X, Y, nrhs, stream, true);
 }
 
+int coarse_op_outer(mrhs_op op, const void* G, const void* X, void* GA, double alpha,
+                    int32_t nrhs, int32_t dtype, void* stream) {
+  MRHS_TRY(check_op(op));
+  MRHS_TRY(check_vec(G, "G"));
+  MRHS_TRY(check_vec(X, "X"));
+  MRHS_TRY(check_vec(GA, "GA"));
+  if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
+  if (dtype != MRHS_C128 && dtype != MRHS_C64) return fail(MRHS_ERR_INVALID_ARG, "dtype");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != op->device) return fail(MRHS_ERR_INVALID_ARG, "operator lives on another device");
+  return outer(op, G, X, (double2*)GA, alpha, nrhs, dtype, (cudaStream_t)stream);
+}
+
 int block_inner(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
                 int32_t dtype, void* stream) {
   if (N < 0 || rx < 1 || ry < 1 || rx > MRHS_MAX_RHS || ry > MRHS_MAX_RHS)

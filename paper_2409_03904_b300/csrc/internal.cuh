@@ -142,6 +142,10 @@ int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* 
           int R, cudaStream_t s);
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam);
 
+// grad.cu
+int outer(const mrhs_op_s* op, const void* G, const void* X, double2* GA, double alpha, int R,
+          int dtype, cudaStream_t s);
+
 // generic apply dispatch (api.cu)
 int op_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
              cudaStream_t s);
