@@ -208,6 +208,9 @@ typedef struct {
   int32_t krylov_prec;  /* MIXED: operator precision inside the inner Krylov loop,
                            MRHS_PREC_FP32 or MRHS_PREC_TC32; -1 (default): TC32
                            if built and nrhs <= 32, else FP32 */
+  int32_t use_graph;    /* 1 (default): after a first uncaptured iteration, each
+                           chunk of check_every block-CG iterations is captured
+                           once as a CUDA graph and replayed */
 } mrhs_solve_params;
 
 enum {

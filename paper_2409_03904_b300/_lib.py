@@ -35,7 +35,8 @@ class SolveParams(ctypes.Structure):
                 ("cheb_order", ctypes.c_int32), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_cycles", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("breakdown_tau", ctypes.c_double), ("krylov_prec", ctypes.c_int32)]
+                ("breakdown_tau", ctypes.c_double), ("krylov_prec", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

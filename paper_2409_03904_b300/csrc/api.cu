@@ -20,6 +20,8 @@ int fail(int code, const std::string& msg) {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return (int64_t)g_launches.load(); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void timer_mark(mrhs_op_s* op, int prec, cudaStream_t s) {
   KernelTimer& t = op->timer[prec];
@@ -441,6 +443,7 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->precond = mode == MRHS_SOLVE_MIXED ? 1 : 0;
   p->precond_prec = -1;
   p->krylov_prec = -1;
+  p->use_graph = 1;
   p->cheb_order = 8;
   p->cheb_lo = 0.0;
   p->cheb_hi = 0.0;

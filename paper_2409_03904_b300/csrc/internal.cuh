@@ -110,6 +110,8 @@ struct mrhs_op_s {
 namespace mrhs {
 
 void count_launch();
+int64_t launch_count();
+void add_launches(int64_t n);   // kernels launched by a graph replay
 void timer_mark(mrhs_op_s* op, int prec, cudaStream_t s);   // call before and after
 
 // op_simt.cu

@@ -360,6 +360,7 @@ struct Ctx {
   double2* gpart = nullptr;   // Gram partials
   double* npart = nullptr;    // column-norm partials
   int64_t applies[MRHS_NUM_PREC] = {0, 0, 0, 0, 0, 0};
+  bool use_graph = true;
   // bump allocation from one grow-only operator-owned workspace: a first
   // pass with base == nullptr only sums the sizes
   char* base = nullptr;
@@ -517,7 +518,9 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
   double best = 1e300;
   std::vector<double> est(cx.R);
   const int stall_checks = check_every > 0 ? (32 + check_every - 1) / check_every : 0;
-  for (it = 1; it <= maxiter; ++it) {
+  // one block-CG iteration (Fig. 2): fixed launches on fixed buffers, so a
+  // chunk of `check_every` of them can be captured once as a CUDA graph
+  auto body = [&]() -> int {
     MRHS_TRY(cx.apply(prec, D, z));                                            // z = H D
     if (precond) MRHS_TRY(cheb_run<C>(cx, pprec, lo, hi, order, z, b.Zz, b.cw, b.c1, b.c2));
     MRHS_TRY(cx.gram<C>(D, z, cx.st->G));                                      // D^dag z
@@ -533,28 +536,88 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
     }
     MRHS_TRY(cx.small_launch(2, precond ? 1 : 0));                             // S, W, C = S C
     MRHS_TRY(cx.rotate<C>(q, precond ? Q : nullptr, D));                       // q, Q, D
-    if (it % check_every == 0 || it == maxiter) {
-      MRHS_CUDA_TRY(cudaMemcpyAsync(&flag, &cx.st->flag, sizeof(int), cudaMemcpyDeviceToHost, cx.s));
-      MRHS_CUDA_TRY(cudaMemcpyAsync(est.data(), cx.st->est, sizeof(double) * cx.R,
-                                    cudaMemcpyDeviceToHost, cx.s));
-      MRHS_CUDA_TRY(cudaStreamSynchronize(cx.s));
-      if (flag & (1 | 4)) break;
-      // stagnation: the worst column's distance to its target has not shrunk
-      // by 30% over `stall_checks` reads (a low-precision preconditioner is
-      // not exactly linear, so the recurrences can plateau above the target;
-      // the caller then restarts from the true residual)
-      double worst = 0.0;
-      for (int j = 0; j < cx.R; ++j)
-        if (target_host[j] > 0.0) worst = std::fmax(worst, est[j] / target_host[j]);
-      if (worst < 0.7 * best) {
-        best = worst;
-        stalled = 0;
-      } else if (stall_checks > 0 && ++stalled >= stall_checks) {
-        flag |= 8;
-        break;
+    return MRHS_OK;
+  };
+  bool timing = false;
+  for (const auto& t : cx.op->timer) timing = timing || t.on;
+  bool graph_ok = cx.use_graph && !timing && check_every > 1;
+  int64_t graph_launches = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_applies[MRHS_NUM_PREC] = {0, 0, 0, 0, 0, 0};
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  };
+  it = 0;
+  while (it < maxiter) {
+    const int chunk = (maxiter - it) < check_every ? (maxiter - it) : check_every;
+    if (graph_ok && it >= 1 && chunk == check_every) {
+      if (!exec) {
+        // workspaces were sized by the iterations already run uncaptured;
+        // if capture or instantiation fails the chunk runs uncaptured instead
+        int64_t before[MRHS_NUM_PREC];
+        for (int i = 0; i < MRHS_NUM_PREC; ++i) before[i] = cx.applies[i];
+        const int64_t l0 = launch_count();
+        cudaGraph_t gr = nullptr;
+        int st = cudaStreamBeginCapture(cx.s, cudaStreamCaptureModeThreadLocal) == cudaSuccess
+                     ? MRHS_OK : MRHS_ERR_CUDA;
+        for (int j = 0; j < chunk && st == MRHS_OK; ++j) st = body();
+        const cudaError_t ce = cudaStreamEndCapture(cx.s, &gr);
+        const bool ok = st == MRHS_OK && ce == cudaSuccess && gr &&
+                        cudaGraphInstantiate(&exec, gr, 0) == cudaSuccess;
+        if (gr) cudaGraphDestroy(gr);
+        for (int i = 0; i < MRHS_NUM_PREC; ++i) {
+          graph_applies[i] = cx.applies[i] - before[i];
+          cx.applies[i] = before[i];
+        }
+        graph_launches = launch_count() - l0;
+        add_launches(-graph_launches);
+        if (!ok) {
+          cudaGetLastError();
+          if (exec) cudaGraphExecDestroy(exec);
+          exec = nullptr;
+          graph_ok = false;
+          continue;   // nothing of the chunk ran: redo it uncaptured
+        }
+      }
+      const cudaError_t le = cudaGraphLaunch(exec, cx.s);
+      if (le != cudaSuccess) {
+        cleanup();
+        return fail(MRHS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(le));
+      }
+      for (int i = 0; i < MRHS_NUM_PREC; ++i) cx.applies[i] += graph_applies[i];
+      add_launches(graph_launches);
+    } else {
+      for (int j = 0; j < chunk; ++j) {
+        const int st = body();
+        if (st != MRHS_OK) {
+          cleanup();
+          return st;
+        }
       }
     }
+    it += chunk;
+    MRHS_CUDA_TRY(cudaMemcpyAsync(&flag, &cx.st->flag, sizeof(int), cudaMemcpyDeviceToHost, cx.s));
+    MRHS_CUDA_TRY(cudaMemcpyAsync(est.data(), cx.st->est, sizeof(double) * cx.R,
+                                  cudaMemcpyDeviceToHost, cx.s));
+    MRHS_CUDA_TRY(cudaStreamSynchronize(cx.s));
+    if (flag & (1 | 4)) break;
+    // stagnation: the worst column's distance to its target has not shrunk
+    // by 30% over `stall_checks` reads (a low-precision preconditioner is
+    // not exactly linear, so the recurrences can plateau above the target;
+    // the caller then restarts from the true residual)
+    double worst = 0.0;
+    for (int j = 0; j < cx.R; ++j)
+      if (target_host[j] > 0.0) worst = std::fmax(worst, est[j] / target_host[j]);
+    if (worst < 0.7 * best) {
+      best = worst;
+      stalled = 0;
+    } else if (stall_checks > 0 && ++stalled >= stall_checks) {
+      flag |= 8;
+      break;
+    }
   }
+  cleanup();
   if (it > maxiter) it = maxiter;
   *iters = it;
   *flag_out = flag;
@@ -640,6 +703,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
   cx.R = R;
   cx.N = op->V * op->nb;
   cx.tau = p.breakdown_tau > 0 ? p.breakdown_tau : 1e-12;
+  cx.use_graph = p.use_graph != 0;
   const int64_t n = cx.N * R;
   const int g = grid_for(n);
   const bool mixed = p.mode == MRHS_SOLVE_MIXED;

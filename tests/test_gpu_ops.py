@@ -345,3 +345,27 @@ def test_mixed_solve_automatic_precisions(mrhs):
         assert max(info["resid"]) <= 1e-9, info
         assert (info["krylov_prec"], info["precond_prec"]) == (kp, pp)
         assert info["applies"][kp] > 0 and info["applies"][pp] > 0
+
+
+def test_graph_replay_matches_eager(mrhs):
+    """Block-CG chunks captured as CUDA graphs give the same iterates as the
+    eager launches (same kernels, same order)."""
+    L, nb, npts, R = (4, 3, 2, 3), 16, 81, 8
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 555, 18.0)
+    B = vectors(L, nb, R, 556)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "fp16", "fp16x", "tc32"))
+    op.lambda_max("fp16x", 40)      # cached: both solves below reuse it
+    for mode in ("fp64", "mixed"):
+        kw = dict(mode=mode, tol=1e-9, maxiter=400, check_every=4)
+        if mode == "mixed":
+            kw.update(precond=1, cheb_order=8)
+        n0 = mrhs.launch_count()
+        Xg, ig = op.solve(dev(B), use_graph=1, **kw)
+        n1 = mrhs.launch_count()
+        Xe, ie = op.solve(dev(B), use_graph=0, **kw)
+        n2 = mrhs.launch_count()
+        assert torch.equal(Xg, Xe), mode
+        assert ig["iters"] == ie["iters"] and ig["applies"] == ie["applies"]
+        assert n1 - n0 == n2 - n1          # replays are counted as launches
+        assert max(ig["resid"]) <= 1e-9
