@@ -3,15 +3,19 @@
 precision vs plain FP64) and the coarse operator's TFLOP/s at 32 RHS.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME]
+                    [--workload NAME] [--op PREC [--lattice a,b,c,d]]
 
 Workload (default): 12^4 coarse lattice, nb = 48, 81-point stencil, 32
 right-hand sides, condition ~1e4, synthetic seeded operator and sources
 (see synth/).  One step = one complete mixed-precision solve to a true FP64
 relative residual of 1e-8 on every RHS: FP64 outer defect correction (true
-residual, Gram accumulation, Cholesky, solution update), complex64 inner
-Chebyshev-preconditioned block CG with the FP32 operator, FP16 tensor-core
-Chebyshev preconditioner.  value = ms per RHS (lower is better).
+residual, solution update), complex64 inner block CG with the TC32
+tensor-core operator and a degree-8 Chebyshev preconditioner applied with the
+FP16X tensor-core operator.  value = ms per RHS (lower is better).
+
+--op PREC: one step = one application of the coarse operator in precision
+PREC at the workload's shape (optionally on another lattice, same per-site
+work); value = TFLOP/s (8 nb^2 nrhs npts V flop per application).
 
 Multi-GPU (torchrun): the solve does not shard in this build; every rank
 solves its own independent batch of right-hand sides against its own copy of
@@ -54,6 +58,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the standalone operator, FP64 and e2e measurements")
     ap.add_argument("--cpu-sites", type=int, default=96, help="oracle sample size (sites)")
+    ap.add_argument("--op", default=None, choices=["fp64", "fp32", "bf16", "fp16", "fp16x", "tc32"],
+                    help="time the coarse operator alone in this precision")
+    ap.add_argument("--lattice", default=None, help="a,b,c,d: override the workload's lattice "
+                    "(operator mode; same per-site work)")
     return ap.parse_args()
 
 
@@ -212,6 +220,76 @@ def run_reference(a, w, shift):
 
 
 # ---------------------------------------------------------------- our arm
+def run_op(a, w, shift):
+    """Coarse-operator throughput: K applications of the operator in one
+    precision, inputs resident in HBM (coefficients far larger than L2)."""
+    import torch
+    import paper_2409_03904_b300 as mrhs
+    import synth.device as sdev
+    from synth import stencil
+    if a.lattice:
+        w = dict(w, L=tuple(int(v) for v in a.lattice.split(",")))
+    R, V, nb, prec = w["nrhs"], int(np.prod(w["L"])), w["nb"], a.op
+    disp, _ = stencil(w["npts"])
+    dev = torch.device("cuda", 0)
+    A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
+    op = mrhs.CoarseOp(A, w["L"], disp, (prec,))
+    del A
+    torch.cuda.empty_cache()
+    vdt = torch.complex128 if prec == "fp64" else torch.complex64
+    X = sdev.vectors(w["L"], nb, R, w["seed"], device=dev).to(vdt)
+    Y = torch.empty_like(X)
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        op.apply(X, prec, out=Y)
+    op.kernel_timing(True)
+    l0 = mrhs.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            op.apply(X, prec, out=Y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = mrhs.launch_count() - l0
+    ms = e0.elapsed_time(e1) / a.steps
+    nk, kms = op.kernel_time(prec)
+    op.kernel_timing(False)
+    flops = op_flops(w, R)
+    byts = op_bytes(w, R, prec)
+    hbm, bf16_peak, kind = peaks()
+    per = kms / max(nk, 1)
+    roof = {"bound": "hbm", "achieved": byts / (per * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": byts / (per * 1e-3) / 1e9 / hbm, "traffic": None,
+            "kernel": f"coarse operator ({prec})", "algorithmic_bytes": byts, "launch_ms": per,
+            "launches": nk, "peak_kind": f"{kind} copy bandwidth"}
+    # end to end: host input -> device, apply, device -> host result
+    Xh = X.cpu().pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        Xd = Xh.to(dev, non_blocking=True)
+        op.apply(Xd, prec, out=Y)
+        Yh.copy_(Y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / a.steps
+    out = {"metric": "coarse-op TFLOP/s at Nrhs=%d" % R, "value": flops / (ms * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": prec, "data": "synthetic",
+           "config": {"workload": w["name"] + ("" if not a.lattice else f" on {a.lattice}"),
+                      "L": list(w["L"]), "nb": nb, "npts": w["npts"], "nrhs": R,
+                      "l2": f"inputs larger than L2 ({byts / 1e9:.2f} GB per application)"},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
+           "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                   "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
+                   "d2h_bytes_per_step": Yh.numel() * Yh.element_size()}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     from synth import WORKLOADS, load_shift
@@ -219,6 +297,8 @@ def main():
     shift = load_shift(a.workload)
     if a.impl == "reference":
         return run_reference(a, w, shift)
+    if a.op:
+        return run_op(a, w, shift)
 
     import torch
     import torch.distributed as dist

@@ -41,7 +41,9 @@ enum {
   MRHS_ERR_BREAKDOWN = -4,     /* block Gram not positive (solve only) */
   MRHS_ERR_NONFINITE = -5,     /* NaN/Inf met in the solve */
   MRHS_ERR_UNSUPPORTED = -6,   /* precision not built into this operator */
-  MRHS_ERR_NO_MEMORY = -7      /* device allocation failed */
+  MRHS_ERR_NO_MEMORY = -7,     /* device allocation failed */
+  MRHS_ERR_DEVICE = -8         /* a kernel's bounded wait expired, or a device
+                                  self-check failed (mrhs_device_error) */
 };
 
 /* Operator precisions (coefficients and arithmetic of one application). */
@@ -71,6 +73,7 @@ enum { MRHS_C128 = 0, MRHS_C64 = 1 };
 #define MRHS_MAX_RHS 64
 #define MRHS_MAX_PTS 81
 #define MRHS_MAX_CYCLES 16
+#define MRHS_MAX_BATCH 16
 
 typedef struct mrhs_op_s* mrhs_op;
 
@@ -249,6 +252,34 @@ typedef struct {
 int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
                    const mrhs_solve_params* params, mrhs_solve_info* info, void* stream);
 
+/* Many independent operators in ONE persistent tensor-core launch: the work
+ * list covers every site of every problem (uneven lattices, nb and nrhs
+ * allowed), each problem keeps its own inputs, scales and packed images.
+ *   ops    host array of n (1..MRHS_MAX_BATCH) distinct operators on the
+ *          current device, all built with precision `prec` (BF16, FP16,
+ *          FP16X or TC32)
+ *   X, Y   host arrays of n device pointers ([V_i][nb_i][nrhs_i] complex64)
+ *   nrhs   host array of n counts
+ * Asynchronous. */
+int mrhs_batch_apply(const mrhs_op* ops, int32_t n, int32_t prec, const void* const* X,
+                     void* const* Y, const int32_t* nrhs, void* stream);
+
+/* Solve n independent systems H_i X_i = B_i side by side.  With
+ * MRHS_SOLVE_MIXED, precond = 1, nrhs_i <= 32 and TC32 plus a tensor-core
+ * preconditioner precision built into every operator, the problems advance in
+ * lockstep: each operator step (Krylov and Chebyshev) of an iteration is one
+ * persistent launch over all still-active problems, chunks of check_every
+ * iterations are captured once as a CUDA graph, and a problem that reaches
+ * its inner target leaves the launches through a device mask.  Otherwise the
+ * problems are solved one after another with block_cg_solve.
+ *   B, X   host arrays of n device pointers (complex128 [V_i][nb_i][nrhs_i])
+ *   info   host array of n records (may be NULL)
+ * Returns MRHS_OK if every problem converged, else the first failure code
+ * (all X and info are still written).  Synchronises `stream`. */
+int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* const* X,
+                     const int32_t* nrhs, const mrhs_solve_params* params, mrhs_solve_info* info,
+                     void* stream);
+
 /* Default parameters for `mode`. */
 void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode);
 
@@ -276,6 +307,38 @@ int mrhs_op_kernel_timing(mrhs_op op, int32_t enable);
  * do not fit shared memory fall back to fewer points per stage.  Results do
  * not depend on the shape. */
 int mrhs_op_tc_tune(mrhs_op op, int32_t pts_per_stage, int32_t ctas_per_sm, int32_t max_stages);
+
+/* Launch-shape autotuner for the tensor-core kernel (the three knobs of
+ * mrhs_op_tc_tune).  mrhs_autotune times candidate shapes for the `n`
+ * operators ops[0..n-1] (n = 1: one operator; n > 1: their batched launch, as
+ * mrhs_batch_apply makes it) in precision `prec` (BF16..TC32) at nrhs[i]
+ * right-hand sides, on scratch inputs it allocates and frees itself: first
+ * points per stage {built-in, 1, 2, 3, 4, 6, 8, 12} x CTAs per SM {1, 2} at
+ * the deepest ring, then ring depths {2, 3, 4, 6, 8, 12, 16} for the best of
+ * those.  Each candidate is timed over `reps` launches (<= 0: 3) after one
+ * warm-up, with CUDA events on `stream`; every candidate's output must equal
+ * the first one's bit for bit, else MRHS_ERR_DEVICE.  The winner is stored in
+ * a process-wide cache keyed, per problem, on (SM count, V, nb, stencil
+ * points, nrhs, prec); every later launch of exactly that shape (or list of
+ * shapes, for a batch) without an explicit mrhs_op_tc_tune uses it.  `out`
+ * (host, may be NULL) receives the winner, the number of candidates timed and
+ * the best and built-in default times in ms per launch.  Synchronises
+ * `stream`; MRHS_ERR_INVALID_ARG if `stream` is being captured into a graph.
+ * mrhs_autotune_save / _load write / merge the cache as text, one entry per
+ * line ("n", n x "sms V nb npts nrhs prec", "pps ctas stages ms"); a malformed
+ * file is rejected whole (MRHS_ERR_INVALID_ARG).  mrhs_autotune_entries
+ * returns the number of cached shapes; mrhs_autotune_clear empties the cache.
+ * The cache calls are host-only and thread-safe. */
+typedef struct {
+  int32_t pts_per_stage, ctas_per_sm, max_stages, candidates;
+  double ms, ms_default;
+} mrhs_tune_result;
+int mrhs_autotune(const mrhs_op* ops, int32_t n, int32_t prec, const int32_t* nrhs, int32_t reps,
+                  mrhs_tune_result* out, void* stream);
+int mrhs_autotune_save(const char* path);
+int mrhs_autotune_load(const char* path);
+int64_t mrhs_autotune_entries(void);
+void mrhs_autotune_clear(void);
 int mrhs_op_kernel_time(mrhs_op op, int32_t prec, int64_t* launches, double* ms);
 int64_t mrhs_launch_count(void);
 

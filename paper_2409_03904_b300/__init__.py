@@ -6,6 +6,7 @@ A[x][p][a][b] complex128; vectors [V][nb][nrhs] (RHS fastest), complex128
 for FP64 and complex64 for the FP32/BF16/FP16 operators.
 """
 import ctypes
+import os
 
 import numpy as np
 import torch
@@ -13,7 +14,9 @@ import torch
 from . import _lib
 from ._lib import C64, C128, PREC, SOLVE_FP64, SOLVE_MIXED, MrhsError, SolveInfo, SolveParams
 
-__all__ = ["CoarseOp", "coarse_apply", "coarse_solve", "block_inner", "block_axpy", "herm_factor", "MrhsError", "PREC",
+__all__ = ["CoarseOp", "coarse_apply", "coarse_solve", "batch_apply", "batch_solve", "autotune",
+           "autotune_save", "autotune_load", "autotune_entries", "autotune_clear", "block_inner",
+           "block_axpy", "herm_factor", "MrhsError", "PREC",
            "SOLVE_FP64", "SOLVE_MIXED", "device_error", "version"]
 
 
@@ -164,6 +167,82 @@ class CoarseOp:
         if code not in (0, -3) or (code == -3 and raise_on_fail):
             _lib.check(code)
         return X, info.as_dict()
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def autotune(ops, prec, nrhs, reps=3):
+    """Time launch shapes of the tensor-core kernel for `ops` (one operator,
+    or a list solved as one batched launch) at `nrhs` right-hand sides (an
+    int, or one per operator); cache and return the winner as a dict."""
+    if isinstance(ops, CoarseOp):
+        ops = [ops]
+    if isinstance(nrhs, int):
+        nrhs = [nrhs] * len(ops)
+    l = _lib.lib()
+    hs = (ctypes.c_void_p * len(ops))(*[o._h.value for o in ops])
+    R = (ctypes.c_int32 * len(ops))(*[int(r) for r in nrhs])
+    res = _lib.TuneResult()
+    _lib.check(l.mrhs_autotune(hs, len(ops), PREC[prec], R, int(reps), ctypes.byref(res),
+                               _lib.stream_ptr()))
+    return res.as_dict()
+
+
+def autotune_save(path):
+    """Write the launch-shape cache to a text file."""
+    _lib.check(_lib.lib().mrhs_autotune_save(os.fsencode(path)))
+
+
+def autotune_load(path):
+    """Merge a saved launch-shape cache into this process's cache."""
+    _lib.check(_lib.lib().mrhs_autotune_load(os.fsencode(path)))
+
+
+def autotune_entries():
+    return int(_lib.lib().mrhs_autotune_entries())
+
+
+def autotune_clear():
+    _lib.lib().mrhs_autotune_clear()
+
+
+def batch_apply(ops, Xs, prec="fp16"):
+    """One persistent launch applying each ops[i] to Xs[i] (complex64)."""
+    dt = _lib.vec_dtype(prec)
+    Ys = [torch.empty_like(X) for X in Xs]
+    for X in Xs:
+        _lib.dev_ptr(X, dt, "X")
+    hs = (ctypes.c_void_p * len(ops))(*[o._h.value for o in ops])
+    R = (ctypes.c_int32 * len(ops))(*[int(X.shape[2]) for X in Xs])
+    _lib.check(_lib.lib().mrhs_batch_apply(hs, len(ops), PREC[prec], _ptr_array(Xs),
+                                           _ptr_array(Ys), R, _lib.stream_ptr()))
+    return Ys
+
+
+def batch_solve(ops, Bs, mode="mixed", raise_on_fail=True, **kw):
+    """Solve ops[i] X_i = Bs[i] side by side; returns ([X_i], [info_i])."""
+    l = _lib.lib()
+    p = SolveParams()
+    l.mrhs_solve_params_default(ctypes.byref(p), SOLVE_MIXED if mode == "mixed" else SOLVE_FP64)
+    for k, v in kw.items():
+        if k in ("precond_prec", "krylov_prec") and isinstance(v, str):
+            v = PREC[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    for B in Bs:
+        _lib.dev_ptr(B, torch.complex128, "B")
+    Xs = [torch.zeros_like(B) for B in Bs]
+    infos = (SolveInfo * len(ops))()
+    hs = (ctypes.c_void_p * len(ops))(*[o._h.value for o in ops])
+    R = (ctypes.c_int32 * len(ops))(*[int(B.shape[2]) for B in Bs])
+    code = l.mrhs_batch_solve(hs, len(ops), _ptr_array(Bs), _ptr_array(Xs), R, ctypes.byref(p),
+                              ctypes.cast(infos, ctypes.c_void_p), _lib.stream_ptr())
+    if code not in (0, -3) or (code == -3 and raise_on_fail):
+        _lib.check(code)
+    return Xs, [i.as_dict() for i in infos]
 
 
 def _dtype_code(t):

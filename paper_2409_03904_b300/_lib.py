@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libmrhs.so")
 
 MRHS_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NOT_CONVERGED", -4: "BREAKDOWN", -5: "NONFINITE",
-          -6: "UNSUPPORTED", -7: "NO_MEMORY"}
+          -6: "UNSUPPORTED", -7: "NO_MEMORY", -8: "DEVICE"}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "fp16x": 4, "tc32": 5}
 NAMES = {v: k for k, v in PREC.items()}
 C128, C64 = 0, 1
@@ -59,6 +59,15 @@ class SolveInfo(ctypes.Structure):
                     cycle_flag=[self.cycle_flag[c] for c in range(min(self.cycles, 16))])
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("pts_per_stage", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("max_stages", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("ms", ctypes.c_double), ("ms_default", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 P, I32, I64, D, U32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
                        ctypes.c_uint32)
@@ -83,6 +92,13 @@ SIGNATURES = {
     "mrhs_launch_count": [],
     "mrhs_op_lambda_max": [P, I32, I32, P, P],
     "mrhs_op_tc_tune": [P, I32, I32, I32],
+    "mrhs_batch_apply": [P, I32, I32, P, P, P, P],
+    "mrhs_batch_solve": [P, I32, P, P, P, ctypes.POINTER(SolveParams), P, P],
+    "mrhs_autotune": [P, I32, I32, P, I32, ctypes.POINTER(TuneResult), P],
+    "mrhs_autotune_save": [ctypes.c_char_p],
+    "mrhs_autotune_load": [ctypes.c_char_p],
+    "mrhs_autotune_entries": [],
+    "mrhs_autotune_clear": [],
 }
 
 
@@ -101,6 +117,8 @@ def lib():
         l.mrhs_version.restype = ctypes.c_char_p
         l.mrhs_solve_params_default.restype = None
         l.mrhs_launch_count.restype = ctypes.c_int64
+        l.mrhs_autotune_entries.restype = ctypes.c_int64
+        l.mrhs_autotune_clear.restype = None
         _lib = l
     return _lib
 

@@ -434,6 +434,117 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
   return solve(op, (const double2*)B, (double2*)X, nrhs, pp, info, (cudaStream_t)stream);
 }
 
+int mrhs_autotune(const mrhs_op* ops, int32_t n, int32_t prec, const int32_t* nrhs, int32_t reps,
+                  mrhs_tune_result* out, void* stream) {
+  if (!ops || !nrhs || n < 1 || n > MRHS_MAX_BATCH)
+    return fail(MRHS_ERR_INVALID_ARG, "mrhs_autotune: arguments (1 <= n <= 16)");
+  if (prec < MRHS_PREC_BF16 || prec >= MRHS_NUM_PREC)
+    return fail(MRHS_ERR_UNSUPPORTED, "only the tensor-core kernel has a tuned launch shape");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < n; ++i) {
+    MRHS_TRY(check_op(ops[i]));
+    MRHS_TRY(check_prec(ops[i], prec));
+    if (ops[i]->device != dev) return fail(MRHS_ERR_INVALID_ARG, "operator on another device");
+    if (nrhs[i] < 1 || nrhs[i] > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs[i]");
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == ops[i]) return fail(MRHS_ERR_INVALID_ARG, "an operator appears twice");
+  }
+  return autotune(const_cast<mrhs_op_s* const*>(ops), n, prec, nrhs, reps, out,
+                  (cudaStream_t)stream);
+}
+
+int mrhs_autotune_save(const char* path) {
+  if (!path) return fail(MRHS_ERR_INVALID_ARG, "path");
+  return tune_save(path);
+}
+
+int mrhs_autotune_load(const char* path) {
+  if (!path) return fail(MRHS_ERR_INVALID_ARG, "path");
+  return tune_load(path);
+}
+
+int64_t mrhs_autotune_entries(void) { return tune_entries(); }
+
+void mrhs_autotune_clear(void) { tune_clear(); }
+
+int mrhs_batch_apply(const mrhs_op* ops, int32_t n, int32_t prec, const void* const* X,
+                     void* const* Y, const int32_t* nrhs, void* stream) {
+  if (!ops || !X || !Y || !nrhs || n < 1 || n > MRHS_MAX_BATCH)
+    return fail(MRHS_ERR_INVALID_ARG, "mrhs_batch_apply: arguments (1 <= n <= 16)");
+  if (prec < MRHS_PREC_BF16 || prec >= MRHS_NUM_PREC)
+    return fail(MRHS_ERR_UNSUPPORTED, "batched applications run on the tensor cores only");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < n; ++i) {
+    MRHS_TRY(check_op(ops[i]));
+    MRHS_TRY(check_prec(ops[i], prec));
+    MRHS_TRY(check_vec(X[i], "X[i]"));
+    MRHS_TRY(check_vec(Y[i], "Y[i]"));
+    if (ops[i]->device != dev) return fail(MRHS_ERR_INVALID_ARG, "operator on another device");
+    if (nrhs[i] < 1 || nrhs[i] > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs[i]");
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == ops[i]) return fail(MRHS_ERR_INVALID_ARG, "an operator appears twice (its input workspace is shared)");
+  }
+  return tc_apply_batch(const_cast<mrhs_op_s* const*>(ops), n, prec, X, Y, nrhs, nullptr,
+                        (cudaStream_t)stream);
+}
+
+int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* const* X,
+                     const int32_t* nrhs, const mrhs_solve_params* params, mrhs_solve_info* info,
+                     void* stream) {
+  if (!ops || !B || !X || !nrhs || !params || n < 1 || n > MRHS_MAX_BATCH)
+    return fail(MRHS_ERR_INVALID_ARG, "mrhs_batch_solve: arguments (1 <= n <= 16)");
+  mrhs_solve_params q = *params;
+  bool batched = q.mode == MRHS_SOLVE_MIXED && q.precond;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < n; ++i) {
+    MRHS_TRY(check_op(ops[i]));
+    MRHS_TRY(check_vec(B[i], "B[i]"));
+    MRHS_TRY(check_vec(X[i], "X[i]"));
+    if (ops[i]->device != dev) return fail(MRHS_ERR_INVALID_ARG, "operator on another device");
+    if (nrhs[i] < 1 || nrhs[i] > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs[i]");
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == ops[i]) return fail(MRHS_ERR_INVALID_ARG, "an operator appears twice");
+    const uint32_t m = ops[i]->prec_mask;
+    if (!(m & MRHS_PREC_BIT(MRHS_PREC_FP64))) return fail(MRHS_ERR_UNSUPPORTED, "FP64 operator needed");
+    if (nrhs[i] > 32 || !(m & MRHS_PREC_BIT(MRHS_PREC_TC32))) batched = false;
+  }
+  // the batched path: TC32 in the Krylov loop and a tensor-core preconditioner
+  // shared by all problems; otherwise each problem is solved in turn
+  if (batched) {
+    if (q.krylov_prec < 0) q.krylov_prec = MRHS_PREC_TC32;
+    if (q.precond_prec < 0) {
+      const int order[] = {MRHS_PREC_FP16X, MRHS_PREC_FP16, MRHS_PREC_BF16, MRHS_PREC_TC32};
+      for (int pr : order) {
+        bool all = true;
+        for (int i = 0; i < n; ++i) all = all && (ops[i]->prec_mask & MRHS_PREC_BIT(pr));
+        if (all) { q.precond_prec = pr; break; }
+      }
+    }
+    batched = q.krylov_prec == MRHS_PREC_TC32 && q.precond_prec >= MRHS_PREC_BF16;
+    for (int i = 0; i < n && batched; ++i)
+      batched = (ops[i]->prec_mask & MRHS_PREC_BIT(q.precond_prec)) != 0;
+  }
+  if (batched) {
+    if (!(q.tol > 0.0) || q.maxiter < 1 || q.cheb_order < 0)
+      return fail(MRHS_ERR_INVALID_ARG, "tol / maxiter / cheb_order");
+    for (int i = 0; i < n; ++i)
+      if (B[i] == X[i]) return fail(MRHS_ERR_INVALID_ARG, "X and B must differ");
+    return solve_batch(const_cast<mrhs_op_s* const*>(ops), n, (const double2* const*)B,
+                       (double2* const*)X, nrhs, q, info, (cudaStream_t)stream);
+  }
+  int worst = MRHS_OK;
+  for (int i = 0; i < n; ++i) {
+    const int st = block_cg_solve(ops[i], B[i], X[i], nrhs[i], params, info ? info + i : nullptr,
+                                  stream);
+    if (st != MRHS_OK && st != MRHS_ERR_NOT_CONVERGED) return st;
+    if (st != MRHS_OK && worst == MRHS_OK) worst = st;
+  }
+  return worst;
+}
+
 void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));

@@ -23,57 +23,132 @@ namespace {
 constexpr int kTile = 32;      // rows staged per step
 constexpr int kThreads = 256;
 
-template <typename C>
+// Partial Gram of one row range per CTA.  A thread owns a T x T tile of
+// entries (T = 1, 2 or 4 by the block width, so the tiles number at most 256)
+// and the threads left over form row groups: group g takes rows g, g + G, ...
+// of every staged tile, so all 256 threads work even for a 4 x 4 Gram.
+// Products are summed in the vectors' precision over at most kFlushRows rows
+// per thread and then added into FP64; the groups are summed in a fixed
+// order, so the result is bitwise reproducible.
+constexpr int kFlushRows = 64;
+
+template <typename C, int T>
 __global__ void __launch_bounds__(kThreads)
     k_gram_partial(const C* __restrict__ X, const C* __restrict__ Y, double2* __restrict__ part,
                    int64_t N, int rx, int ry, int64_t rows_per_block) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sX = reinterpret_cast<C*>(smem_raw);
   C* sY = sX + kTile * rx;
-  constexpr int kMaxE = (MRHS_MAX_RHS * MRHS_MAX_RHS) / kThreads;
-  const int ne = rx * ry;
-  double2 acc[kMaxE];
+  const int tx = (rx + T - 1) / T, ty = (ry + T - 1) / T;
+  const int nt = tx * ty;
+  const int G = kThreads / nt;
+  const int tid = threadIdx.x;
+  const int g = tid / nt, et = tid % nt;
+  const bool worker = g < G;
+  const int i0 = (et / ty) * T, j0 = (et % ty) * T;
+  double2 acc[T][T];
+  C sum[T][T];
 #pragma unroll
-  for (int k = 0; k < kMaxE; ++k) acc[k] = make_double2(0.0, 0.0);
+  for (int a = 0; a < T; ++a)
+#pragma unroll
+    for (int b = 0; b < T; ++b) {
+      acc[a][b] = make_double2(0.0, 0.0);
+      sum[a][b] = czero<C>();
+    }
+  int pending = 0;
   const int64_t n0 = (int64_t)blockIdx.x * rows_per_block;
   int64_t n1 = n0 + rows_per_block;
   if (n1 > N) n1 = N;
   for (int64_t t0 = n0; t0 < n1; t0 += kTile) {
     const int rows = (int)((n1 - t0) < kTile ? (n1 - t0) : kTile);
     __syncthreads();
-    for (int i = threadIdx.x; i < rows * rx; i += kThreads) sX[i] = X[t0 * rx + i];
-    for (int i = threadIdx.x; i < rows * ry; i += kThreads) sY[i] = Y[t0 * ry + i];
+    for (int i = tid; i < rows * rx; i += kThreads) sX[i] = X[t0 * rx + i];
+    for (int i = tid; i < rows * ry; i += kThreads) sY[i] = Y[t0 * ry + i];
     __syncthreads();
+    if (!worker) continue;
+    for (int n = g; n < rows; n += G) {
+      C xv[T], yv[T];
 #pragma unroll
-    for (int k = 0; k < kMaxE; ++k) {
-      const int e = threadIdx.x + k * kThreads;
-      if (e < ne) {
-        const int i = e / ry, j = e % ry;
-        C s = czero<C>();
-        for (int n = 0; n < rows; ++n) s = cfma_conj(sX[n * rx + i], sY[n * ry + j], s);
-        acc[k].x += (double)s.x;
-        acc[k].y += (double)s.y;
+      for (int a = 0; a < T; ++a) xv[a] = (i0 + a < rx) ? sX[n * rx + i0 + a] : czero<C>();
+#pragma unroll
+      for (int b = 0; b < T; ++b) yv[b] = (j0 + b < ry) ? sY[n * ry + j0 + b] : czero<C>();
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b) sum[a][b] = cfma_conj(xv[a], yv[b], sum[a][b]);
+      if (++pending == kFlushRows) {
+#pragma unroll
+        for (int a = 0; a < T; ++a)
+#pragma unroll
+          for (int b = 0; b < T; ++b) {
+            acc[a][b].x += (double)sum[a][b].x;
+            acc[a][b].y += (double)sum[a][b].y;
+            sum[a][b] = czero<C>();
+          }
+        pending = 0;
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < kMaxE; ++k) {
-    const int e = threadIdx.x + k * kThreads;
-    if (e < ne) part[(int64_t)blockIdx.x * ne + e] = acc[k];
+  for (int a = 0; a < T; ++a)
+#pragma unroll
+    for (int b = 0; b < T; ++b) {
+      acc[a][b].x += (double)sum[a][b].x;
+      acc[a][b].y += (double)sum[a][b].y;
+    }
+  const int ne = rx * ry;
+  double2* out = part + (int64_t)blockIdx.x * ne;
+  if (G == 1) {
+    if (worker)
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b)
+          if (i0 + a < rx && j0 + b < ry) out[(i0 + a) * ry + j0 + b] = acc[a][b];
+    return;
+  }
+  // groups -> shared memory [G][nt][T][T], then a fixed-order sum per entry
+  __syncthreads();
+  double2* red = reinterpret_cast<double2*>(smem_raw);
+  if (worker)
+#pragma unroll
+    for (int a = 0; a < T; ++a)
+#pragma unroll
+      for (int b = 0; b < T; ++b) red[((g * nt + et) * T + a) * T + b] = acc[a][b];
+  __syncthreads();
+  for (int e = tid; e < nt * T * T; e += kThreads) {
+    const int t = e / (T * T), a = (e / T) % T, b = e % T;
+    const int i = (t / ty) * T + a, j = (t % ty) * T + b;
+    if (i >= rx || j >= ry) continue;
+    double2 v = make_double2(0.0, 0.0);
+    for (int gg = 0; gg < G; ++gg) {
+      const double2 w = red[gg * nt * T * T + e];
+      v.x += w.x;
+      v.y += w.y;
+    }
+    out[i * ry + j] = v;
   }
 }
 
+// Sum of the partial Grams: one warp per entry, lanes striding over the
+// blocks, then a fixed shuffle tree (bitwise reproducible).
 __global__ void k_gram_final(const double2* __restrict__ part, double2* __restrict__ G, int nblk,
                              int ne) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (e >= ne) return;
   double2 s = make_double2(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     const double2 v = part[(int64_t)b * ne + e];
     s.x += v.x;
     s.y += v.y;
   }
-  G[e] = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+  }
+  if (lane == 0) G[e] = s;
 }
 
 template <typename C>
@@ -149,9 +224,9 @@ void Workspace::release() {
 }
 
 int gram_blocks(int64_t N) {
-  const int64_t per = 4096;   // at least this many rows per CTA
+  const int64_t per = 512;    // at least this many rows per CTA
   int64_t nblk = (N + per - 1) / per;
-  const int64_t cap = (int64_t)num_sms() * 4;
+  const int64_t cap = (int64_t)num_sms() * 2;
   if (nblk > cap) nblk = cap;
   if (nblk < 1) nblk = 1;
   return (int)nblk;
@@ -161,38 +236,44 @@ size_t gram_workspace_bytes(int64_t N, int rx, int ry) {
   return (size_t)gram_blocks(N) * rx * ry * sizeof(double2);
 }
 
-int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
-            double2* part, cudaStream_t s) {
-  const int nblk = gram_blocks(N);
-  int64_t per = (N + nblk - 1) / nblk;
-  per = ((per + kTile - 1) / kTile) * kTile;
-  const int ne = rx * ry;
-  if (N == 0) {
-    MRHS_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double2) * ne, s));
-    return MRHS_OK;
-  }
-  if (dtype == MRHS_C128) {
-    const size_t smem = sizeof(double2) * kTile * (rx + ry);
-    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<double2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    { k_gram_partial<double2><<<nblk, kThreads, smem, s>>>((const double2*)X, (const double2*)Y,
-                                                          part, N, rx, ry, per); ::mrhs::count_launch(); }
-  } else {
-    const size_t smem = sizeof(float2) * kTile * (rx + ry);
-    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<float2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    { k_gram_partial<float2><<<nblk, kThreads, smem, s>>>((const float2*)X, (const float2*)Y, part,
-                                                         N, rx, ry, per); ::mrhs::count_launch(); }
-  }
-  MRHS_CUDA_TRY(cudaGetLastError());
-  { k_gram_final<<<(ne + 127) / 128, 128, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
-  MRHS_CUDA_TRY(cudaGetLastError());
+int gram_tile(int rx, int ry) {
+  const int r = rx > ry ? rx : ry;
+  return r <= 8 ? 1 : (r <= 16 ? 2 : 4);
+}
+
+template <typename C, int T>
+int launch_gram(const void* X, const void* Y, double2* part, int64_t N, int rx, int ry,
+                int nblk, int64_t per, cudaStream_t s) {
+  const int nt = ((rx + T - 1) / T) * ((ry + T - 1) / T);
+  const int G = kThreads / nt;
+  const size_t stage = sizeof(C) * kTile * (rx + ry);
+  const size_t red = G > 1 ? sizeof(double2) * (size_t)G * nt * T * T : 0;
+  const size_t smem = stage > red ? stage : red;
+  MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<C, T>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  { k_gram_partial<C, T><<<nblk, kThreads, smem, s>>>((const C*)X, (const C*)Y, part, N, rx, ry,
+                                                      per); ::mrhs::count_launch(); }
   return MRHS_OK;
 }
 
-// Same two kernels as gram_ws, with the number of row blocks capped so that
-// the partial Grams fit a caller-provided buffer of `max_entries` complex128
-// values (used by the entry point that must not allocate).
+template <typename C>
+int launch_gram(const void* X, const void* Y, double2* part, int64_t N, int rx, int ry,
+                int nblk, int64_t per, cudaStream_t s) {
+  switch (gram_tile(rx, ry)) {
+    case 1: return launch_gram<C, 1>(X, Y, part, N, rx, ry, nblk, per, s);
+    case 2: return launch_gram<C, 2>(X, Y, part, N, rx, ry, nblk, per, s);
+    default: return launch_gram<C, 4>(X, Y, part, N, rx, ry, nblk, per, s);
+  }
+}
+
+int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
+            double2* part, cudaStream_t s) {
+  return gram_ws_capped(X, Y, G, N, rx, ry, dtype, part, (int64_t)gram_blocks(N) * rx * ry, s);
+}
+
+// The two Gram kernels with the number of row blocks capped so that the
+// partial Grams fit a buffer of `max_entries` complex128 values (the entry
+// point that must not allocate passes its own static buffer).
 int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
                    double2* part, int64_t max_entries, cudaStream_t s) {
   const int ne = rx * ry;
@@ -205,21 +286,10 @@ int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, 
     MRHS_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double2) * ne, s));
     return MRHS_OK;
   }
-  if (dtype == MRHS_C128) {
-    const size_t smem = sizeof(double2) * kTile * (rx + ry);
-    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<double2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    { k_gram_partial<double2><<<nblk, kThreads, smem, s>>>((const double2*)X, (const double2*)Y,
-                                                          part, N, rx, ry, per); ::mrhs::count_launch(); }
-  } else {
-    const size_t smem = sizeof(float2) * kTile * (rx + ry);
-    MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<float2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    { k_gram_partial<float2><<<nblk, kThreads, smem, s>>>((const float2*)X, (const float2*)Y, part,
-                                                         N, rx, ry, per); ::mrhs::count_launch(); }
-  }
+  if (dtype == MRHS_C128) MRHS_TRY(launch_gram<double2>(X, Y, part, N, rx, ry, nblk, per, s));
+  else MRHS_TRY(launch_gram<float2>(X, Y, part, N, rx, ry, nblk, per, s));
   MRHS_CUDA_TRY(cudaGetLastError());
-  { k_gram_final<<<(ne + 127) / 128, 128, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
+  { k_gram_final<<<(unsigned)((ne * 32 + 255) / 256), 256, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }

@@ -120,6 +120,17 @@ int simt_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nr
 // op_tc.cu
 int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s);
 unsigned tc_read_and_clear_error();
+int tc_apply_batch(mrhs_op_s* const* ops, int n, int prec, const void* const* X,
+                   void* const* Y, const int32_t* nrhs, const int32_t* active, cudaStream_t s,
+                   const TcTune* force = nullptr);
+// launch-shape cache (tune.cu)
+bool tune_lookup(mrhs_op_s* const* ops, const int32_t* nrhs, int n, int prec, TcTune* out);
+int autotune(mrhs_op_s* const* ops, int n, int prec, const int32_t* nrhs, int reps,
+             mrhs_tune_result* res, cudaStream_t s);
+int64_t tune_entries();
+void tune_clear();
+int tune_save(const char* path);
+int tune_load(const char* path);
 int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
              cudaStream_t s);
 int tc_supported(const mrhs_op_s* op, int prec, int nrhs);
@@ -143,6 +154,9 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
 int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* X, void* P,
           int R, cudaStream_t s);
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam);
+int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* const* X,
+                const int32_t* nrhs, const mrhs_solve_params& p, mrhs_solve_info* infos,
+                cudaStream_t s);
 
 // grad.cu
 int outer(const mrhs_op_s* op, const void* G, const void* X, double2* GA, double alpha, int R,

@@ -11,7 +11,16 @@
 // owns one RHS column r = t % nrhs and rows a = t / nrhs + k * (T / nrhs), so
 // the neighbour value X[b][r] is loaded once per b and reused for all its
 // rows while A[a][b] is a warp-wide broadcast.  On B300 the FP64 variant is
-// bound by the FP64 pipe, the FP32 variant by FFMA issue.
+// bound by the FP64 pipe, the FP32 variant by shared-memory loads.
+//
+// The FP64 variant forms each complex product from three real products
+// (Gauss / Karatsuba): with A = Ar + i Ai and x = Br + i Bi it accumulates
+// T1 = sum Ar Br, T2 = sum Ai Bi and T3 = sum (Ar + Ai)(Br + Bi), and writes
+// Re = T1 - T2, Im = T3 - T1 - T2 (for the adjoint, conj(A) x: T3 = sum
+// (Ar - Ai)(Br + Bi), Re = T1 + T2, Im = T3 - T1 + T2).  Ar +- Ai is formed
+// once per coefficient when it is staged, Br + Bi once per neighbour value,
+// so the FP64 pipe does three fused multiply-adds per complex product
+// instead of four.
 #include "internal.cuh"
 
 namespace mrhs {
@@ -74,6 +83,104 @@ __global__ void __launch_bounds__(256) k_op_simt(const C* __restrict__ A, const 
   }
 }
 
+template <int OPT>
+__global__ void __launch_bounds__(256) k_op_fp64_k3(const double2* __restrict__ A,
+                                                    const double2* __restrict__ X,
+                                                    double2* __restrict__ Y,
+                                                    const int32_t* __restrict__ nbr, int64_t V,
+                                                    int nb, int npts, int R, int dag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sA = reinterpret_cast<double2*>(smem_raw);
+  double2* sX = sA + nb * nb;                 // (Br, Bi)
+  double* sS = reinterpret_cast<double*>(sX + nb * R);   // Ar +- Ai
+  double* sXs = sS + nb * nb;                 // Br + Bi
+  const int T = blockDim.x;
+  const int rows_per_pass = T / R;
+  const int r = threadIdx.x % R;
+  const int a0 = threadIdx.x / R;
+  const bool lane_ok = threadIdx.x < rows_per_pass * R;
+  const double sg = dag ? -1.0 : 1.0;
+  for (int64_t x = blockIdx.x; x < V; x += gridDim.x) {
+    double t1[OPT], t2[OPT], t3[OPT];
+#pragma unroll
+    for (int k = 0; k < OPT; ++k) t1[k] = t2[k] = t3[k] = 0.0;
+    for (int p = 0; p < npts; ++p) {
+      const int64_t y = nbr[(int64_t)p * V + x];
+      const double2* Ap = A + ((dag ? y : x) * npts + p) * (int64_t)nb * nb;
+      const double2* Xp = X + y * (int64_t)nb * R;
+      __syncthreads();
+      for (int i = threadIdx.x; i < nb * nb; i += T) {
+        const double2 v = Ap[i];
+        sA[i] = v;
+        sS[i] = v.x + sg * v.y;
+      }
+      for (int i = threadIdx.x; i < nb * R; i += T) {
+        const double2 v = Xp[i];
+        sX[i] = v;
+        sXs[i] = v.x + v.y;
+      }
+      __syncthreads();
+      if (lane_ok) {
+        // forward: coefficient (a, b) at a * nb + b; adjoint: conj of (b, a)
+        const int sa = dag ? 1 : nb, sb = dag ? nb : 1;
+        for (int b = 0; b < nb; ++b) {
+          const double2 xv = sX[b * R + r];
+          const double xs = sXs[b * R + r];
+#pragma unroll
+          for (int k = 0; k < OPT; ++k) {
+            const int a = a0 + k * rows_per_pass;
+            if (a < nb) {
+              const int e = a * sa + b * sb;
+              const double2 av = sA[e];
+              t1[k] = fma(av.x, xv.x, t1[k]);
+              t2[k] = fma(av.y, xv.y, t2[k]);
+              t3[k] = fma(sS[e], xs, t3[k]);
+            }
+          }
+        }
+      }
+    }
+    if (lane_ok) {
+      double2* Yx = Y + x * (int64_t)nb * R;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        const int a = a0 + k * rows_per_pass;
+        if (a < nb)
+          Yx[a * R + r] = dag ? make_double2(t1[k] + t2[k], t3[k] - t1[k] + t2[k])
+                              : make_double2(t1[k] - t2[k], t3[k] - t1[k] - t2[k]);
+      }
+    }
+  }
+}
+
+template <int OPT>
+int launch_k3(const double2* A, const double2* X, double2* Y, const int32_t* nbr, int64_t V,
+              int nb, int npts, int R, int dag, int threads, cudaStream_t s) {
+  const size_t smem = sizeof(double2) * ((size_t)nb * nb + (size_t)nb * R) +
+                      sizeof(double) * ((size_t)nb * nb + (size_t)nb * R);
+  auto kern = k_op_fp64_k3<OPT>;
+  MRHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t grid = V < 1048576 ? V : 1048576;
+  { kern<<<(unsigned)grid, threads, smem, s>>>(A, X, Y, nbr, V, nb, npts, R, dag); ::mrhs::count_launch(); }
+  MRHS_CUDA_TRY(cudaGetLastError());
+  return MRHS_OK;
+}
+
+int dispatch_fp64(const double2* A, const double2* X, double2* Y, const int32_t* nbr, int64_t V,
+                  int nb, int npts, int R, int dag, cudaStream_t s) {
+  int rows = 256 / R;
+  if (rows < 1) rows = 1;
+  const int threads = rows * R;
+  const int need = (nb + rows - 1) / rows;
+  if (need <= 1) return launch_k3<1>(A, X, Y, nbr, V, nb, npts, R, dag, threads, s);
+  if (need <= 2) return launch_k3<2>(A, X, Y, nbr, V, nb, npts, R, dag, threads, s);
+  if (need <= 4) return launch_k3<4>(A, X, Y, nbr, V, nb, npts, R, dag, threads, s);
+  if (need <= 6) return launch_k3<6>(A, X, Y, nbr, V, nb, npts, R, dag, threads, s);
+  if (need <= 8) return launch_k3<8>(A, X, Y, nbr, V, nb, npts, R, dag, threads, s);
+  if (need <= 16) return launch_k3<16>(A, X, Y, nbr, V, nb, npts, R, dag, threads, s);
+  return fail(MRHS_ERR_INVALID_ARG, "simt apply: nb too large for nrhs");
+}
+
 template <typename C, int OPT>
 int launch(const C* A, const C* X, C* Y, const int32_t* nbr, int64_t V, int nb, int npts, int R,
            int dag, int threads, cudaStream_t s) {
@@ -110,8 +217,8 @@ int simt_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nr
   int st = MRHS_ERR_UNSUPPORTED;
   timer_mark(op, prec, s);
   if (prec == MRHS_PREC_FP64)
-    st = dispatch<double2>(op->a64, (const double2*)X, (double2*)Y, nbr, op->V, op->nb, op->npts,
-                           nrhs, dag ? 1 : 0, s);
+    st = dispatch_fp64(op->a64, (const double2*)X, (double2*)Y, nbr, op->V, op->nb, op->npts,
+                       nrhs, dag ? 1 : 0, s);
   else if (prec == MRHS_PREC_FP32)
     st = dispatch<float2>(op->a32, (const float2*)X, (float2*)Y, nbr, op->V, op->nb, op->npts,
                           nrhs, dag ? 1 : 0, s);

@@ -54,6 +54,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -66,13 +68,14 @@ namespace {
 constexpr int kThreadsTc = 192;
 constexpr int kAccCols = 64;     // TMEM columns per accumulator (n_mma <= 64)
 constexpr int kM = 128;
-constexpr int kLoRow = 64;       // first row of the input's lo term (XSPLIT)
+constexpr int kLoRowMax = 64;    // last possible first row of the input's lo term (XSPLIT)
 constexpr size_t kSmemBudget = 220 * 1024;   // dynamic shared memory per SM
 constexpr float kLoScale = 1.0f / 2048.0f;   // 2^-11
 
 struct Geom {
   int nb, nbp8, K, n_mma;   // K = 2 nbp8
   int R, xrows;             // rows of a packed input tile
+  int lo_row;               // XSPLIT: first row of the lo term (round8(2R))
   int xsplit, asplit;
   uint32_t coef1;           // one coefficient tile (hi or lo)
   uint32_t coef_bytes;      // coefficient bytes per stencil point (x2 if asplit)
@@ -88,7 +91,10 @@ Geom make_geom(int nb, int R, bool xsplit, bool asplit) {
   g.R = R;
   g.xsplit = xsplit;
   g.asplit = asplit;
-  g.xrows = xsplit ? kM : (2 * R + 7) / 8 * 8;
+  // XSPLIT stacks the lo term right after the hi term, so a tile holds
+  // 2 round8(2R) rows rather than all 128 rows of the MMA operand
+  g.lo_row = (2 * R + 7) / 8 * 8;
+  g.xrows = xsplit ? 2 * g.lo_row : g.lo_row;
   g.coef1 = (uint32_t)g.nbp8 * g.K * 2;
   g.coef_bytes = g.coef1 * (asplit ? 2u : 1u);
   g.xb_bytes = (uint32_t)g.xrows * g.K * 2;
@@ -214,43 +220,90 @@ __global__ void __launch_bounds__(256) k_pack_coef(const double2* __restrict__ A
   }
 }
 
-// Per-column max |Re|, |Im| of a complex64 [N][R] block (as float bits).
-__global__ void k_colmax(const float2* __restrict__ X, int64_t N, int R, unsigned* out) {
-  __shared__ unsigned s_m[MRHS_MAX_RHS];
-  for (int i = threadIdx.x; i < R; i += blockDim.x) s_m[i] = 0u;
-  __syncthreads();
-  const int64_t total = N * R;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = X[i];
-    const float m = fmaxf(fabsf(v.x), fabsf(v.y));
-    atomicMax(&s_m[i % R], __float_as_uint(m));
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < R; i += blockDim.x) atomicMax(&out[i], s_m[i]);
+// Input packing of every problem of a launch, three launches in all: column
+// maxima, column scales, real-split tiles.  Each kernel runs a 2-D grid whose
+// blockIdx.y is the problem; a problem masked out by `active` returns at once.
+struct PackProb {
+  const float2* X;          // complex64 [V][nb][R]
+  unsigned* colmax;         // [64] float bits, zero on entry (reset by k_colscale)
+  float* sigma;             // [64]
+  uint8_t* xb;              // packed tiles
+  int64_t V;
+  Geom g;
+};
+struct PackBatch {
+  int32_t n;
+  const int32_t* active;
+  PackProb p[MRHS_MAX_BATCH];
+};
+
+__device__ __forceinline__ bool pack_live(const PackBatch& pb, int k) {
+  return pb.active == nullptr || pb.active[k] != 0;
 }
 
-// sigma_r = 2^e >= column max (1 for a zero column); stored as float.
-__global__ void k_colscale(const unsigned* __restrict__ colmax, float* sigma, int R) {
+// Per-column max |Re|, |Im| of a problem's [N][R] block (as float bits): a
+// thread keeps one column, so the maximum stays in a register until the end.
+__global__ void k_colmax(const __grid_constant__ PackBatch pb) {
+  const int k = blockIdx.y;
+  if (!pack_live(pb, k)) return;
+  const PackProb& pp = pb.p[k];
+  const int R = pp.g.R;
+  const int rows_per_block = blockDim.x / R;
+  const int t = threadIdx.x;
+  __shared__ unsigned s_m[MRHS_MAX_RHS];
+  for (int i = t; i < R; i += blockDim.x) s_m[i] = 0u;
+  __syncthreads();
+  if (t < rows_per_block * R) {
+    const int c = t % R;
+    const int64_t N = pp.V * pp.g.nb;
+    const float2* X = pp.X;
+    float m = 0.f;
+    for (int64_t row = (int64_t)blockIdx.x * rows_per_block + t / R; row < N;
+         row += (int64_t)gridDim.x * rows_per_block) {
+      const float2 v = X[row * R + c];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    atomicMax(&s_m[c], __float_as_uint(m));
+  }
+  __syncthreads();
+  for (int i = t; i < R; i += blockDim.x)
+    if (s_m[i]) atomicMax(&pp.colmax[i], s_m[i]);
+}
+
+// sigma_r = 2^e >= column max (1 for a zero column); stored as float.  The
+// maxima are cleared for the next application.
+__global__ void k_colscale(const __grid_constant__ PackBatch pb) {
+  const int k = blockIdx.x;
+  if (!pack_live(pb, k)) return;
+  const PackProb& pp = pb.p[k];
   const int r = threadIdx.x;
-  if (r < R) sigma[r] = (float)pow2_ceil((double)__uint_as_float(colmax[r]));
+  if (r < pp.g.R) {
+    pp.sigma[r] = (float)pow2_ceil((double)__uint_as_float(pp.colmax[r]));
+    pp.colmax[r] = 0u;
+  }
 }
 
 // Packed real-split input tiles, one [xrows][K] canonical tile per site.
-// XSPLIT: rows < 2R hold the hi term, rows 64 + (0..2R-1) the lo term.
+// XSPLIT: rows < 2R hold the hi term, rows lo_row + (0..2R-1) the lo term.
 template <bool BF16, bool XSPLIT>
-__global__ void k_pack_xb(const float2* __restrict__ X, const float* __restrict__ sigma,
-                          uint8_t* xb, int64_t V, int nb, Geom g) {
+__global__ void k_pack_xb(const __grid_constant__ PackBatch pb) {
+  const int k = blockIdx.y;
+  if (!pack_live(pb, k)) return;
+  const PackProb& pp = pb.p[k];
+  const Geom g = pp.g;
+  const float2* __restrict__ X = pp.X;
+  const float* __restrict__ sigma = pp.sigma;
+  uint8_t* xb = pp.xb;
+  const int nb = g.nb, R = g.R;
   const int units = g.xrows * (g.K / 8);   // 16-byte units per site
-  const int64_t total = V * units;
+  const int64_t total = pp.V * units;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total;
        u += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = u / units;
     const int w = (int)(u % units);
     const int kc = w / g.xrows, mrow = w % g.xrows;
-    const bool lo_term = XSPLIT && mrow >= kLoRow;
-    const int m = lo_term ? mrow - kLoRow : mrow;
-    const int R = g.R;
+    const bool lo_term = XSPLIT && mrow >= g.lo_row;
+    const int m = lo_term ? mrow - g.lo_row : mrow;
     uint16_t h[8];
     const bool re_row = m < R;
     const int r = re_row ? m : m - R;
@@ -258,9 +311,9 @@ __global__ void k_pack_xb(const float2* __restrict__ X, const float* __restrict_
     const float inv = live ? 1.0f / sigma[r] : 0.f;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int k = kc * 8 + e;
-      const bool first = k < g.nbp8;
-      const int b = first ? k : k - g.nbp8;
+      const int kk = kc * 8 + e;
+      const bool first = kk < g.nbp8;
+      const int b = first ? kk : kk - g.nbp8;
       float v = 0.f;
       if (live && b < nb) {
         const float2 xv = X[(x * nb + b) * R + r];
@@ -285,12 +338,43 @@ __global__ void k_pack_xb(const float2* __restrict__ X, const float* __restrict_
   }
 }
 
+// One problem of a launch: its operands, geometry and stencil.
+struct ProbDesc {
+  const uint8_t* coef;      // packed coefficient image
+  const uint8_t* xb;        // packed input tiles
+  const float* scale;       // s_x
+  const float* diag;        // d_x
+  const float* sigma;       // sigma_r
+  const float* X;           // complex64 input (as floats), for d_x X(x)
+  float* Y;                 // complex64 output
+  int64_t V, item0;         // sites; first item of this problem in the work list
+  int32_t npts, nb, K, n_mma, R, pps, lo_row;
+  uint32_t coef1, coef_bytes, xb_bytes, sbo, idesc, xb_off;
+  Stencil st;
+};
+
+// Every problem of one launch, by value in the kernel parameters (large
+// kernel parameters: no upload, nothing to capture separately in a graph).
+struct Batch {
+  int32_t n;
+  int64_t total;            // items (sites) over all problems
+  const int32_t* active;    // per problem 0/1, or null (all active)
+  ProbDesc p[MRHS_MAX_BATCH];
+};
+
+__device__ __forceinline__ int find_prob(const Batch& bt, int64_t t) {
+  int k = 0;
+  for (int i = 1; i < bt.n; ++i)
+    if (t >= bt.p[i].item0) k = i;
+  return k;
+}
+__device__ __forceinline__ bool item_live(const Batch& bt, int k) {
+  return bt.active == nullptr || bt.active[k] != 0;
+}
+
 template <bool BF16, bool XSPLIT, bool ASPLIT>
 __global__ void __launch_bounds__(kThreadsTc, 2)
-    k_op_tc(const uint8_t* __restrict__ coef, const uint8_t* __restrict__ xb,
-            const float* __restrict__ sscale, const float* __restrict__ sdiag,
-            const float* __restrict__ sigma, const float* __restrict__ Xf, float* __restrict__ Yf,
-            const Stencil st, int64_t V, int npts, Geom g, int nstages, int pps) {
+    k_op_tc(const __grid_constant__ Batch bt, int nstages, uint32_t stage_bytes) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int kAccStride = ASPLIT ? 2 * kAccCols : kAccCols;   // TMEM cols per buffer
   constexpr uint32_t kTmemCols = ASPLIT ? 256u : 128u;
@@ -300,11 +384,10 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
   uint64_t* acc_empty = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   uint8_t* stages = smem + 1024;
-  // a stage holds `pps` consecutive stencil points of one site: their
-  // coefficient tiles (contiguous in HBM, one bulk copy) then their pps
-  // neighbour input tiles
-  const uint32_t stage_bytes = (uint32_t)pps * (g.coef_bytes + g.xb_bytes);
-  const uint32_t xb_off = (uint32_t)pps * g.coef_bytes;
+  // a stage holds up to `pps` consecutive stencil points of one site: their
+  // coefficient tiles (contiguous in HBM, one bulk copy) at the start, their
+  // neighbour input tiles from the problem's `xb_off` on (one stage size for
+  // all problems; each packs as many points as fit)
   // XSPLIT exchange buffer for the lo rows, after the ring
   float* ex = reinterpret_cast<float*>(stages + (size_t)nstages * stage_bytes);
   __shared__ volatile int s_abort;
@@ -340,35 +423,47 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
       uint32_t ph = 0;
       int64_t issued = 0;
       bool ok = true;
-      for (int64_t x = blockIdx.x; x < V && ok; x += gridDim.x) {
-        int c[4];
+      for (int64_t t = blockIdx.x; t < bt.total && ok; t += gridDim.x) {
+        const int k = find_prob(bt, t);
+        if (!item_live(bt, k)) continue;
+        // the problem's fields in registers: the waits and copies below
+        // clobber memory, and would otherwise reload them from the parameters
+        const ProbDesc& pd = bt.p[k];
+        const int64_t x = t - pd.item0;
+        const uint8_t* coef = pd.coef;
+        const uint8_t* xbp = pd.xb;
+        const int npts = pd.npts, pps = pd.pps, sign = pd.st.sign;
+        const uint32_t cbytes = pd.coef_bytes, xbytes = pd.xb_bytes, xb_off = pd.xb_off;
+        const uint32_t* dwords = reinterpret_cast<const uint32_t*>(&pd.st.d[0][0]);
+        int Lm[4], c[4];
         {
           int64_t r = x;
 #pragma unroll
           for (int mu = 0; mu < 4; ++mu) {
-            c[mu] = (int)(r % st.L[mu]);
-            r /= st.L[mu];
+            Lm[mu] = pd.st.L[mu];
+            c[mu] = (int)(r % Lm[mu]);
+            r /= Lm[mu];
           }
         }
         for (int p0 = 0; p0 < npts; p0 += pps) {
           const int np = (npts - p0) < pps ? (npts - p0) : pps;
           if (!ptx::mbar_wait(&empty[s], ph ^ 1u, &s_abort)) { ok = false; break; }
           uint8_t* st_smem = stages + (size_t)s * stage_bytes;
-          ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)np * (g.coef_bytes + g.xb_bytes));
-          ptx::bulk_g2s(st_smem, coef + ((uint64_t)x * npts + p0) * g.coef_bytes,
-                        (uint32_t)np * g.coef_bytes, &full[s], pol_stream);
+          ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)np * (cbytes + xbytes));
+          ptx::bulk_g2s(st_smem, coef + ((uint64_t)x * npts + p0) * cbytes,
+                        (uint32_t)np * cbytes, &full[s], pol_stream);
           for (int i = 0; i < np; ++i) {
-            const int p = p0 + i;
+            const uint32_t dw = dwords[p0 + i];      // delta_p, four signed bytes
             int64_t y = 0;
 #pragma unroll
             for (int mu = 3; mu >= 0; --mu) {
-              int v = c[mu] + st.sign * (int)st.d[p][mu];
-              v += (v < 0) ? st.L[mu] : 0;
-              v -= (v >= st.L[mu]) ? st.L[mu] : 0;
-              y = y * st.L[mu] + v;
+              int v = c[mu] + sign * (int)(int8_t)(dw >> (8 * mu));
+              v += (v < 0) ? Lm[mu] : 0;
+              v -= (v >= Lm[mu]) ? Lm[mu] : 0;
+              y = y * Lm[mu] + v;
             }
-            ptx::bulk_g2s(st_smem + xb_off + (uint32_t)i * g.xb_bytes,
-                          xb + (uint64_t)y * g.xb_bytes, g.xb_bytes, &full[s], pol_keep);
+            ptx::bulk_g2s(st_smem + xb_off + (uint32_t)i * xbytes, xbp + (uint64_t)y * xbytes,
+                          xbytes, &full[s], pol_keep);
           }
           ++issued;
           if (++s == nstages) { s = 0; ph ^= 1u; }
@@ -391,12 +486,16 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      const uint32_t idesc = ptx::idesc_f16(kM, g.n_mma, BF16);
       int s = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
-      const int nk = g.K / 16;
       bool ok = true;
-      for (int64_t x = blockIdx.x; x < V && ok; x += gridDim.x) {
+      for (int64_t t = blockIdx.x; t < bt.total && ok; t += gridDim.x) {
+        const int k = find_prob(bt, t);
+        if (!item_live(bt, k)) continue;
+        const ProbDesc& pd = bt.p[k];
+        const int nk = pd.K / 16, npts = pd.npts, pps = pd.pps;
+        const uint32_t cbytes = pd.coef_bytes, xbytes = pd.xb_bytes, sbo = pd.sbo,
+                       idesc = pd.idesc, coef1 = pd.coef1, xb_off = pd.xb_off;
         if (!ptx::mbar_wait(&acc_empty[acc], aph ^ 1u, &s_abort)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t tmem_d = tmem_base + (uint32_t)(acc * kAccStride);
@@ -406,15 +505,16 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
           ptx::tc_fence_after();
           const uint32_t sb = ptx::smem_u32(stages + (size_t)s * stage_bytes);
           for (int i = 0; i < np; ++i) {
-            const uint32_t cb = sb + (uint32_t)i * g.coef_bytes;
-            const uint32_t ab = sb + xb_off + (uint32_t)i * g.xb_bytes;
+            const uint32_t cb = sb + (uint32_t)i * cbytes;
+            const uint32_t ab = sb + xb_off + (uint32_t)i * xbytes;
             const uint32_t first = (p0 > 0 || i > 0) ? 1u : 0u;
             for (int j = 0; j < nk; ++j) {
-              const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)j * 256u, 128u, g.sbo);
-              const uint64_t bdesc = ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, g.sbo);
+              const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)j * 256u, 128u, sbo);
+              const uint64_t bdesc = ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, sbo);
               ptx::mma_f16(tmem_d, adesc, bdesc, idesc, (first || j > 0) ? 1u : 0u);
               if (ASPLIT) {
-                const uint64_t ldesc = ptx::smem_desc(cb + g.coef1 + (uint32_t)j * 256u, 128u, g.sbo);
+                const uint64_t ldesc =
+                    ptx::smem_desc(cb + coef1 + (uint32_t)j * 256u, 128u, sbo);
                 ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc, ldesc, idesc,
                              (first || j > 0) ? 1u : 0u);
               }
@@ -436,27 +536,33 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
     // ---------------- epilogue, warps 2..5 -> TMEM lane quarters 2,3,0,1
     const int q = warp & 3;
     const int mrow = 32 * q + lane;              // D row = TMEM lane
-    const bool lo_thread = XSPLIT && mrow >= kLoRow;
-    const int m = lo_thread ? mrow - kLoRow : mrow;
-    const int R = g.R, nb = g.nb;
-    const bool valid = m < 2 * R;
-    const bool writer = valid && !lo_thread;
-    const int r = valid ? (m < R ? m : m - R) : 0;
-    const int part = m < R ? 0 : 1;
-    const float sig = writer ? sigma[r] : 0.f;
     int acc = 0;
     uint32_t aph = 0;
-    for (int64_t x = blockIdx.x; x < V; x += gridDim.x) {
+    for (int64_t t = blockIdx.x; t < bt.total; t += gridDim.x) {
+      const int k = find_prob(bt, t);
+      if (!item_live(bt, k)) continue;
+      const ProbDesc& pd = bt.p[k];
+      const int64_t x = t - pd.item0;
+      const int R = pd.R, nb = pd.nb, n_mma = pd.n_mma, lo_row = pd.lo_row;
+      // XSPLIT: rows [lo_row, 2 lo_row) carry the input's lo term
+      const bool lo_thread = XSPLIT && mrow >= lo_row && mrow < 2 * lo_row;
+      const int m = lo_thread ? mrow - lo_row : mrow;
+      float* Yp = pd.Y;
+      const bool valid = m < 2 * R;
+      const bool writer = valid && !lo_thread;
+      const int r = valid ? (m < R ? m : m - R) : 0;
+      const int part = m < R ? 0 : 1;
       // the d_x X(x) term: load it before waiting, so its latency overlaps
       // the site's MMAs
       float xv[kAccCols];
       float sc = 0.f, dx = 0.f;
       if (writer) {
-        sc = __ldg(&sscale[x]) * sig;
-        dx = __ldg(&sdiag[x]);
+        const float* Xp = pd.X;
+        sc = __ldg(&pd.scale[x]) * __ldg(&pd.sigma[r]);
+        dx = __ldg(&pd.diag[x]);
 #pragma unroll
         for (int a = 0; a < kAccCols; ++a)
-          xv[a] = a < nb ? __ldg(&Xf[(((int64_t)x * nb + a) * R + r) * 2 + part]) : 0.f;
+          xv[a] = a < nb ? __ldg(&Xp[(((int64_t)x * nb + a) * R + r) * 2 + part]) : 0.f;
       }
       const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort);
       // give up together: tcgen05.ld below is .aligned per warp, and with
@@ -472,16 +578,22 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
       const uint32_t taddr =
           tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccStride);
       ptx::tmem_ld32_sync(taddr, v);
-      if (g.n_mma > 32) ptx::tmem_ld32_sync(taddr + 32u, v + 32);
-      if (ASPLIT && !lo_thread) {      // + 2^-11 Alo Xhi (rows < 64 only)
+      if (n_mma > 32) ptx::tmem_ld32_sync(taddr + 32u, v + 32);
+      if (ASPLIT) {      // + 2^-11 Alo Xhi, kept on the hi rows only
+        // tcgen05.ld is warp-collective (.sync.aligned): every lane loads,
+        // whatever its row, and the lo rows discard the value
         float w[32];
         ptx::tmem_ld32_sync(taddr + (uint32_t)kAccCols, w);
+        if (!lo_thread) {
 #pragma unroll
-        for (int a = 0; a < 32; ++a) v[a] = fmaf(kLoScale, w[a], v[a]);
-        if (g.n_mma > 32) {
+          for (int a = 0; a < 32; ++a) v[a] = fmaf(kLoScale, w[a], v[a]);
+        }
+        if (n_mma > 32) {
           ptx::tmem_ld32_sync(taddr + (uint32_t)kAccCols + 32u, w);
+          if (!lo_thread) {
 #pragma unroll
-          for (int a = 0; a < 32; ++a) v[32 + a] = fmaf(kLoScale, w[a], v[32 + a]);
+            for (int a = 0; a < 32; ++a) v[32 + a] = fmaf(kLoScale, w[a], v[32 + a]);
+          }
         }
       }
       ptx::tc_fence_before();
@@ -507,7 +619,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
         for (int a = 0; a < kAccCols; ++a) {
           if (a < nb) {
             const int64_t idx = (((int64_t)x * nb + a) * R + r) * 2 + part;
-            Yf[idx] = fmaf(sc, v[a], dx * xv[a]);
+            Yp[idx] = fmaf(sc, v[a], dx * xv[a]);
           }
         }
       }
@@ -523,45 +635,183 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
   }
 }
 
-// Ring depth and shared memory for `pps` points per stage within `budget`
-// bytes of shared memory per CTA.
-int tc_stages(const Geom& g, int pps, size_t budget, int max_stages, size_t* smem_out) {
-  const size_t stage = (size_t)pps * (g.coef_bytes + g.xb_bytes);
-  // the M = 128 operand read runs past an input tile of fewer than 128 rows,
-  // and the N = n_mma read past an nbp8-row coefficient tile: keep that much
-  // slack at the end (plus the XSPLIT exchange buffer)
-  const size_t row_bytes = (size_t)g.K * 2;
-  size_t tail = (size_t)(kM - g.xrows) * row_bytes + (size_t)(g.n_mma) * row_bytes + 1024;
-  if (g.xsplit) tail += (size_t)kLoRow * kAccCols * sizeof(float);
+// Ring layout for a launch: one stage size for every problem, set by the
+// largest request; a stage of problem i holds pps[i] coefficient tiles and,
+// from xb_off[i] on, pps[i] input tiles.  After the size is fixed each
+// problem's pps grows to fill the stage (at most 8 and its stencil size).
+struct Ring {
+  int nstages = 0;
+  uint32_t stage_bytes = 0;
+  size_t smem = 0;
+};
+
+int plan_ring(const Geom* g, int* pps, const int* npts, int n, size_t budget, int max_stages,
+              Ring* out, uint32_t* xb_off) {
+  size_t stage = 0, tail = 0;
+  bool xs = false;
+  for (int i = 0; i < n; ++i) {
+    stage = std::max(stage, (size_t)pps[i] * (g[i].coef_bytes + g[i].xb_bytes));
+    // the M = 128 operand read runs past an input tile of fewer than 128
+    // rows, and the N = n_mma read past an nbp8-row coefficient tile
+    const size_t row_bytes = (size_t)g[i].K * 2;
+    tail = std::max(tail, (size_t)(kM - g[i].xrows) * row_bytes + (size_t)g[i].n_mma * row_bytes);
+    xs = xs || g[i].xsplit;
+  }
+  tail += 1024;
+  if (xs) tail += (size_t)kLoRowMax * kAccCols * sizeof(float);
   if (budget < 1024 + tail + 2 * stage) return 0;
-  int n = (int)((budget - 1024 - tail) / stage);
-  if (n > max_stages) n = max_stages;
-  if (n > 32) n = 32;                 // barrier area: 2 * 32 + 4 words < 1024 bytes
-  if (n < 2) return 0;
-  *smem_out = 1024 + (size_t)n * stage + tail;
-  return n;
+  int ns = (int)((budget - 1024 - tail) / stage);
+  if (ns > max_stages) ns = max_stages;
+  if (ns > 32) ns = 32;                 // barrier area: 2 * 32 + 4 words < 1024 bytes
+  if (ns < 2) return 0;
+  for (int i = 0; i < n && xb_off; ++i) {
+    const size_t u = g[i].coef_bytes + g[i].xb_bytes;
+    int fit = (int)(stage / u);
+    if (fit > 8) fit = 8;
+    if (fit > npts[i]) fit = npts[i];
+    if (fit > pps[i]) pps[i] = fit;
+    xb_off[i] = (uint32_t)pps[i] * g[i].coef_bytes;
+  }
+  out->nstages = ns;
+  out->stage_bytes = (uint32_t)stage;
+  out->smem = 1024 + (size_t)ns * stage + tail;
+  return ns;
 }
 
-TcTune default_tune(const Geom& g) {
-  TcTune t;
+int default_pps(const Geom& g) {
   // points per stage: aim for >= 16 KB of coefficients per copy
-  t.pps = (int)((16384 + g.coef_bytes - 1) / g.coef_bytes);
-  if (t.pps > 8) t.pps = 8;
-  if (t.pps < 1) t.pps = 1;
-  t.ctas_per_sm = 2;    // two independent copy/MMA rings per SM
-  t.max_stages = 32;
-  return t;
+  int pps = (int)((16384 + g.coef_bytes - 1) / g.coef_bytes);
+  return pps > 8 ? 8 : (pps < 1 ? 1 : pps);
 }
 
 template <bool BF16, bool XS, bool AS>
-int launch_tc(const TcImage& img, const uint8_t* xb, const float* sigma, const void* X, void* Y,
-              const Stencil& stn, int64_t V, int npts, const Geom& g, int nst, int pps,
-              size_t smem, int64_t grid, cudaStream_t s) {
+int launch_tc(const Batch& bt, const Ring& ring, int64_t grid, cudaStream_t s) {
   auto kern = k_op_tc<BF16, XS, AS>;
-  MRHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  { kern<<<(unsigned)grid, kThreadsTc, smem, s>>>((const uint8_t*)img.codes, xb, img.scale, img.diag,
-                                                  sigma, (const float*)X, (float*)Y, stn, V, npts,
-                                                  g, nst, pps); ::mrhs::count_launch(); }
+  MRHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ring.smem));
+  { kern<<<(unsigned)grid, kThreadsTc, ring.smem, s>>>(bt, ring.nstages, ring.stage_bytes); ::mrhs::count_launch(); }
+  return MRHS_OK;
+}
+
+bool xsplit_of(int prec) { return prec == MRHS_PREC_FP16X || prec == MRHS_PREC_TC32; }
+
+// Reserve one problem's packing workspace (column maxima and scales at a
+// fixed offset, so the maxima stay zero between applications; tiles after)
+// and fill its kernel and packing descriptors.
+constexpr size_t kXpackHead = 1024;
+
+int prepare(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs, int pps_req,
+            cudaStream_t s, ProbDesc* pd, PackProb* pk, Geom* gout) {
+  const int i = image_index(prec);
+  if (dag && !op->tc_dag[i].codes) {
+    if (!op->a64) return fail(MRHS_ERR_UNSUPPORTED, "daggered low-precision image needs FP64 coefficients");
+    MRHS_TRY(tc_build(op, prec, true, op->a64, s));
+  }
+  const TcImage& img = dag ? op->tc_dag[i] : op->tc[i];
+  const bool xs = xsplit_of(prec);
+  const Geom g = make_geom(op->nb, nrhs, xs, prec == MRHS_PREC_TC32);
+  const size_t xb_bytes = (size_t)op->V * g.xb_bytes;
+  const size_t before = op->ws_xpack.bytes;      // grows on every reallocation
+  MRHS_TRY(op->ws_xpack.ensure(kXpackHead + xb_bytes));
+  unsigned* colmax = (unsigned*)op->ws_xpack.ptr;
+  float* sigma = (float*)(colmax + MRHS_MAX_RHS);
+  uint8_t* xb = (uint8_t*)op->ws_xpack.ptr + kXpackHead;
+  if (op->ws_xpack.bytes != before)
+    MRHS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned) * MRHS_MAX_RHS, s));
+  pk->X = (const float2*)X;
+  pk->colmax = colmax;
+  pk->sigma = sigma;
+  pk->xb = xb;
+  pk->V = op->V;
+  pk->g = g;
+  pd->coef = (const uint8_t*)img.codes;
+  pd->xb = xb;
+  pd->scale = img.scale;
+  pd->diag = img.diag;
+  pd->sigma = sigma;
+  pd->X = (const float*)X;
+  pd->Y = (float*)Y;
+  pd->V = op->V;
+  pd->npts = op->npts;
+  pd->nb = op->nb;
+  pd->K = g.K;
+  pd->n_mma = g.n_mma;
+  pd->R = nrhs;
+  pd->lo_row = g.lo_row;
+  pd->pps = pps_req > 0 ? pps_req : default_pps(g);
+  if (pd->pps > op->npts) pd->pps = op->npts;
+  pd->coef1 = g.coef1;
+  pd->coef_bytes = g.coef_bytes;
+  pd->xb_bytes = g.xb_bytes;
+  pd->sbo = g.sbo;
+  pd->idesc = ptx::idesc_f16(kM, g.n_mma, prec == MRHS_PREC_BF16);
+  for (int mu = 0; mu < 4; ++mu) pd->st.L[mu] = op->L[mu];
+  pd->st.sign = dag ? -1 : 1;
+  for (int p = 0; p < op->npts; ++p)
+    for (int mu = 0; mu < 4; ++mu) pd->st.d[p][mu] = op->disp[p][mu];
+  *gout = g;
+  return MRHS_OK;
+}
+
+// The three packing launches for every problem of `pb`.
+int pack_batch(const PackBatch& pb, int prec, cudaStream_t s) {
+  const int sms = num_sms();
+  const dim3 g4((unsigned)(sms * 4), (unsigned)pb.n), g8((unsigned)(sms * 8), (unsigned)pb.n);
+  { k_colmax<<<g4, 256, 0, s>>>(pb); ::mrhs::count_launch(); }
+  { k_colscale<<<pb.n, 64, 0, s>>>(pb); ::mrhs::count_launch(); }
+  if (prec == MRHS_PREC_BF16)
+    { k_pack_xb<true, false><<<g8, 256, 0, s>>>(pb); ::mrhs::count_launch(); }
+  else if (!xsplit_of(prec))
+    { k_pack_xb<false, false><<<g8, 256, 0, s>>>(pb); ::mrhs::count_launch(); }
+  else
+    { k_pack_xb<false, true><<<g8, 256, 0, s>>>(pb); ::mrhs::count_launch(); }
+  MRHS_CUDA_TRY(cudaGetLastError());
+  return MRHS_OK;
+}
+
+int run_batch(Batch& bt, Geom* geoms, int prec, const TcTune& tune, bool tune_set, int timer_prec,
+              mrhs_op_s* timer_op, cudaStream_t s) {
+  int ctas = tune_set ? tune.ctas_per_sm : 2;
+  const int max_stages = tune_set ? tune.max_stages : 32;
+  Ring ring;
+  int pps[MRHS_MAX_BATCH], npts[MRHS_MAX_BATCH];
+  uint32_t xb_off[MRHS_MAX_BATCH];
+  for (int i = 0; i < bt.n; ++i) {
+    pps[i] = bt.p[i].pps;
+    npts[i] = bt.p[i].npts;
+  }
+  for (;;) {   // fall back to fewer points per stage, then one CTA per SM
+    if (plan_ring(geoms, pps, npts, bt.n, kSmemBudget / (size_t)ctas, max_stages, &ring, xb_off) >= 2)
+      break;
+    bool shrunk = false;
+    for (int i = 0; i < bt.n; ++i)
+      if (pps[i] > 1) { pps[i] = (pps[i] + 1) / 2; shrunk = true; }
+    if (!shrunk) {
+      if (ctas == 1) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core ring does not fit");
+      ctas = 1;
+      for (int i = 0; i < bt.n; ++i) pps[i] = bt.p[i].pps;
+    }
+  }
+  for (int i = 0; i < bt.n; ++i) {
+    bt.p[i].pps = pps[i];
+    bt.p[i].xb_off = xb_off[i];
+  }
+  bt.total = 0;
+  for (int i = 0; i < bt.n; ++i) {
+    bt.p[i].item0 = bt.total;
+    bt.total += bt.p[i].V;
+  }
+  const int64_t cap = (int64_t)num_sms() * ctas;
+  const int64_t grid = bt.total < cap ? bt.total : cap;
+  if (timer_op) timer_mark(timer_op, timer_prec, s);
+  int st;
+  if (prec == MRHS_PREC_BF16) st = launch_tc<true, false, false>(bt, ring, grid, s);
+  else if (prec == MRHS_PREC_FP16) st = launch_tc<false, false, false>(bt, ring, grid, s);
+  else if (prec == MRHS_PREC_FP16X) st = launch_tc<false, true, false>(bt, ring, grid, s);
+  else st = launch_tc<false, true, true>(bt, ring, grid, s);
+  if (timer_op) timer_mark(timer_op, timer_prec, s);
+  MRHS_TRY(st);
+  MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }
 
@@ -569,11 +819,12 @@ int launch_tc(const TcImage& img, const uint8_t* xb, const float* sigma, const v
 
 int tc_supported(const mrhs_op_s* op, int prec, int nrhs) {
   if (op->nb > 64 || nrhs > 64 || nrhs < 1) return 0;
-  const bool xs = prec == MRHS_PREC_FP16X || prec == MRHS_PREC_TC32;
+  const bool xs = xsplit_of(prec);
   if (xs && nrhs > 32) return 0;
-  size_t smem;
-  return tc_stages(make_geom(op->nb, nrhs, xs, prec == MRHS_PREC_TC32), 1, kSmemBudget, 32,
-                   &smem) > 0;
+  const Geom g = make_geom(op->nb, nrhs, xs, prec == MRHS_PREC_TC32);
+  int one = 1;
+  Ring r;
+  return plan_ring(&g, &one, &one, 1, kSmemBudget, 32, &r, nullptr) > 0;
 }
 
 int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s) {
@@ -614,74 +865,55 @@ int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs
   if (!tc_supported(op, prec, nrhs))
     return fail(MRHS_ERR_UNSUPPORTED,
                 "tensor-core shape (nb <= 64; nrhs <= 64, or <= 32 for FP16X/TC32)");
-  if (dag && !op->tc_dag[i].codes) {
-    if (!op->a64) return fail(MRHS_ERR_UNSUPPORTED, "daggered low-precision image needs FP64 coefficients");
-    MRHS_TRY(tc_build(op, prec, true, op->a64, s));
+  // launch shape: set on the operator, else tuned for this shape, else default
+  TcTune tune = op->tc_tune;
+  bool set = op->tc_set;
+  if (!set) {
+    const int32_t r = nrhs;
+    set = tune_lookup(&op, &r, 1, prec, &tune);
   }
-  const TcImage& img = dag ? op->tc_dag[i] : op->tc[i];
-  const bool xs = prec == MRHS_PREC_FP16X || prec == MRHS_PREC_TC32;
-  const bool as = prec == MRHS_PREC_TC32;
-  const Geom g = make_geom(op->nb, nrhs, xs, as);
-  const size_t xb_bytes = (size_t)op->V * g.xb_bytes;
-  const size_t small = 256 * sizeof(unsigned);
-  MRHS_TRY(op->ws_xpack.ensure(xb_bytes + small));
-  uint8_t* xb = (uint8_t*)op->ws_xpack.ptr;
-  unsigned* colmax = (unsigned*)(xb + xb_bytes);
-  float* sigma = (float*)(colmax + MRHS_MAX_RHS);
-  const int sms = num_sms();
-  MRHS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned) * MRHS_MAX_RHS, s));
-  { k_colmax<<<sms * 4, 256, 0, s>>>((const float2*)X, op->V * op->nb, nrhs, colmax); ::mrhs::count_launch(); }
-  { k_colscale<<<1, 64, 0, s>>>(colmax, sigma, nrhs); ::mrhs::count_launch(); }
-  if (prec == MRHS_PREC_BF16)
-    { k_pack_xb<true, false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
-  else if (!xs)
-    { k_pack_xb<false, false><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
-  else
-    { k_pack_xb<false, true><<<sms * 8, 256, 0, s>>>((const float2*)X, sigma, xb, op->V, op->nb, g); ::mrhs::count_launch(); }
-  MRHS_CUDA_TRY(cudaGetLastError());
-  TcTune t = default_tune(g);
-  if (op->tc_tune.pps > 0) t.pps = op->tc_tune.pps;
-  if (op->tc_set) {
-    t.ctas_per_sm = op->tc_tune.ctas_per_sm;
-    t.max_stages = op->tc_tune.max_stages;
+  Batch bt;
+  bt.n = 1;
+  bt.active = nullptr;
+  PackBatch pb;
+  pb.n = 1;
+  pb.active = nullptr;
+  Geom g;
+  MRHS_TRY(prepare(op, prec, dag, X, Y, nrhs, set ? tune.pps : 0, s, &bt.p[0], &pb.p[0], &g));
+  MRHS_TRY(pack_batch(pb, prec, s));
+  return run_batch(bt, &g, prec, tune, set, prec, op, s);
+}
+
+// Many operators in one persistent launch (each with its own inputs).
+int tc_apply_batch(mrhs_op_s* const* ops, int n, int prec, const void* const* X,
+                   void* const* Y, const int32_t* nrhs, const int32_t* active, cudaStream_t s,
+                   const TcTune* force) {
+  if (n < 1 || n > MRHS_MAX_BATCH) return fail(MRHS_ERR_INVALID_ARG, "batch size 1..16");
+  if (image_index(prec) < 0) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
+  TcTune tune = ops[0]->tc_tune;
+  bool set = ops[0]->tc_set;
+  if (force) {
+    tune = *force;
+    set = true;
+  } else if (!set) {
+    set = tune_lookup(ops, nrhs, n, prec, &tune);
   }
-  size_t smem = 0;
-  int nst = 0;
-  for (;;) {   // fall back to fewer points per stage if the ring does not fit
-    nst = tc_stages(g, t.pps, kSmemBudget / (size_t)t.ctas_per_sm, t.max_stages, &smem);
-    if (nst >= 2 || t.pps == 1) break;
-    t.pps = (t.pps + 1) / 2;
+  Batch bt;
+  bt.n = n;
+  bt.active = active;
+  PackBatch pb;
+  pb.n = n;
+  pb.active = active;
+  Geom g[MRHS_MAX_BATCH];
+  for (int i = 0; i < n; ++i) {
+    if (!tc_supported(ops[i], prec, nrhs[i]))
+      return fail(MRHS_ERR_UNSUPPORTED, "tensor-core shape of a batch member");
+    MRHS_TRY(prepare(ops[i], prec, false, X[i], Y[i], nrhs[i], set ? tune.pps : 0, s, &bt.p[i],
+                     &pb.p[i], &g[i]));
   }
-  if (nst < 2 && t.ctas_per_sm > 1) {
-    t.ctas_per_sm = 1;
-    nst = tc_stages(g, t.pps, kSmemBudget, t.max_stages, &smem);
-  }
-  if (nst < 2) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core ring does not fit");
-  Stencil stn;
-  for (int mu = 0; mu < 4; ++mu) stn.L[mu] = op->L[mu];
-  stn.sign = dag ? -1 : 1;
-  for (int p = 0; p < op->npts; ++p)
-    for (int mu = 0; mu < 4; ++mu) stn.d[p][mu] = op->disp[p][mu];
-  const int64_t cap = (int64_t)sms * t.ctas_per_sm;
-  const int64_t grid = op->V < cap ? op->V : cap;
-  timer_mark(op, prec, s);
-  int st = MRHS_OK;
-  if (prec == MRHS_PREC_BF16)
-    st = launch_tc<true, false, false>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
-                                       smem, grid, s);
-  else if (prec == MRHS_PREC_FP16)
-    st = launch_tc<false, false, false>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
-                                        smem, grid, s);
-  else if (prec == MRHS_PREC_FP16X)
-    st = launch_tc<false, true, false>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
-                                       smem, grid, s);
-  else
-    st = launch_tc<false, true, true>(img, xb, sigma, X, Y, stn, op->V, op->npts, g, nst, t.pps,
-                                      smem, grid, s);
-  timer_mark(op, prec, s);
-  MRHS_TRY(st);
-  MRHS_CUDA_TRY(cudaGetLastError());
-  return MRHS_OK;
+  MRHS_TRY(pack_batch(pb, prec, s));
+  // a single problem keeps its operator's kernel timer
+  return run_batch(bt, g, prec, tune, set, prec, n == 1 ? ops[0] : nullptr, s);
 }
 
 unsigned tc_read_and_clear_error() {

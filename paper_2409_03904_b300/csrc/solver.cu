@@ -19,6 +19,7 @@
 // scaling to complex64, an inner preconditioned block CG on complex64 vectors
 // with the FP32 operator and a BF16/FP16 (or FP32) Chebyshev preconditioner,
 // Grams accumulated in FP64 and factorised in FP64, and x += rho e in FP64.
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -867,6 +868,410 @@ int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* 
                              (double2*)(base + 2 * stride));
   return cheb_run<float2>(cx, prec, lo, hi, order, (const float2*)X, (float2*)P, (float2*)base,
                           (float2*)(base + stride), (float2*)(base + 2 * stride));
+}
+
+
+// ---------------------------------------------------------------- batches
+// Many independent problems solved side by side (mixed mode, Chebyshev-
+// preconditioned).  The problems advance in lockstep: every operator
+// application of an iteration -- the Krylov step and each Chebyshev step --
+// is one persistent tensor-core launch over the sites of all active problems
+// (tc_apply_batch); the per-problem nrhs x nrhs algebra and block updates are
+// ordinary launches in the same stream.  Chunks of check_every iterations are
+// captured once as a CUDA graph and replayed.  A problem whose inner solve
+// reached its target (or stalled) is masked out of the batched launches
+// through a device flag; its search block and rank are zeroed, so the
+// remaining iterations of the chunk leave it unchanged.
+namespace {
+
+struct BatchProb {
+  Ctx cx;
+  SolveBufs sb;
+  std::vector<double> bnorm, rnorm, target, est;
+  double lo = 0, hi = 0, best = 1e300;
+  int iters = 0, cycles = 0, flag = 0, stalled = 0;
+  bool done = false, in_cycle = false, inner_live = false;
+  double cycle_resid[MRHS_MAX_CYCLES] = {0};
+  int cycle_iters[MRHS_MAX_CYCLES] = {0}, cycle_flag[MRHS_MAX_CYCLES] = {0};
+};
+
+}  // namespace
+
+int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* const* X,
+                const int32_t* nrhs, const mrhs_solve_params& p, mrhs_solve_info* infos,
+                cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<BatchProb> P(n);
+  int32_t* d_active = nullptr;
+  for (int i = 0; i < n; ++i) {
+    BatchProb& b = P[i];
+    Ctx& cx = b.cx;
+    cx.op = ops[i];
+    cx.s = s;
+    cx.R = nrhs[i];
+    cx.N = ops[i]->V * ops[i]->nb;
+    cx.tau = p.breakdown_tau > 0 ? p.breakdown_tau : 1e-12;
+    const int64_t nn = cx.N * cx.R;
+    b.sb.carve(cx, cx.R, nn, true, true);
+    int32_t* act = nullptr;
+    cx.alloc(&act, MRHS_MAX_BATCH);
+    MRHS_TRY(ops[i]->ws_solve.ensure(cx.used));
+    cx.base = (char*)ops[i]->ws_solve.ptr;
+    cx.used = 0;
+    b.sb.carve(cx, cx.R, nn, true, true);
+    cx.alloc(&act, MRHS_MAX_BATCH);
+    if (i == 0) d_active = act;
+    MRHS_CUDA_TRY(cudaMemsetAsync(cx.st, 0, sizeof(Small), s));
+    b.bnorm.resize(cx.R);
+    b.rnorm.resize(cx.R);
+    b.target.resize(cx.R);
+    b.est.resize(cx.R);
+    // Chebyshev interval of this problem
+    b.hi = p.cheb_hi;
+    if (b.hi <= 0.0) {
+      double& cached = ops[i]->lam_max[p.precond_prec];
+      if (!(cached > 0.0)) MRHS_TRY(lambda_max(ops[i], p.precond_prec, 40, s, &cached));
+      b.hi = 1.08 * cached;
+    }
+    b.lo = p.cheb_lo > 0.0 ? p.cheb_lo : b.hi / 400.0;
+    MRHS_TRY(cx.colnorms<double2>(B[i], b.sb.bnorm_d));
+    const int g = grid_for(nn);
+    { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X[i], b.sb.bnorm_d, cx.N, cx.R); ::mrhs::count_launch(); }
+    MRHS_CUDA_TRY(cudaMemcpyAsync(b.bnorm.data(), b.sb.bnorm_d, sizeof(double) * cx.R,
+                                  cudaMemcpyDeviceToHost, s));
+  }
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+
+  auto true_residual = [&](BatchProb& b, int i) -> int {
+    Ctx& cx = b.cx;
+    const int64_t nn = cx.N * cx.R;
+    MRHS_TRY(cx.apply(MRHS_PREC_FP64, X[i], b.sb.r64));
+    { k_sub<double2><<<grid_for(nn), kThreads, 0, s>>>(b.sb.r64, B[i], b.sb.r64, nn); ::mrhs::count_launch(); }
+    MRHS_TRY(cx.colnorms<double2>(b.sb.r64, b.sb.rnorm_d));
+    MRHS_CUDA_TRY(cudaMemcpyAsync(b.rnorm.data(), b.sb.rnorm_d, sizeof(double) * cx.R,
+                                  cudaMemcpyDeviceToHost, s));
+    return MRHS_OK;
+  };
+  auto problem_done = [&](BatchProb& b) {
+    for (int j = 0; j < b.cx.R; ++j)
+      if (b.bnorm[j] > 0 && !(b.rnorm[j] <= p.tol * b.bnorm[j])) return false;
+    return true;
+  };
+  // initial residuals: a zero guess needs no operator application
+  for (int i = 0; i < n; ++i) {
+    BatchProb& b = P[i];
+    std::vector<double> xn(b.cx.R);
+    MRHS_TRY(b.cx.colnorms<double2>(X[i], b.sb.rnorm_d));
+    MRHS_CUDA_TRY(cudaMemcpyAsync(xn.data(), b.sb.rnorm_d, sizeof(double) * b.cx.R,
+                                  cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    bool zero = true;
+    for (double v : xn) zero = zero && v == 0.0;
+    if (zero) {
+      MRHS_CUDA_TRY(cudaMemcpyAsync(b.sb.r64, B[i], sizeof(double2) * b.cx.N * b.cx.R,
+                                    cudaMemcpyDeviceToDevice, s));
+      b.rnorm = b.bnorm;
+    } else {
+      MRHS_TRY(true_residual(b, i));
+    }
+  }
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  for (auto& b : P) b.done = problem_done(b);
+
+  const int kp = p.krylov_prec, pp = p.precond_prec, order = p.cheb_order;
+  const int every = p.check_every > 1 ? p.check_every : 2;
+  std::vector<int32_t> h_active(MRHS_MAX_BATCH, 0);
+  std::vector<std::vector<double>> coef(n);
+  for (int i = 0; i < n; ++i) cheb_coeffs(P[i].lo, P[i].hi, order, coef[i]);
+  int total_iters = 0;
+
+  for (int cycle = 0; cycle < p.max_cycles; ++cycle) {
+    // problems taking part in this refinement cycle
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i) {
+      P[i].in_cycle = !P[i].done;
+      if (P[i].in_cycle) idx.push_back(i);
+    }
+    if (idx.empty() || total_iters >= p.maxiter) break;
+    const int m = (int)idx.size();
+    std::vector<mrhs_op_s*> bops(m);
+    std::vector<int32_t> bR(m);
+    for (int k = 0; k < m; ++k) {
+      const int i = idx[k];
+      BatchProb& b = P[i];
+      Ctx& cx = b.cx;
+      bops[k] = ops[i];
+      bR[k] = cx.R;
+      std::vector<double> rho(cx.R);
+      for (int j = 0; j < cx.R; ++j) {
+        rho[j] = (b.bnorm[j] > 0 && b.rnorm[j] > p.tol * b.bnorm[j]) ? b.rnorm[j] : 0.0;
+        const double want = rho[j] > 0 ? 0.5 * p.tol * b.bnorm[j] / rho[j] : 1.0;
+        b.target[j] = std::fmax(p.inner_tol, want);
+      }
+      const int64_t nn = cx.N * cx.R;
+      MRHS_CUDA_TRY(cudaMemcpyAsync(b.sb.rho_d, rho.data(), sizeof(double) * cx.R,
+                                    cudaMemcpyHostToDevice, s));
+      MRHS_CUDA_TRY(cudaMemcpyAsync(cx.st->target, b.target.data(), sizeof(double) * cx.R,
+                                    cudaMemcpyHostToDevice, s));
+      MRHS_CUDA_TRY(cudaMemsetAsync(&cx.st->flag, 0, sizeof(int), s));
+      { k_scale_to_c64<<<grid_for(nn), kThreads, 0, s>>>(b.sb.f32, b.sb.r64, b.sb.rho_d, cx.N, cx.R); ::mrhs::count_launch(); }
+      MRHS_CUDA_TRY(cudaMemsetAsync(b.sb.e32, 0, sizeof(float2) * nn, s));
+      // zero inner guess: r0 = F
+      MRHS_CUDA_TRY(cudaMemcpyAsync(b.sb.b32.q, b.sb.f32, sizeof(float2) * nn,
+                                    cudaMemcpyDeviceToDevice, s));
+      b.inner_live = true;
+      b.flag = 0;
+      b.stalled = 0;
+      b.best = 1e300;
+      h_active[k] = 1;
+    }
+    for (int k = m; k < MRHS_MAX_BATCH; ++k) h_active[k] = 0;
+    MRHS_CUDA_TRY(cudaMemcpyAsync(d_active, h_active.data(), sizeof(int32_t) * MRHS_MAX_BATCH,
+                                  cudaMemcpyHostToDevice, s));
+
+    // batched operator application: inputs in[k], outputs out[k]
+    std::vector<const void*> in(m);
+    std::vector<void*> out(m);
+    auto bapply = [&](int prec) -> int {
+      for (int k = 0; k < m; ++k) P[idx[k]].cx.applies[prec]++;
+      return tc_apply_batch(bops.data(), m, prec, in.data(), out.data(), bR.data(), d_active, s);
+    };
+    // batched Chebyshev: P_k = p(H_k) X_k for all problems of the cycle
+    auto bcheb = [&](float2* const* Xs, float2* const* Ps) -> int {
+      std::vector<const float2*> Tprev(m);
+      std::vector<float2*> Tcur(m);
+      for (int k = 0; k < m; ++k) {
+        in[k] = Xs[k];
+        out[k] = P[idx[k]].sb.b32.cw;
+      }
+      MRHS_TRY(bapply(pp));
+      for (int k = 0; k < m; ++k) {
+        BatchProb& b = P[idx[k]];
+        const std::vector<double>& c = coef[idx[k]];
+        const double a = 2.0 / (b.hi - b.lo), bb = -(b.hi + b.lo) / (b.hi - b.lo);
+        const int64_t nn = b.cx.N * b.cx.R;
+        { k_cheb_first<float2><<<grid_for(nn), kThreads, 0, s>>>(b.sb.b32.c1, Ps[k], b.sb.b32.cw, Xs[k], a, bb, c[0], order > 0 ? c[1] : 0.0, nn); ::mrhs::count_launch(); }
+        Tprev[k] = Xs[k];
+        Tcur[k] = b.sb.b32.c1;
+      }
+      for (int j = 2; j <= order; ++j) {
+        for (int k = 0; k < m; ++k) {
+          in[k] = Tcur[k];
+          out[k] = P[idx[k]].sb.b32.cw;
+        }
+        MRHS_TRY(bapply(pp));
+        for (int k = 0; k < m; ++k) {
+          BatchProb& b = P[idx[k]];
+          const std::vector<double>& c = coef[idx[k]];
+          const double a = 2.0 / (b.hi - b.lo), bb = -(b.hi + b.lo) / (b.hi - b.lo);
+          const int64_t nn = b.cx.N * b.cx.R;
+          float2* dst = (Tprev[k] == Xs[k]) ? b.sb.b32.c2 : const_cast<float2*>(Tprev[k]);
+          { k_cheb_step<float2><<<grid_for(nn), kThreads, 0, s>>>(dst, Ps[k], b.sb.b32.cw, Tcur[k], Tprev[k], a, bb, c[j], nn); ::mrhs::count_launch(); }
+          Tprev[k] = Tcur[k];
+          Tcur[k] = dst;
+        }
+      }
+      MRHS_CUDA_TRY(cudaGetLastError());
+      return MRHS_OK;
+    };
+
+    // start: Z0 = M^-1 r0, C0 from Z0^dag r0, q <- q W, Q <- Q W, D <- Q
+    {
+      std::vector<float2*> Xs(m), Ps(m);
+      for (int k = 0; k < m; ++k) {
+        Xs[k] = P[idx[k]].sb.b32.q;
+        Ps[k] = P[idx[k]].sb.b32.Q;
+      }
+      MRHS_TRY(bcheb(Xs.data(), Ps.data()));
+      for (int k = 0; k < m; ++k) {
+        BatchProb& b = P[idx[k]];
+        Ctx& cx = b.cx;
+        MRHS_TRY(cx.gram<float2>(b.sb.b32.Q, b.sb.b32.q, cx.st->G));
+        MRHS_TRY(cx.small_launch(0));
+        MRHS_CUDA_TRY(cudaMemsetAsync(b.sb.b32.D, 0, sizeof(float2) * cx.N * cx.R, s));
+        MRHS_CUDA_TRY(cudaMemsetAsync(cx.st->S, 0, sizeof(double2) * 64 * 64, s));
+        MRHS_TRY(cx.rotate<float2>(b.sb.b32.q, b.sb.b32.Q, b.sb.b32.D));
+      }
+    }
+    auto body = [&]() -> int {
+      for (int k = 0; k < m; ++k) {
+        in[k] = P[idx[k]].sb.b32.D;
+        out[k] = P[idx[k]].sb.b32.z;
+      }
+      MRHS_TRY(bapply(kp));                                          // z = H D
+      std::vector<float2*> Xs(m), Ps(m);
+      for (int k = 0; k < m; ++k) {
+        Xs[k] = P[idx[k]].sb.b32.z;
+        Ps[k] = P[idx[k]].sb.b32.Zz;
+      }
+      MRHS_TRY(bcheb(Xs.data(), Ps.data()));                         // Z = M^-1 z
+      for (int k = 0; k < m; ++k) {
+        BatchProb& b = P[idx[k]];
+        Ctx& cx = b.cx;
+        BcgBufs<float2>& q = b.sb.b32;
+        MRHS_TRY(cx.gram<float2>(q.D, q.z, cx.st->G));
+        MRHS_TRY(cx.small_launch(1));
+        MRHS_TRY(axpy(b.sb.e32, q.D, cx.st->MC, 1.0, cx.N, cx.R, cx.R, MRHS_C64, s));
+        MRHS_TRY(axpy(q.q, q.z, cx.st->negM, 1.0, cx.N, cx.R, cx.R, MRHS_C64, s));
+        MRHS_TRY(axpy(q.Q, q.Zz, cx.st->negM, 1.0, cx.N, cx.R, cx.R, MRHS_C64, s));
+        MRHS_TRY(cx.gram<float2>(q.Q, q.q, cx.st->G));
+        MRHS_TRY(cx.gram<float2>(q.q, q.q, cx.st->G2));
+        MRHS_TRY(cx.small_launch(2, 1));
+        MRHS_TRY(cx.rotate<float2>(q.q, q.Q, q.D));
+      }
+      return MRHS_OK;
+    };
+
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ok = p.use_graph != 0;
+    int64_t graph_launches = 0;
+    std::vector<std::array<int64_t, MRHS_NUM_PREC>> graph_applies(m);
+    int it = 0;
+    const int maxit = p.maxiter - total_iters;
+    const int stall_checks = (32 + every - 1) / every;
+    while (it < maxit) {
+      const int chunk = (maxit - it) < every ? (maxit - it) : every;
+      if (graph_ok && it >= 1 && chunk == every) {
+        if (!exec) {
+          std::vector<std::array<int64_t, MRHS_NUM_PREC>> before(m);
+          for (int k = 0; k < m; ++k)
+            for (int q = 0; q < MRHS_NUM_PREC; ++q) before[k][q] = P[idx[k]].cx.applies[q];
+          const int64_t l0 = launch_count();
+          cudaGraph_t gr = nullptr;
+          int st = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess
+                       ? MRHS_OK : MRHS_ERR_CUDA;
+          for (int j = 0; j < chunk && st == MRHS_OK; ++j) st = body();
+          const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+          const bool ok = st == MRHS_OK && ce == cudaSuccess && gr &&
+                          cudaGraphInstantiate(&exec, gr, 0) == cudaSuccess;
+          if (gr) cudaGraphDestroy(gr);
+          for (int k = 0; k < m; ++k)
+            for (int q = 0; q < MRHS_NUM_PREC; ++q) {
+              graph_applies[k][q] = P[idx[k]].cx.applies[q] - before[k][q];
+              P[idx[k]].cx.applies[q] = before[k][q];
+            }
+          graph_launches = launch_count() - l0;
+          add_launches(-graph_launches);
+          if (!ok) {
+            cudaGetLastError();
+            if (exec) cudaGraphExecDestroy(exec);
+            exec = nullptr;
+            graph_ok = false;
+            continue;
+          }
+        }
+        if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+          cudaGraphExecDestroy(exec);
+          return fail(MRHS_ERR_CUDA, "batched graph launch failed");
+        }
+        add_launches(graph_launches);
+        for (int k = 0; k < m; ++k)
+          for (int q = 0; q < MRHS_NUM_PREC; ++q) P[idx[k]].cx.applies[q] += graph_applies[k][q];
+      } else {
+        for (int j = 0; j < chunk; ++j) {
+          const int st = body();
+          if (st != MRHS_OK) {
+            if (exec) cudaGraphExecDestroy(exec);
+            return st;
+          }
+        }
+      }
+      it += chunk;
+      for (int k = 0; k < m; ++k) {
+        BatchProb& b = P[idx[k]];
+        if (!b.inner_live) continue;
+        MRHS_CUDA_TRY(cudaMemcpyAsync(&b.flag, &b.cx.st->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MRHS_CUDA_TRY(cudaMemcpyAsync(b.est.data(), b.cx.st->est, sizeof(double) * b.cx.R,
+                                      cudaMemcpyDeviceToHost, s));
+      }
+      MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+      bool any = false, changed = false;
+      for (int k = 0; k < m; ++k) {
+        BatchProb& b = P[idx[k]];
+        if (!b.inner_live) continue;
+        b.iters += chunk;
+        bool stop = (b.flag & (1 | 4)) != 0;
+        if (!stop) {
+          double worst = 0.0;
+          for (int j = 0; j < b.cx.R; ++j)
+            if (b.target[j] > 0.0) worst = std::fmax(worst, b.est[j] / b.target[j]);
+          if (worst < 0.7 * b.best) {
+            b.best = worst;
+            b.stalled = 0;
+          } else if (++b.stalled >= stall_checks) {
+            b.flag |= 8;
+            stop = true;
+          }
+        }
+        if (stop) {
+          // freeze: out of the batched launches, zero search block and rank
+          b.inner_live = false;
+          h_active[k] = 0;
+          changed = true;
+          MRHS_CUDA_TRY(cudaMemsetAsync(b.sb.b32.D, 0, sizeof(float2) * b.cx.N * b.cx.R, s));
+          MRHS_CUDA_TRY(cudaMemsetAsync(&b.cx.st->rank, 0, sizeof(int32_t), s));
+        } else {
+          any = true;
+        }
+      }
+      if (changed)
+        MRHS_CUDA_TRY(cudaMemcpyAsync(d_active, h_active.data(), sizeof(int32_t) * MRHS_MAX_BATCH,
+                                      cudaMemcpyHostToDevice, s));
+      if (!any) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    total_iters += it;
+    // FP64 outer step for every problem of the cycle
+    for (int k = 0; k < m; ++k) {
+      const int i = idx[k];
+      BatchProb& b = P[i];
+      Ctx& cx = b.cx;
+      { k_update_x<<<grid_for(cx.N * cx.R), kThreads, 0, s>>>(X[i], b.sb.e32, b.sb.rho_d, cx.N, cx.R); ::mrhs::count_launch(); }
+      MRHS_TRY(true_residual(b, i));
+    }
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = 0; k < m; ++k) {
+      BatchProb& b = P[idx[k]];
+      if (b.cycles < MRHS_MAX_CYCLES) {
+        double mr = 0.0;
+        for (int j = 0; j < b.cx.R; ++j)
+          if (b.bnorm[j] > 0) mr = std::fmax(mr, b.rnorm[j] / b.bnorm[j]);
+        b.cycle_resid[b.cycles] = mr;
+        b.cycle_iters[b.cycles] = b.iters;
+        b.cycle_flag[b.cycles] = b.flag;
+      }
+      b.cycles++;
+      b.done = problem_done(b) || (b.flag & 4);
+    }
+  }
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  int worst = MRHS_OK;
+  for (int i = 0; i < n; ++i) {
+    BatchProb& b = P[i];
+    const int status = (b.flag & 4) ? MRHS_ERR_NONFINITE : (problem_done(b) ? MRHS_OK : MRHS_ERR_NOT_CONVERGED);
+    if (status != MRHS_OK && worst == MRHS_OK) worst = status;
+    if (!infos) continue;
+    mrhs_solve_info& inf = infos[i];
+    inf.status = status;
+    inf.iters = b.iters;
+    inf.cycles = b.cycles;
+    inf.nrhs = b.cx.R;
+    for (int q = 0; q < MRHS_NUM_PREC; ++q) inf.applies[q] = b.cx.applies[q];
+    for (int j = 0; j < MRHS_MAX_RHS; ++j)
+      inf.resid[j] = j < b.cx.R ? (b.bnorm[j] > 0 ? b.rnorm[j] / b.bnorm[j] : 0.0) : 0.0;
+    inf.cheb_lo = b.lo;
+    inf.cheb_hi = b.hi;
+    inf.ms_total = ms;
+    inf.krylov_prec = kp;
+    inf.precond_prec = pp;
+    for (int c = 0; c < MRHS_MAX_CYCLES; ++c) {
+      inf.cycle_iters[c] = c < b.cycles ? b.cycle_iters[c] - (c ? b.cycle_iters[c - 1] : 0) : 0;
+      inf.cycle_resid[c] = b.cycle_resid[c];
+      inf.cycle_flag[c] = b.cycle_flag[c];
+    }
+  }
+  if (worst != MRHS_OK) set_error(worst == MRHS_ERR_NONFINITE ? "non-finite value in a batched solve" : "a batched problem did not converge");
+  return worst;
 }
 
 }  // namespace mrhs

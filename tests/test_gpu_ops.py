@@ -142,7 +142,9 @@ def test_tc_repeat_and_large_nrhs_stream(mrhs):
 
 
 @pytest.mark.parametrize("N,rx,ry", [(1, 1, 1), (1000, 4, 4), (33333, 12, 7), (200000, 32, 32),
-                                     (5, 64, 64), (0, 3, 3)])
+                                     (5, 64, 64), (0, 3, 3), (70001, 1, 9), (4097, 16, 3),
+                                     (100000, 24, 24), (12345, 64, 1), (777, 9, 64),
+                                     (300000, 1, 1)])
 def test_block_inner(mrhs, N, rx, ry):
     rng = np.random.default_rng(N + rx)
     X = rng.standard_normal((N, rx)) + 1j * rng.standard_normal((N, rx))
