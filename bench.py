@@ -191,6 +191,21 @@ def fp64_iteration_count(name):
     return None
 
 
+def dram_traffic(prec, name):
+    """Measured DRAM bytes per launch of the operator kernel (ncu), from
+    profiles/dram_traffic_per_launch.txt, or None if not captured."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic_per_launch.txt")
+    try:
+        with open(p) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 3 and parts[0] == prec and parts[1] == name:
+                    return float(parts[2])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def run_reference(a, w, shift):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -374,7 +389,7 @@ def main():
         byts = op_bytes(w, R, a.precond)
         ach = byts / (per * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "kernel": f"tcgen05 {a.precond} coarse operator",
+                "frac": ach / hbm, "traffic": dram_traffic(a.precond, w["name"]), "kernel": f"tcgen05 {a.precond} coarse operator",
                 "algorithmic_bytes": byts, "launch_ms": per, "launches": n16,
                 "peak_kind": f"{peak_kind} copy bandwidth"}
 
