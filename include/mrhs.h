@@ -196,8 +196,8 @@ typedef struct {
   int32_t precond;      /* 0: BlockCGrQ (Fig. 2 left); 1: Chebyshev-preconditioned
                            BlockCGrQ (Fig. 2 right) */
   int32_t precond_prec; /* MRHS_PREC_* of the Chebyshev operator applications;
-                           -1 (default): FP16X if built and nrhs <= 32, else
-                           FP16, BF16 or FP32, the first one built */
+                           -1 (default): FP16X, FP16, BF16, TC32 or FP32, the
+                           first one built that fits nrhs (FP16X/TC32: <= 32) */
   int32_t cheb_order;   /* polynomial degree */
   double cheb_lo;       /* Chebyshev interval; cheb_hi <= 0: hi = 1.08 x power- */
   double cheb_hi;       /*   method estimate; cheb_lo <= 0: lo = hi / 400 */

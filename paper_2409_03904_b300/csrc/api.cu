@@ -398,7 +398,7 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
   mrhs_solve_params q = p;   // resolve the automatic precision choices
   auto built = [&](int pr) { return (op->prec_mask & MRHS_PREC_BIT(pr)) != 0; };
   auto fits = [&](int pr) {
-    return !(pr == MRHS_PREC_FP16X || pr == MRHS_PREC_TC32) || nrhs <= 32;
+    return pr < MRHS_PREC_BF16 || tc_supported(op, pr, nrhs) != 0;
   };
   if (q.mode == MRHS_SOLVE_MIXED) {
     if (q.krylov_prec < 0)
@@ -406,7 +406,7 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
     if (q.krylov_prec != MRHS_PREC_FP32 && q.krylov_prec != MRHS_PREC_TC32)
       return fail(MRHS_ERR_INVALID_ARG, "krylov_prec must be FP32 or TC32");
     if (!built(q.krylov_prec) || !fits(q.krylov_prec))
-      return fail(MRHS_ERR_UNSUPPORTED, "mixed mode needs the FP32 (or TC32, nrhs <= 32) operator");
+      return fail(MRHS_ERR_UNSUPPORTED, "mixed mode needs the FP32 or TC32 operator");
   }
   if (q.precond && q.precond_prec < 0) {
     const int order[] = {MRHS_PREC_FP16X, MRHS_PREC_FP16, MRHS_PREC_BF16, MRHS_PREC_TC32,
@@ -421,7 +421,7 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
     if (pp.precond_prec < 0 || pp.precond_prec >= MRHS_NUM_PREC)
       return fail(MRHS_ERR_INVALID_ARG, "precond_prec");
     if (!fits(pp.precond_prec))
-      return fail(MRHS_ERR_UNSUPPORTED, "FP16X/TC32 preconditioner needs nrhs <= 32");
+      return fail(MRHS_ERR_UNSUPPORTED, "preconditioner precision does not fit this shape");
     if (!built(pp.precond_prec))
       return fail(MRHS_ERR_UNSUPPORTED, "preconditioner precision not built");
     if (pp.mode == MRHS_SOLVE_FP64 && pp.precond_prec != MRHS_PREC_FP64)

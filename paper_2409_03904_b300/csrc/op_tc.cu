@@ -10,28 +10,33 @@
 //   Y(x) = s_x sigma_r sum_p Ahat_p(x) Xhat(x + delta_p) + d_x X(x),
 // with the sum accumulated in FP32 in tensor memory.
 //
-// Complex GEMM by real splitting.  For one site and stencil point the
-// complex product A (nb x nb) X (nb x R) is the real product
-//     D (2R x nb) = XB (2R x 2nb) . AB^T,   AB = [Re A | Im A]   (nb x 2nb)
-//     XB rows r < R:  [Re X[:,r] | -Im X[:,r]]  -> D[r][a]   = Re Y[a][r]
-//     XB rows R + r:  [Im X[:,r] |  Re X[:,r]]  -> D[R+r][a] = Im Y[a][r]
-// so the streamed coefficient block enters unexpanded (its bytes are the HBM
-// traffic that bounds the kernel) and the sign/duplication goes to the small
-// X operand, which is packed once per call and re-read from L2 by the 9 or
-// 81 sites that neighbour it.  M = 128, N = nb rounded up to 16, K = 2 nb,
-// summed over all stencil points into one accumulator.
+// Complex GEMM with the real and imaginary coefficient blocks stacked along
+// N.  For one site and stencil point, with the coefficient tile
+//     AT = [Re A ; Im A]   (2 nb8 rows: rows a < nb8 = Re A[a][:], rows
+//                           nb8 + a = Im A[a][:]; K = nb16 columns over b)
+// and input rows Xr_r = Re X[:,r], Xi_r = Im X[:,r] (K = nb16 columns),
+//     D (rows x 2 nb8) = XT . AT^T
+// gives on an Xr row the products Xr.Re A^T | Xr.Im A^T and on an Xi row
+// Xi.Re A^T | Xi.Im A^T, so
+//     Re Y[a][r] = D[Xr_r][a] - D[Xi_r][nb8 + a]
+//     Im Y[a][r] = D[Xr_r][nb8 + a] + D[Xi_r][a].
+// Neither operand is duplicated and one MMA of N = 2 nb8 covers both parts:
+// M = 128, N = 2 nb8, K = 16, nb16/16 MMAs per stencil point, summed over all
+// points into one accumulator.  The tensor core reads the whole 128-row A
+// operand from shared memory for every MMA, so few wide MMAs (large N) keep
+// that read traffic, which shares shared-memory bandwidth with the TMA
+// writes, low.  The epilogue combines the Xi row's values with the Xr row's
+// through shared memory.
 //
-// Split forms (up to 32 right-hand sides, so 2R <= 64): a value u is held as
-// hi = fp16(u), lo = fp16((u - hi) 2^11).  XSPLIT puts the input's lo rows in
-// rows 64..127 of the same M = 128 operand (rows that are idle otherwise),
-// so one MMA gives both Ahi Xhi (rows < 64) and Ahi Xlo (rows >= 64); ASPLIT
-// adds a second MMA per step against the coefficients' lo tile into a second
-// accumulator, whose rows < 64 are Alo Xhi.  The epilogue combines
-//   D1[m] + 2^-11 (D1[64 + m] + D2[m]),
-// fetching D1[64 + m] from the warps that own those TMEM lanes through
-// shared memory.  FP16X = FP16 coefficients with a two-term input (linear in
-// X to ~2^-22, for a stationary preconditioner); TC32 = both operands in two
-// terms (FP32-class operator, same bytes per coefficient as complex64).
+// Split forms (up to 32 right-hand sides): a value u is held as hi = fp16(u),
+// lo = fp16((u - hi) 2^11).  XSPLIT adds the input's lo rows (Xr_lo, Xi_lo)
+// as two more row groups of the same operand, so one MMA also gives Ahi Xlo;
+// ASPLIT adds a second MMA per step against the coefficients' lo tile into a
+// second accumulator (Alo Xhi on the hi rows).  The epilogue adds 2^-11 times
+// the lo contributions.  FP16X = FP16 coefficients with a two-term input
+// (linear in X to ~2^-22, for a stationary preconditioner); TC32 = both
+// operands in two terms (FP32-class operator, same bytes per coefficient as
+// complex64).
 //
 // Both operands are pre-packed in global memory in the canonical K-major
 // no-swizzle tcgen05 layout (8 x 16-byte core matrices, K groups 128 bytes
@@ -39,16 +44,19 @@
 // per tile lands it ready for the MMA.  Element (row, k) of a tile with K
 // columns sits at byte (row/8)*(K/8)*128 + (k/8)*128 + (row%8)*16 + (k%8)*2.
 //
-// Kernel: persistent, two CTAs per SM by default (two independent rings),
+// Kernel: persistent, two CTAs per SM by default (two independent rings;
+// TC32, whose two double-buffered accumulators fill the tensor memory, runs
+// one),
 // warp-specialised:
 //   warp 0      TMA producer: per stage the coefficient tiles of `pps`
 //               consecutive stencil points of one site (contiguous, one bulk
 //               copy, L2 evict-first) and their neighbours' packed X tiles
 //               (L2 evict-last), into an nstage ring of shared memory
 //   warp 1      allocates TMEM, issues tcgen05.mma (one elected thread) into
-//               two alternating accumulators, commits stage releases
-//   warps 2-5   epilogue: tcgen05.ld of their 32-lane quarter, scales, adds
-//               d_x X(x) (loaded before the wait), stores complex64 Y
+//               two alternating sets of accumulators, commits stage releases
+//   warps 2-5   epilogue: tcgen05.ld of their 32-lane quarter in 8-column
+//               chunks, exchanges the Xi and lo rows' contributions through
+//               shared memory, scales, adds d_x X(x), stores complex64 Y
 // Every mbarrier wait is bounded (1 s); on expiry the kernel records an
 // error, drains its own copies, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -66,16 +74,17 @@ __device__ unsigned int g_tc_error = 0;
 namespace {
 
 constexpr int kThreadsTc = 192;
-constexpr int kAccCols = 64;     // TMEM columns per accumulator (n_mma <= 64)
+constexpr int kAccCols = 128;    // TMEM columns per accumulator (n_mma <= 128)
+constexpr int kChunk = 8;        // epilogue columns per tcgen05.ld
+constexpr int kExFloats = 96 * 2 * kChunk;   // one exchange buffer (3 x 32 or 64 rows)
 constexpr int kM = 128;
-constexpr int kLoRowMax = 64;    // last possible first row of the input's lo term (XSPLIT)
 constexpr size_t kSmemBudget = 220 * 1024;   // dynamic shared memory per SM
+constexpr size_t kSmemOneCta = 120 * 1024;   // at least this much keeps a CTA alone on its SM
 constexpr float kLoScale = 1.0f / 2048.0f;   // 2^-11
 
 struct Geom {
-  int nb, nbp8, K, n_mma;   // K = 2 nbp8
-  int R, xrows;             // rows of a packed input tile
-  int lo_row;               // XSPLIT: first row of the lo term (round8(2R))
+  int nb, nbp8, nb16, K, n_mma;   // K = nb16, N = 2 nb8
+  int R, rb, xrows;         // rb = round8(R): rows per input row group
   int xsplit, asplit;
   uint32_t coef1;           // one coefficient tile (hi or lo)
   uint32_t coef_bytes;      // coefficient bytes per stencil point (x2 if asplit)
@@ -86,16 +95,16 @@ Geom make_geom(int nb, int R, bool xsplit, bool asplit) {
   Geom g;
   g.nb = nb;
   g.nbp8 = (nb + 7) / 8 * 8;
-  g.K = 2 * g.nbp8;
-  g.n_mma = (nb + 15) / 16 * 16;
+  g.nb16 = (nb + 15) / 16 * 16;
+  g.K = g.nb16;
+  g.n_mma = 2 * g.nbp8;
   g.R = R;
   g.xsplit = xsplit;
   g.asplit = asplit;
-  // XSPLIT stacks the lo term right after the hi term, so a tile holds
-  // 2 round8(2R) rows rather than all 128 rows of the MMA operand
-  g.lo_row = (2 * R + 7) / 8 * 8;
-  g.xrows = xsplit ? 2 * g.lo_row : g.lo_row;
-  g.coef1 = (uint32_t)g.nbp8 * g.K * 2;
+  // input row groups Xr, Xi (then Xr_lo, Xi_lo), round8(R) rows each
+  g.rb = (R + 7) / 8 * 8;
+  g.xrows = (xsplit ? 4 : 2) * g.rb;
+  g.coef1 = (uint32_t)(2 * g.nbp8) * g.K * 2;
   g.coef_bytes = g.coef1 * (asplit ? 2u : 1u);
   g.xb_bytes = (uint32_t)g.xrows * g.K * 2;
   g.sbo = (uint32_t)(g.K / 8) * 128;
@@ -196,25 +205,26 @@ __global__ void __launch_bounds__(256) k_pack_coef(const double2* __restrict__ A
   }
   __syncthreads();
   const double inv = 1.0 / s_scale;   // exact: power of two
-  const int tile_elems = g.nbp8 * g.K;
+  const int tile_elems = 2 * g.nbp8 * g.K;
   for (int p = 0; p < npts; ++p) {
     uint8_t* tile = codes + ((uint64_t)x * npts + p) * g.coef_bytes;
     for (int i = threadIdx.x; i < tile_elems; i += blockDim.x) {
-      const int a = i / g.K, k = i % g.K;
-      const int b = k < g.nbp8 ? k : k - g.nbp8;
+      const int row = i / g.K, b = i % g.K;
+      const bool re = row < g.nbp8;           // [Re A ; Im A], nb8 rows each
+      const int a = re ? row : row - g.nbp8;
       float v = 0.f;
       if (a < nb && b < nb) {
         double2 c = src(p, a, b);
         if (p == 0 && a == b) c.x -= d;
-        v = __double2float_rn((k < g.nbp8 ? c.x : c.y) * inv);
+        v = __double2float_rn((re ? c.x : c.y) * inv);
       }
       if (ASPLIT) {
         uint16_t hi, lo;
         split16(v, hi, lo);
-        *reinterpret_cast<uint16_t*>(tile + canon_off(a, k, g.K)) = hi;
-        *reinterpret_cast<uint16_t*>(tile + g.coef1 + canon_off(a, k, g.K)) = lo;
+        *reinterpret_cast<uint16_t*>(tile + canon_off(row, b, g.K)) = hi;
+        *reinterpret_cast<uint16_t*>(tile + g.coef1 + canon_off(row, b, g.K)) = lo;
       } else {
-        *reinterpret_cast<uint16_t*>(tile + canon_off(a, k, g.K)) = code16<BF16>(v);
+        *reinterpret_cast<uint16_t*>(tile + canon_off(row, b, g.K)) = code16<BF16>(v);
       }
     }
   }
@@ -283,8 +293,10 @@ __global__ void k_colscale(const __grid_constant__ PackBatch pb) {
   }
 }
 
-// Packed real-split input tiles, one [xrows][K] canonical tile per site.
-// XSPLIT: rows < 2R hold the hi term, rows lo_row + (0..2R-1) the lo term.
+// Packed input tiles, one [xrows][K] canonical tile per site: row group 0
+// holds Re X[:,r] / sigma_r in row r, group 1 Im X[:,r] / sigma_r (groups
+// round8(R) rows apart, K = nb16 columns over b); XSPLIT: groups 0, 1 the hi
+// terms, groups 2, 3 the lo terms.
 template <bool BF16, bool XSPLIT>
 __global__ void k_pack_xb(const __grid_constant__ PackBatch pb) {
   const int k = blockIdx.y;
@@ -302,24 +314,19 @@ __global__ void k_pack_xb(const __grid_constant__ PackBatch pb) {
     const int64_t x = u / units;
     const int w = (int)(u % units);
     const int kc = w / g.xrows, mrow = w % g.xrows;
-    const bool lo_term = XSPLIT && mrow >= g.lo_row;
-    const int m = lo_term ? mrow - g.lo_row : mrow;
-    uint16_t h[8];
-    const bool re_row = m < R;
-    const int r = re_row ? m : m - R;
-    const bool live = m < 2 * R;
+    const int grp = mrow / g.rb, r = mrow % g.rb;
+    const bool lo_term = XSPLIT && grp >= 2;
+    const bool imag = (grp & 1) != 0;
+    const bool live = r < R;
     const float inv = live ? 1.0f / sigma[r] : 0.f;
+    uint16_t h[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int kk = kc * 8 + e;
-      const bool first = kk < g.nbp8;
-      const int b = first ? kk : kk - g.nbp8;
+      const int b = kc * 8 + e;
       float v = 0.f;
       if (live && b < nb) {
         const float2 xv = X[(x * nb + b) * R + r];
-        if (re_row) v = first ? xv.x : -xv.y;
-        else v = first ? xv.y : xv.x;
-        v *= inv;
+        v = (imag ? xv.y : xv.x) * inv;
       }
       if (XSPLIT) {
         uint16_t hi, lo;
@@ -348,7 +355,7 @@ struct ProbDesc {
   const float* X;           // complex64 input (as floats), for d_x X(x)
   float* Y;                 // complex64 output
   int64_t V, item0;         // sites; first item of this problem in the work list
-  int32_t npts, nb, K, n_mma, R, pps, lo_row;
+  int32_t npts, nb, nbp8, K, n_mma, R, pps, rb;
   uint32_t coef1, coef_bytes, xb_bytes, sbo, idesc, xb_off;
   Stencil st;
 };
@@ -373,11 +380,12 @@ __device__ __forceinline__ bool item_live(const Batch& bt, int k) {
 }
 
 template <bool BF16, bool XSPLIT, bool ASPLIT>
-__global__ void __launch_bounds__(kThreadsTc, 2)
+__global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
     k_op_tc(const __grid_constant__ Batch bt, int nstages, uint32_t stage_bytes) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  constexpr int kAccStride = ASPLIT ? 2 * kAccCols : kAccCols;   // TMEM cols per buffer
-  constexpr uint32_t kTmemCols = ASPLIT ? 256u : 128u;
+  // accumulators per buffer: D (+ the lo-coefficient D2), kAccCols each
+  constexpr int kAccStride = (ASPLIT ? 2 : 1) * kAccCols;   // TMEM cols per buffer
+  constexpr uint32_t kTmemCols = 2u * kAccStride;           // two buffers
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + nstages;
   uint64_t* acc_full = empty + nstages;
@@ -388,7 +396,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
   // coefficient tiles (contiguous in HBM, one bulk copy) at the start, their
   // neighbour input tiles from the problem's `xb_off` on (one stage size for
   // all problems; each packs as many points as fit)
-  // XSPLIT exchange buffer for the lo rows, after the ring
+  // two exchange buffers (Xi and lo rows -> Xr rows), after the ring
   float* ex = reinterpret_cast<float*>(stages + (size_t)nstages * stage_bytes);
   __shared__ volatile int s_abort;
 
@@ -509,15 +517,14 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
             const uint32_t ab = sb + xb_off + (uint32_t)i * xbytes;
             const uint32_t first = (p0 > 0 || i > 0) ? 1u : 0u;
             for (int j = 0; j < nk; ++j) {
+              const uint32_t accum = (first || j > 0) ? 1u : 0u;
               const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)j * 256u, 128u, sbo);
-              const uint64_t bdesc = ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, sbo);
-              ptx::mma_f16(tmem_d, adesc, bdesc, idesc, (first || j > 0) ? 1u : 0u);
-              if (ASPLIT) {
-                const uint64_t ldesc =
-                    ptx::smem_desc(cb + coef1 + (uint32_t)j * 256u, 128u, sbo);
-                ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc, ldesc, idesc,
-                             (first || j > 0) ? 1u : 0u);
-              }
+              ptx::mma_f16(tmem_d, adesc, ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, sbo),
+                           idesc, accum);
+              if (ASPLIT)
+                ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc,
+                             ptx::smem_desc(cb + coef1 + (uint32_t)j * 256u, 128u, sbo), idesc,
+                             accum);
             }
           }
           ptx::mma_commit(&empty[s]);
@@ -536,92 +543,94 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
     // ---------------- epilogue, warps 2..5 -> TMEM lane quarters 2,3,0,1
     const int q = warp & 3;
     const int mrow = 32 * q + lane;              // D row = TMEM lane
-    int acc = 0;
+    int acc = 0, xbuf = 0;
     uint32_t aph = 0;
     for (int64_t t = blockIdx.x; t < bt.total; t += gridDim.x) {
       const int k = find_prob(bt, t);
       if (!item_live(bt, k)) continue;
       const ProbDesc& pd = bt.p[k];
       const int64_t x = t - pd.item0;
-      const int R = pd.R, nb = pd.nb, n_mma = pd.n_mma, lo_row = pd.lo_row;
-      // XSPLIT: rows [lo_row, 2 lo_row) carry the input's lo term
-      const bool lo_thread = XSPLIT && mrow >= lo_row && mrow < 2 * lo_row;
-      const int m = lo_thread ? mrow - lo_row : mrow;
-      float* Yp = pd.Y;
-      const bool valid = m < 2 * R;
-      const bool writer = valid && !lo_thread;
-      const int r = valid ? (m < R ? m : m - R) : 0;
-      const int part = m < R ? 0 : 1;
-      // the d_x X(x) term: load it before waiting, so its latency overlaps
-      // the site's MMAs
-      float xv[kAccCols];
+      const int R = pd.R, nb = pd.nb, nbp8 = pd.nbp8, rb = pd.rb;
+      const float2* Xp = reinterpret_cast<const float2*>(pd.X);
+      float2* Yp = reinterpret_cast<float2*>(pd.Y);
+      // row group of this lane: 0 Xr (writes Y), 1 Xi, 2 Xr_lo, 3 Xi_lo
+      const int grp = mrow / rb, r = mrow % rb;
+      const bool live = r < R && grp < (XSPLIT ? 4 : 2);
+      const bool writer = live && grp == 0;
+      const bool imag = (grp & 1) != 0;
+      const float gs = grp >= 2 ? kLoScale : 1.0f;
       float sc = 0.f, dx = 0.f;
       if (writer) {
-        const float* Xp = pd.X;
         sc = __ldg(&pd.scale[x]) * __ldg(&pd.sigma[r]);
         dx = __ldg(&pd.diag[x]);
-#pragma unroll
-        for (int a = 0; a < kAccCols; ++a)
-          xv[a] = a < nb ? __ldg(&Xp[(((int64_t)x * nb + a) * R + r) * 2 + part]) : 0.f;
       }
       const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort);
-      // give up together: tcgen05.ld below is .aligned per warp, and with
-      // XSPLIT the four epilogue warps also meet at named barriers
-      const bool all_got = XSPLIT ? ptx::epilogue_all(got) : __all_sync(0xffffffffu, got);
-      if (!all_got) {
+      // give up together: tcgen05.ld below is .aligned per warp and the four
+      // epilogue warps meet at named barriers
+      if (!ptx::epilogue_all(got)) {
         s_abort = 1;
         atomicOr(&g_tc_error, 4u);
         break;
       }
       ptx::tc_fence_after();
-      float v[kAccCols];
       const uint32_t taddr =
           tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccStride);
-      ptx::tmem_ld32_sync(taddr, v);
-      if (n_mma > 32) ptx::tmem_ld32_sync(taddr + 32u, v + 32);
-      if (ASPLIT) {      // + 2^-11 Alo Xhi, kept on the hi rows only
-        // tcgen05.ld is warp-collective (.sync.aligned): every lane loads,
-        // whatever its row, and the lo rows discard the value
-        float w[32];
-        ptx::tmem_ld32_sync(taddr + (uint32_t)kAccCols, w);
-        if (!lo_thread) {
+      for (int c0 = 0; c0 < nbp8; c0 += kChunk) {
+        // every lane loads (tcgen05.ld is warp-collective), whatever its row:
+        // u = D[.][a] (times Re A), w = D[.][nb8 + a] (times Im A)
+        float u[kChunk], w[kChunk];
+        ptx::tmem_ld8_sync(taddr + (uint32_t)c0, u);
+        ptx::tmem_ld8_sync(taddr + (uint32_t)(nbp8 + c0), w);
+        if (ASPLIT) {      // + 2^-11 Alo X, kept on the hi rows
+          float u2[kChunk], w2[kChunk];
+          ptx::tmem_ld8_sync(taddr + (uint32_t)(kAccCols + c0), u2);
+          ptx::tmem_ld8_sync(taddr + (uint32_t)(kAccCols + nbp8 + c0), w2);
+          if (grp < 2) {
 #pragma unroll
-          for (int a = 0; a < 32; ++a) v[a] = fmaf(kLoScale, w[a], v[a]);
-        }
-        if (n_mma > 32) {
-          ptx::tmem_ld32_sync(taddr + (uint32_t)kAccCols + 32u, w);
-          if (!lo_thread) {
-#pragma unroll
-            for (int a = 0; a < 32; ++a) v[32 + a] = fmaf(kLoScale, w[a], v[32 + a]);
+            for (int e = 0; e < kChunk; ++e) {
+              u[e] = fmaf(kLoScale, u2[e], u[e]);
+              w[e] = fmaf(kLoScale, w2[e], w[e]);
+            }
           }
         }
-      }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
-      if (XSPLIT) {
-        // lo rows hand 2^-11 Ahi Xlo to the thread of the matching hi row
-        if (lo_thread && valid) {
+        if (c0 + kChunk >= nbp8) {      // last chunk read: release the buffer
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
+        }
+        // contribution of this row to (Re Y, Im Y)[a][r]: an Xr row gives
+        // (u, w), an Xi row (-w, u); lo rows scaled by 2^-11
+        float* xe = ex + xbuf * kExFloats;
+        if (live && !writer) {
+          float* slot = xe + ((grp - 1) * rb + r) * 2 * kChunk;
 #pragma unroll
-          for (int a = 0; a < kAccCols; ++a)
-            if (a < nb) ex[m * kAccCols + a] = kLoScale * v[a];
+          for (int e = 0; e < kChunk; ++e) {
+            slot[e] = gs * (imag ? -w[e] : u[e]);
+            slot[kChunk + e] = gs * (imag ? u[e] : w[e]);
+          }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (writer) {
 #pragma unroll
-          for (int a = 0; a < kAccCols; ++a)
-            if (a < nb) v[a] += ex[m * kAccCols + a];
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-      }
-      if (writer) {
+          for (int gg = 1; gg < (XSPLIT ? 4 : 2); ++gg) {
+            const float* slot = xe + ((gg - 1) * rb + r) * 2 * kChunk;
 #pragma unroll
-        for (int a = 0; a < kAccCols; ++a) {
-          if (a < nb) {
-            const int64_t idx = (((int64_t)x * nb + a) * R + r) * 2 + part;
-            Yp[idx] = fmaf(sc, v[a], dx * xv[a]);
+            for (int e = 0; e < kChunk; ++e) {
+              u[e] += slot[e];
+              w[e] += slot[kChunk + e];
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < kChunk; ++e) {
+            const int a = c0 + e;
+            if (a < nb) {
+              const int64_t idx = ((int64_t)x * nb + a) * R + r;
+              const float2 xv = __ldg(&Xp[idx]);
+              Yp[idx] = make_float2(fmaf(sc, u[e], dx * xv.x), fmaf(sc, w[e], dx * xv.y));
+            }
           }
         }
+        xbuf ^= 1;      // the next chunk writes the other buffer
       }
       if (++acc == 2) { acc = 0; aph ^= 1u; }
     }
@@ -658,7 +667,8 @@ int plan_ring(const Geom* g, int* pps, const int* npts, int n, size_t budget, in
     xs = xs || g[i].xsplit;
   }
   tail += 1024;
-  if (xs) tail += (size_t)kLoRowMax * kAccCols * sizeof(float);
+  tail += 2 * (size_t)kExFloats * sizeof(float);
+  (void)xs;
   if (budget < 1024 + tail + 2 * stage) return 0;
   int ns = (int)((budget - 1024 - tail) / stage);
   if (ns > max_stages) ns = max_stages;
@@ -737,7 +747,8 @@ int prepare(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
   pd->K = g.K;
   pd->n_mma = g.n_mma;
   pd->R = nrhs;
-  pd->lo_row = g.lo_row;
+  pd->nbp8 = g.nbp8;
+  pd->rb = g.rb;
   pd->pps = pps_req > 0 ? pps_req : default_pps(g);
   if (pd->pps > op->npts) pd->pps = op->npts;
   pd->coef1 = g.coef1;
@@ -771,7 +782,10 @@ int pack_batch(const PackBatch& pb, int prec, cudaStream_t s) {
 
 int run_batch(Batch& bt, Geom* geoms, int prec, const TcTune& tune, bool tune_set, int timer_prec,
               mrhs_op_s* timer_op, cudaStream_t s) {
-  int ctas = tune_set ? tune.ctas_per_sm : 2;
+  // TC32 holds 512 TMEM columns (two buffers of four accumulators): one CTA
+  // per SM, kept alone there by its shared-memory request
+  const bool tc32 = prec == MRHS_PREC_TC32;
+  int ctas = tc32 ? 1 : (tune_set ? tune.ctas_per_sm : 2);
   const int max_stages = tune_set ? tune.max_stages : 32;
   Ring ring;
   int pps[MRHS_MAX_BATCH], npts[MRHS_MAX_BATCH];
@@ -796,6 +810,7 @@ int run_batch(Batch& bt, Geom* geoms, int prec, const TcTune& tune, bool tune_se
     bt.p[i].pps = pps[i];
     bt.p[i].xb_off = xb_off[i];
   }
+  if (tc32 && ring.smem < kSmemOneCta) ring.smem = kSmemOneCta;
   bt.total = 0;
   for (int i = 0; i < bt.n; ++i) {
     bt.p[i].item0 = bt.total;
@@ -820,7 +835,7 @@ int run_batch(Batch& bt, Geom* geoms, int prec, const TcTune& tune, bool tune_se
 int tc_supported(const mrhs_op_s* op, int prec, int nrhs) {
   if (op->nb > 64 || nrhs > 64 || nrhs < 1) return 0;
   const bool xs = xsplit_of(prec);
-  if (xs && nrhs > 32) return 0;
+  if (xs && nrhs > 32) return 0;      // four row groups of round8(R) <= 128 rows
   const Geom g = make_geom(op->nb, nrhs, xs, prec == MRHS_PREC_TC32);
   int one = 1;
   Ring r;

@@ -336,12 +336,15 @@ def test_lambda_max_and_auto_interval(mrhs):
 
 def test_mixed_solve_automatic_precisions(mrhs):
     """With every form built, the mixed solve picks TC32 in the Krylov loop
-    and FP16X in the preconditioner for <= 32 RHS, FP32/FP16 above."""
+    and FP16X in the preconditioner up to 32 RHS and FP32 / FP16 above; an
+    operator without the split forms falls back to FP32 and FP16 too."""
     L, nb, npts = (3, 2, 2, 2), 8, 81
     disp, _ = stencil(npts)
     A = coarse_op(L, nb, npts, 4321, 18.0)
-    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "fp16", "fp16x", "tc32"))
-    for R, kp, pp in ((8, "tc32", "fp16x"), (40, "fp32", "fp16")):
+    full = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "fp16", "fp16x", "tc32"))
+    plain = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp32", "fp16"))
+    for op, R, kp, pp in ((full, 8, "tc32", "fp16x"), (full, 40, "fp32", "fp16"),
+                          (plain, 12, "fp32", "fp16")):
         B = vectors(L, nb, R, 4322)
         X, info = op.solve(dev(B), mode="mixed", tol=1e-9)
         assert max(info["resid"]) <= 1e-9, info
