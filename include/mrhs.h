@@ -55,11 +55,16 @@ enum {
   MRHS_PREC_FP16 = 3, /* as BF16 with fp16 codes */
   MRHS_PREC_FP16X = 4, /* fp16 coefficient codes, input in two fp16 terms
                           (hi + 2^-11 lo): linear in X to ~2^-22; nrhs <= 32 */
-  MRHS_PREC_TC32 = 5  /* coefficients and input in two fp16 terms, lo x lo
+  MRHS_PREC_TC32 = 5, /* coefficients and input in two fp16 terms, lo x lo
                           dropped: FP32-class accuracy on the tensor cores,
                           8 bytes per complex coefficient; nrhs <= 32 */
+  MRHS_PREC_DF32 = 6  /* the FP64 coefficients and complex128 vectors in
+                          double-float arithmetic (FP32 pairs, error-free
+                          products and sums) on the FP32 pipes: about 2^-44
+                          relative; built whenever FP64 is */
 };
-#define MRHS_NUM_PREC 6
+#define MRHS_NUM_PREC 7
+#define MRHS_PREC_IS_TC(p) ((p) >= MRHS_PREC_BF16 && (p) <= MRHS_PREC_TC32)
 #define MRHS_PREC_BIT(p) (1u << (p))
 
 /* The four tensor-core forms share one design (op_tc.cu): per site, the
@@ -214,6 +219,11 @@ typedef struct {
   int32_t use_graph;    /* 1 (default): after a first uncaptured iteration, each
                            chunk of check_every block-CG iterations is captured
                            once as a CUDA graph and replayed */
+  int32_t residual_prec; /* MIXED: operator of each cycle's residual B - H X:
+                           MRHS_PREC_FP64 or MRHS_PREC_DF32; -1 (default):
+                           DF32.  A DF32 residual that meets tol is recomputed
+                           with FP64 before the solve returns, so the residuals
+                           reported are FP64 ones */
 } mrhs_solve_params;
 
 enum {

@@ -39,7 +39,8 @@ class CoarseOp:
 
     A: CUDA complex128 tensor [V][npts][nb][nb]; L: 4 lattice extents; disp:
     int8 [npts][4] displacements (disp[0] = 0); precisions: any of "fp64",
-    "fp32", "bf16", "fp16".  The operator keeps its own packed copies.
+    "fp32", "bf16", "fp16", "fp16x", "tc32", "df32" ("df32" comes with
+    "fp64" and implies it).  The operator keeps its own packed copies.
     """
 
     def __init__(self, A, L, disp, precisions=("fp64", "fp32")):
@@ -52,7 +53,12 @@ class CoarseOp:
             raise ValueError(f"A must be [V][npts][nb][nb], got {tuple(A.shape)}")
         self.nb = int(A.shape[2])
         self.N = self.V * self.nb
-        self.precisions = tuple(precisions)
+        precisions = tuple(precisions)
+        if "fp64" in precisions and "df32" not in precisions:
+            precisions += ("df32",)
+        if "df32" in precisions and "fp64" not in precisions:
+            precisions = ("fp64",) + precisions
+        self.precisions = precisions
         mask = 0
         for p in self.precisions:
             mask |= 1 << PREC[p]
@@ -154,7 +160,7 @@ class CoarseOp:
         p = SolveParams()
         l.mrhs_solve_params_default(ctypes.byref(p), SOLVE_MIXED if mode == "mixed" else SOLVE_FP64)
         for k, v in kw.items():
-            if k in ("precond_prec", "krylov_prec") and isinstance(v, str):
+            if k in ("precond_prec", "krylov_prec", "residual_prec") and isinstance(v, str):
                 v = PREC[v]
             if not hasattr(p, k):
                 raise KeyError(k)
@@ -227,7 +233,7 @@ def batch_solve(ops, Bs, mode="mixed", raise_on_fail=True, **kw):
     p = SolveParams()
     l.mrhs_solve_params_default(ctypes.byref(p), SOLVE_MIXED if mode == "mixed" else SOLVE_FP64)
     for k, v in kw.items():
-        if k in ("precond_prec", "krylov_prec") and isinstance(v, str):
+        if k in ("precond_prec", "krylov_prec", "residual_prec") and isinstance(v, str):
             v = PREC[v]
         if not hasattr(p, k):
             raise KeyError(k)

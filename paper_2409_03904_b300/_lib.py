@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libmrhs.so")
 MRHS_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NOT_CONVERGED", -4: "BREAKDOWN", -5: "NONFINITE",
           -6: "UNSUPPORTED", -7: "NO_MEMORY", -8: "DEVICE"}
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "fp16x": 4, "tc32": 5}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "fp16x": 4, "tc32": 5, "df32": 6}
+NUM_PREC = 7
 NAMES = {v: k for k, v in PREC.items()}
 C128, C64 = 0, 1
 MAX_RHS = 64
@@ -36,12 +37,12 @@ class SolveParams(ctypes.Structure):
                 ("cheb_hi", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_cycles", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("breakdown_tau", ctypes.c_double), ("krylov_prec", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("residual_prec", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
-                ("nrhs", ctypes.c_int32), ("applies", ctypes.c_int64 * 6),
+                ("nrhs", ctypes.c_int32), ("applies", ctypes.c_int64 * NUM_PREC),
                 ("resid", ctypes.c_double * MAX_RHS), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("krylov_prec", ctypes.c_int32), ("precond_prec", ctypes.c_int32),
@@ -144,4 +145,4 @@ def dev_ptr(t, dtype=None, name="tensor"):
 
 
 def vec_dtype(prec):
-    return torch.complex128 if prec == "fp64" else torch.complex64
+    return torch.complex128 if prec in ("fp64", "df32") else torch.complex64

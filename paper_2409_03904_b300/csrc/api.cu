@@ -105,8 +105,7 @@ int check_prec(const mrhs_op_s* op, int prec) {
 
 int op_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
              cudaStream_t s) {
-  if (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_FP32)
-    return simt_apply(op, prec, dag, X, Y, nrhs, s);
+  if (!MRHS_PREC_IS_TC(prec)) return simt_apply(op, prec, dag, X, Y, nrhs, s);
   return tc_apply(op, prec, dag, X, Y, nrhs, s);
 }
 
@@ -132,7 +131,10 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   if (nb < 1 || nb > 64) return fail(MRHS_ERR_INVALID_ARG, "nb must be in 1..64");
   if (npts < 1 || npts > MRHS_MAX_PTS) return fail(MRHS_ERR_INVALID_ARG, "npts must be in 1..81");
   if (prec_mask == 0 || (prec_mask >> MRHS_NUM_PREC))
-    return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..5");
+    return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..6");
+  // DF32 runs on the FP64 coefficients; with them it comes for free
+  if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_DF32)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_FP64);
+  if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_DF32);
   if (!aligned16(A)) return fail(MRHS_ERR_INVALID_ARG, "A not 16-byte aligned");
   int64_t V = 1;
   for (int mu = 0; mu < 4; ++mu) {
@@ -193,7 +195,7 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
     }
     { k_to_c64<<<num_sms() * 8, 256, 0, s>>>((const double2*)A, op->a32, (int64_t)nA); ::mrhs::count_launch(); }
   }
-  for (int prec = MRHS_PREC_BF16; prec < MRHS_NUM_PREC; ++prec)
+  for (int prec = MRHS_PREC_BF16; prec <= MRHS_PREC_TC32; ++prec)
     if (prec_mask & MRHS_PREC_BIT(prec)) {
       int st = tc_build(op, prec, false, (const double2*)A, s);
       if (st != MRHS_OK) {
@@ -290,7 +292,7 @@ static int apply_common(mrhs_op op, int32_t prec, const void* X, void* Y, int32_
   MRHS_TRY(check_vec(X, "X"));
   MRHS_TRY(check_vec(Y, "Y"));
   if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
-  const size_t es = prec == MRHS_PREC_FP64 ? 16 : 8;
+  const size_t es = (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32) ? 16 : 8;
   const size_t bytes = es * (size_t)op->V * op->nb * nrhs;
   const char* x = (const char*)X;
   const char* y = (const char*)Y;
@@ -398,9 +400,12 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
   mrhs_solve_params q = p;   // resolve the automatic precision choices
   auto built = [&](int pr) { return (op->prec_mask & MRHS_PREC_BIT(pr)) != 0; };
   auto fits = [&](int pr) {
-    return pr < MRHS_PREC_BF16 || tc_supported(op, pr, nrhs) != 0;
+    return !MRHS_PREC_IS_TC(pr) || tc_supported(op, pr, nrhs) != 0;
   };
   if (q.mode == MRHS_SOLVE_MIXED) {
+    if (q.residual_prec < 0) q.residual_prec = MRHS_PREC_DF32;
+    if (q.residual_prec != MRHS_PREC_FP64 && q.residual_prec != MRHS_PREC_DF32)
+      return fail(MRHS_ERR_INVALID_ARG, "residual_prec must be FP64 or DF32");
     if (q.krylov_prec < 0)
       q.krylov_prec = (built(MRHS_PREC_TC32) && fits(MRHS_PREC_TC32)) ? MRHS_PREC_TC32 : MRHS_PREC_FP32;
     if (q.krylov_prec != MRHS_PREC_FP32 && q.krylov_prec != MRHS_PREC_TC32)
@@ -438,7 +443,7 @@ int mrhs_autotune(const mrhs_op* ops, int32_t n, int32_t prec, const int32_t* nr
                   mrhs_tune_result* out, void* stream) {
   if (!ops || !nrhs || n < 1 || n > MRHS_MAX_BATCH)
     return fail(MRHS_ERR_INVALID_ARG, "mrhs_autotune: arguments (1 <= n <= 16)");
-  if (prec < MRHS_PREC_BF16 || prec >= MRHS_NUM_PREC)
+  if (!MRHS_PREC_IS_TC(prec))
     return fail(MRHS_ERR_UNSUPPORTED, "only the tensor-core kernel has a tuned launch shape");
   int dev = 0;
   cudaGetDevice(&dev);
@@ -472,7 +477,7 @@ int mrhs_batch_apply(const mrhs_op* ops, int32_t n, int32_t prec, const void* co
                      void* const* Y, const int32_t* nrhs, void* stream) {
   if (!ops || !X || !Y || !nrhs || n < 1 || n > MRHS_MAX_BATCH)
     return fail(MRHS_ERR_INVALID_ARG, "mrhs_batch_apply: arguments (1 <= n <= 16)");
-  if (prec < MRHS_PREC_BF16 || prec >= MRHS_NUM_PREC)
+  if (!MRHS_PREC_IS_TC(prec))
     return fail(MRHS_ERR_UNSUPPORTED, "batched applications run on the tensor cores only");
   int dev = 0;
   cudaGetDevice(&dev);
@@ -514,6 +519,9 @@ int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* 
   // the batched path: TC32 in the Krylov loop and a tensor-core preconditioner
   // shared by all problems; otherwise each problem is solved in turn
   if (batched) {
+    if (q.residual_prec < 0) q.residual_prec = MRHS_PREC_DF32;
+    if (q.residual_prec != MRHS_PREC_FP64 && q.residual_prec != MRHS_PREC_DF32)
+      return fail(MRHS_ERR_INVALID_ARG, "residual_prec must be FP64 or DF32");
     if (q.krylov_prec < 0) q.krylov_prec = MRHS_PREC_TC32;
     if (q.precond_prec < 0) {
       const int order[] = {MRHS_PREC_FP16X, MRHS_PREC_FP16, MRHS_PREC_BF16, MRHS_PREC_TC32};
@@ -555,6 +563,7 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->precond_prec = -1;
   p->krylov_prec = -1;
   p->use_graph = 1;
+  p->residual_prec = -1;
   p->cheb_order = 8;
   p->cheb_lo = 0.0;
   p->cheb_hi = 0.0;

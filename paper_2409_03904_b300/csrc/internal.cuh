@@ -102,7 +102,7 @@ struct mrhs_op_s {
   mrhs::Workspace ws_small;     // column scales etc.
   mrhs::Workspace ws_solve;     // block CG vectors and state
   mrhs::KernelTimer timer[MRHS_NUM_PREC];   // per precision
-  double lam_max[MRHS_NUM_PREC] = {0, 0, 0, 0, 0, 0};  // cached power-method estimates
+  double lam_max[MRHS_NUM_PREC] = {};   // cached power-method estimates
   mrhs::TcTune tc_tune;              // tensor-core launch shape
   bool tc_set = false;               // tc_tune set explicitly
 };

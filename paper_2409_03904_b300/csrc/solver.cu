@@ -360,7 +360,7 @@ struct Ctx {
   Small* st = nullptr;        // device
   double2* gpart = nullptr;   // Gram partials
   double* npart = nullptr;    // column-norm partials
-  int64_t applies[MRHS_NUM_PREC] = {0, 0, 0, 0, 0, 0};
+  int64_t applies[MRHS_NUM_PREC] = {};
   bool use_graph = true;
   // bump allocation from one grow-only operator-owned workspace: a first
   // pass with base == nullptr only sums the sizes
@@ -544,7 +544,7 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
   bool graph_ok = cx.use_graph && !timing && check_every > 1;
   int64_t graph_launches = 0;
   cudaGraphExec_t exec = nullptr;
-  int64_t graph_applies[MRHS_NUM_PREC] = {0, 0, 0, 0, 0, 0};
+  int64_t graph_applies[MRHS_NUM_PREC] = {};
   auto cleanup = [&]() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -691,7 +691,8 @@ int power_run(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
 // Chebyshev upper bound "with a cheap application of the power method"):
 // Rayleigh quotient of H^k v0, one right-hand side, operator in `prec`.
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
-  if (prec == MRHS_PREC_FP64) return power_run<double2>(op, prec, iters, s, lam);
+  if (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32)
+    return power_run<double2>(op, prec, iters, s, lam);
   return power_run<float2>(op, prec, iters, s, lam);
 }
 
@@ -735,14 +736,28 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
   MRHS_CUDA_TRY(cudaStreamSynchronize(s));
   int total_iters = 0, cycles = 0, status = MRHS_OK, flag = 0;
 
-  auto true_residual = [&]() -> int {   // r64 = B - H X (FP64), rnorm
-    MRHS_TRY(cx.apply(MRHS_PREC_FP64, X, sb.r64));
+  // r64 = B - H X with the operator of precision `rp` (FP64 or DF32), rnorm
+  auto residual_in = [&](int rp) -> int {
+    MRHS_TRY(cx.apply(rp, X, sb.r64));
     { k_sub<double2><<<g, kThreads, 0, s>>>(sb.r64, B, sb.r64, n); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaGetLastError());
     MRHS_TRY(cx.colnorms<double2>(sb.r64, sb.rnorm_d));
     MRHS_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), sb.rnorm_d, sizeof(double) * R,
                                   cudaMemcpyDeviceToHost, s));
     MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    return MRHS_OK;
+  };
+  auto all_done = [&]() {
+    for (int j = 0; j < R; ++j)
+      if (bnorm[j] > 0 && !(rnorm[j] <= p.tol * bnorm[j])) return false;
+    return true;
+  };
+  // the cycle residual in residual_prec; one that meets tol is confirmed in
+  // FP64, so convergence is always decided on an FP64 residual
+  const int res_prec = (mixed && p.residual_prec >= 0) ? p.residual_prec : MRHS_PREC_FP64;
+  auto true_residual = [&]() -> int {
+    MRHS_TRY(residual_in(res_prec));
+    if (res_prec != MRHS_PREC_FP64 && all_done()) MRHS_TRY(residual_in(MRHS_PREC_FP64));
     return MRHS_OK;
   };
   // a zero initial guess needs no operator application: r = B
@@ -758,11 +773,6 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     MRHS_CUDA_TRY(cudaMemcpyAsync(sb.r64, B, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
     rnorm = bnorm;
     return MRHS_OK;
-  };
-  auto all_done = [&]() {
-    for (int j = 0; j < R; ++j)
-      if (bnorm[j] > 0 && !(rnorm[j] <= p.tol * bnorm[j])) return false;
-    return true;
   };
   auto max_rel = [&]() {
     double m = 0.0;
@@ -858,11 +868,12 @@ int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* 
   cx.R = R;
   cx.N = op->V * op->nb;
   const int64_t n = cx.N * R;
-  const size_t es = prec == MRHS_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  const bool wide = prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32;
+  const size_t es = wide ? sizeof(double2) : sizeof(float2);
   MRHS_TRY(op->ws_cheb.ensure(3 * (n * es + 256)));
   char* base = (char*)op->ws_cheb.ptr;
   const size_t stride = (n * es + 255) / 256 * 256;
-  if (prec == MRHS_PREC_FP64)
+  if (wide)
     return cheb_run<double2>(cx, prec, lo, hi, order, (const double2*)X, (double2*)P,
                              (double2*)base, (double2*)(base + stride),
                              (double2*)(base + 2 * stride));
@@ -942,10 +953,10 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
   }
   MRHS_CUDA_TRY(cudaStreamSynchronize(s));
 
-  auto true_residual = [&](BatchProb& b, int i) -> int {
+  auto residual_in = [&](BatchProb& b, int i, int rp) -> int {
     Ctx& cx = b.cx;
     const int64_t nn = cx.N * cx.R;
-    MRHS_TRY(cx.apply(MRHS_PREC_FP64, X[i], b.sb.r64));
+    MRHS_TRY(cx.apply(rp, X[i], b.sb.r64));
     { k_sub<double2><<<grid_for(nn), kThreads, 0, s>>>(b.sb.r64, B[i], b.sb.r64, nn); ::mrhs::count_launch(); }
     MRHS_TRY(cx.colnorms<double2>(b.sb.r64, b.sb.rnorm_d));
     MRHS_CUDA_TRY(cudaMemcpyAsync(b.rnorm.data(), b.sb.rnorm_d, sizeof(double) * cx.R,
@@ -956,6 +967,16 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
     for (int j = 0; j < b.cx.R; ++j)
       if (b.bnorm[j] > 0 && !(b.rnorm[j] <= p.tol * b.bnorm[j])) return false;
     return true;
+  };
+  // the cycle residual in residual_prec, confirmed in FP64 once it meets tol
+  const int res_prec = p.residual_prec >= 0 ? p.residual_prec : MRHS_PREC_FP64;
+  auto true_residual = [&](BatchProb& b, int i) -> int {
+    MRHS_TRY(residual_in(b, i, res_prec));
+    if (res_prec != MRHS_PREC_FP64) {
+      MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+      if (problem_done(b)) MRHS_TRY(residual_in(b, i, MRHS_PREC_FP64));
+    }
+    return MRHS_OK;
   };
   // initial residuals: a zero guess needs no operator application
   for (int i = 0; i < n; ++i) {

@@ -57,3 +57,33 @@ def test_no_oracle_in_product_path():
     for f in glob.glob(os.path.join(ROOT, "paper_2409_03904_b300", "**", "*"), recursive=True):
         if os.path.isfile(f) and f.endswith((".py", ".cu", ".cuh", ".h")):
             assert "oracle" not in open(f).read().lower(), f
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The Python mirrors of mrhs_solve_params / mrhs_solve_info / mrhs_tune_result
+    have the C layout: sizes and field offsets from a C program built against
+    include/mrhs.h with the host compiler."""
+    from paper_2409_03904_b300 import _lib
+    structs = {"mrhs_solve_params": _lib.SolveParams, "mrhs_solve_info": _lib.SolveInfo,
+               "mrhs_tune_result": _lib.TuneResult}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mrhs.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

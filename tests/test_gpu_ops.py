@@ -374,3 +374,42 @@ def test_graph_replay_matches_eager(mrhs):
         assert ig["iters"] == ie["iters"] and ig["applies"] == ie["applies"]
         assert n1 - n0 == n2 - n1          # replays are counted as launches
         assert max(ig["resid"]) <= 1e-9
+
+
+@pytest.mark.parametrize("L,nb,npts,R", [((3, 2, 2, 3), 48, 81, 32), ((4, 3, 2, 3), 16, 9, 8),
+                                         ((2, 2, 2, 2), 5, 81, 3), ((3, 3, 2, 2), 24, 81, 64)])
+def test_df32_operator(mrhs, L, nb, npts, R):
+    """Double-float operator against the oracle's FP64 operator and adjoint:
+    relative error per RHS well below 1e-11 (2^-44 arithmetic)."""
+    disp, _ = stencil(npts)
+    rng = np.random.default_rng(nb * 7 + R)
+    V = int(np.prod(L))
+    A = rng.standard_normal((V, npts, nb, nb)) + 1j * rng.standard_normal((V, npts, nb, nb))
+    X = vectors(L, nb, R, 808)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64",))
+    Y = op.apply(dev(X), "df32").cpu().numpy()
+    assert rel_per_rhs(Y, coarse_op_apply(A, X, L, disp)) <= 1e-11
+    Yd = op.apply_dag(dev(X), "df32").cpu().numpy()
+    assert rel_per_rhs(Yd, coarse_op_apply_dag(A, X, L, disp)) <= 1e-11
+
+
+def test_df32_cycle_residuals_fp64_confirmation(mrhs):
+    """Mixed solve with DF32 cycle residuals (default) and with FP64 ones:
+    both end on an FP64 residual <= tol; the DF32 run spends one FP64
+    application, on the confirmation."""
+    from synth import WORKLOADS
+    w = WORKLOADS["L4_nb24_9pt_r4"]
+    L, nb, npts, R = w["L"], w["nb"], w["npts"], w["nrhs"]
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, w["seed"], load_shift(w["name"]))
+    B = vectors(L, nb, R, w["seed"])
+    op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp16x", "tc32"))
+    X1, i1 = op.solve(dev(B), mode="mixed", tol=1e-10)
+    X2, i2 = op.solve(dev(B), mode="mixed", tol=1e-10, residual_prec="fp64")
+    for X, info in ((X1, i1), (X2, i2)):
+        assert info["status"] == 0 and max(info["resid"]) <= 1e-10
+        r = B - coarse_op_apply(A, X.cpu().numpy(), L, disp)
+        rel = np.linalg.norm(r.reshape(-1, R), axis=0) / np.linalg.norm(B.reshape(-1, R), axis=0)
+        assert np.max(rel) <= 1.5e-10
+    assert i1["applies"]["df32"] == i1["cycles"] and i1["applies"]["fp64"] == 1
+    assert i2["applies"]["df32"] == 0 and i2["applies"]["fp64"] == i2["cycles"]
