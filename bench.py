@@ -58,10 +58,17 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the standalone operator, FP64 and e2e measurements")
     ap.add_argument("--cpu-sites", type=int, default=96, help="oracle sample size (sites)")
-    ap.add_argument("--op", default=None, choices=["fp64", "fp32", "bf16", "fp16", "fp16x", "tc32"],
+    ap.add_argument("--op", default=None,
+                    choices=["fp64", "df32", "fp32", "bf16", "fp16", "fp16x", "tc32"],
                     help="time the coarse operator alone in this precision")
     ap.add_argument("--lattice", default=None, help="a,b,c,d: override the workload's lattice "
                     "(operator mode; same per-site work)")
+    ap.add_argument("--nrhs", type=int, default=None, help="operator mode: right-hand sides")
+    ap.add_argument("--nb", type=int, default=None, help="operator mode: basis size")
+    ap.add_argument("--npts", type=int, default=None, choices=[1, 9, 81],
+                    help="operator mode: stencil points")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the launch-shape autotuner (run before the timed region)")
     return ap.parse_args()
 
 
@@ -135,9 +142,9 @@ def op_bytes(w, R, prec):
     """Algorithmic bytes of one application: coefficients once, input and
     output vectors once (neighbour re-reads not counted)."""
     V = int(np.prod(w["L"]))
-    coef = {"fp64": 16, "fp32": 8, "bf16": 4, "fp16": 4, "fp16x": 4, "tc32": 8}[prec]
-    vec = 16 if prec == "fp64" else 8
-    extra = 8 * V if prec not in ("fp64", "fp32") else 0      # site scale + diagonal
+    coef = {"fp64": 16, "df32": 16, "fp32": 8, "bf16": 4, "fp16": 4, "fp16x": 4, "tc32": 8}[prec]
+    vec = 16 if prec in ("fp64", "df32") else 8
+    extra = 8 * V if prec not in ("fp64", "df32", "fp32") else 0   # site scale + diagonal
     return w["npts"] * V * w["nb"] ** 2 * coef + extra + 2 * V * w["nb"] * R * vec
 
 
@@ -242,8 +249,13 @@ def run_op(a, w, shift):
     import paper_2409_03904_b300 as mrhs
     import synth.device as sdev
     from synth import stencil
+    over = {}
     if a.lattice:
-        w = dict(w, L=tuple(int(v) for v in a.lattice.split(",")))
+        over["L"] = tuple(int(v) for v in a.lattice.split(","))
+    for k in ("nrhs", "nb", "npts"):
+        if getattr(a, k) is not None:
+            over[k] = getattr(a, k)
+    w = dict(w, **over)
     R, V, nb, prec = w["nrhs"], int(np.prod(w["L"])), w["nb"], a.op
     disp, _ = stencil(w["npts"])
     dev = torch.device("cuda", 0)
@@ -251,10 +263,16 @@ def run_op(a, w, shift):
     op = mrhs.CoarseOp(A, w["L"], disp, (prec,))
     del A
     torch.cuda.empty_cache()
-    vdt = torch.complex128 if prec == "fp64" else torch.complex64
+    vdt = torch.complex128 if prec in ("fp64", "df32") else torch.complex64
     X = sdev.vectors(w["L"], nb, R, w["seed"], device=dev).to(vdt)
     Y = torch.empty_like(X)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not a.no_autotune and prec not in ("fp64", "fp32", "df32"):
+        try:
+            tuned = mrhs.autotune(op, prec, R, reps=3)
+        except mrhs.MrhsError:
+            tuned = None
     for _ in range(a.warmup):
         op.apply(X, prec, out=Y)
     op.kernel_timing(True)
@@ -295,8 +313,10 @@ def run_op(a, w, shift):
            "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": prec, "data": "synthetic",
-           "config": {"workload": w["name"] + ("" if not a.lattice else f" on {a.lattice}"),
+           "config": {"workload": w["name"] + ("" if not over else " with " + ", ".join(
+                          f"{k}={v}" for k, v in over.items())),
                       "L": list(w["L"]), "nb": nb, "npts": w["npts"], "nrhs": R,
+                      "launch_shape": tuned,
                       "l2": f"inputs larger than L2 ({byts / 1e9:.2f} GB per application)"},
            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
            "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
@@ -337,7 +357,7 @@ def main():
 
     t0 = time.time()
     A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
-    precs = tuple(dict.fromkeys(("fp64", "fp32", "fp16", a.precond, a.krylov)))
+    precs = tuple(dict.fromkeys(("fp64", "df32", "fp32", "bf16", "fp16", a.precond, a.krylov)))
     op = mrhs.CoarseOp(A, w["L"], disp, precs)
     del A
     torch.cuda.empty_cache()
@@ -351,6 +371,15 @@ def main():
                   inner_tol=a.inner_tol, maxiter=20000, max_cycles=20, check_every=4)
 
     stream = torch.cuda.current_stream()
+    # launch shapes of the two tensor-core forms, tuned once for this shape
+    tuned = {}
+    if not a.no_autotune:
+        for p in dict.fromkeys((a.precond, a.krylov)):
+            if p in ("fp16x", "fp16", "bf16", "tc32"):
+                try:
+                    tuned[p] = mrhs.autotune(op, p, R, reps=3)
+                except mrhs.MrhsError:
+                    pass
     for _ in range(a.warmup):
         X, info = op.solve(B, **params)
     # ---------------- timed region: K complete solves
@@ -398,8 +427,8 @@ def main():
         # standalone coarse-operator throughput at this RHS count, per precision
         cop = {}
         for p in precs:
-            Xp = B if p == "fp64" else B.to(torch.complex64)
-            reps = 2 if p == "fp64" else 10
+            Xp = B if p in ("fp64", "df32") else B.to(torch.complex64)
+            reps = 2 if p in ("fp64", "df32", "fp32") else 10
             op.apply(Xp, p)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -458,12 +487,14 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": "ms/RHS", "n_gpus": world,
                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step,
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-               "dtype": f"f64+{a.krylov}+{a.precond}", "data": "synthetic",
+               "dtype": f"f64+df32+{a.krylov}+{a.precond}", "data": "synthetic",
                "config": {"workload": w["name"], "L": list(w["L"]), "nb": nb, "npts": w["npts"],
                           "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
                           "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
                                      f"[{hi / a.cheb_ratio:.4g}, {hi:.4g}]",
                           "inner_tol": a.inner_tol, "parallelism": f"replicas x{world}",
+                          "residuals": "df32 per cycle, fp64 for the one that meets tol",
+                          "launch_shapes": tuned,
                           "l2": "inputs larger than L2 (coefficients "
                                 f"{op_bytes(w, R, a.precond) / 1e9:.1f} GB per application)"},
                "solve": {"iters": inf["iters"], "cycles": inf["cycles"], "applies": inf["applies"],

@@ -661,9 +661,9 @@ int plan_ring(const Geom* g, int* pps, const int* npts, int n, size_t budget, in
   for (int i = 0; i < n; ++i) {
     stage = std::max(stage, (size_t)pps[i] * (g[i].coef_bytes + g[i].xb_bytes));
     // the M = 128 operand read runs past an input tile of fewer than 128
-    // rows, and the N = n_mma read past an nbp8-row coefficient tile
+    // rows (the coefficient tile has exactly the N = 2 nb8 rows read)
     const size_t row_bytes = (size_t)g[i].K * 2;
-    tail = std::max(tail, (size_t)(kM - g[i].xrows) * row_bytes + (size_t)g[i].n_mma * row_bytes);
+    tail = std::max(tail, (size_t)(kM - g[i].xrows) * row_bytes);
     xs = xs || g[i].xsplit;
   }
   tail += 1024;
