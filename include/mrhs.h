@@ -184,6 +184,25 @@ int herm_factor(const void* G, void* S, void* W, int32_t* rank, int32_t r, doubl
 int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, const void* X,
                 void* P, int32_t nrhs, void* stream);
 
+/* Deflated Chebyshev coarse solve Q^{Cheby+defl} (Sec. 2.3, the "two step
+ * deflated/Chebyshev coarse solve"):
+ *   X = U Lambda^-1 U^dagger B + p(H) (B - U U^dagger B),
+ * the exact inverse on the span of n_ev eigenvectors u_i (eigenvalues
+ * lambda_i) of the Hermitian operator plus the degree-`order` Chebyshev
+ * approximation p of 1/x on [lo, hi] (as cheby_apply) on the rest.
+ * U: device, [V][nb][n_ev] (column i = u_i, the layout of a block of n_ev
+ * right-hand sides), orthonormal columns expected (not checked); lambda:
+ * host, n_ev positive values; B, X: device [V][nb][nrhs].  Element type of
+ * U, B and X: complex128 for FP64/DF32, complex64 for the other precisions
+ * (the deflation GEMMs and the recurrence run in it; the n_ev x nrhs
+ * coefficients are summed in FP64).  n_ev = 0 reduces to cheby_apply; U may
+ * then be NULL.  X may equal B; U must not overlap either.  Uses
+ * operator-owned workspace (calls on one operator must not overlap on the
+ * GPU); asynchronous on `stream` apart from the copy of lambda. */
+int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const double* lambda,
+                            int32_t n_ev, double lo, double hi, int32_t order, const void* B,
+                            void* X, int32_t nrhs, void* stream);
+
 /* Largest-eigenvalue estimate of a Hermitian positive operator by the power
  * method (Sec. 2.3: the upper end of the Chebyshev interval is obtained
  * "with a cheap application of the power method"): Rayleigh quotient after

@@ -148,6 +148,26 @@ class CoarseOp:
                                           int(X.shape[2]), _lib.stream_ptr()))
         return P
 
+    def defl_cheby(self, U, lam, B, lo, hi, order, prec="fp64", out=None):
+        """Deflated Chebyshev coarse solve (Sec. 2.3): U Lambda^-1 U^dagger B
+        + p(H)(B - U U^dagger B), p the degree-`order` Chebyshev
+        approximation of 1/x on [lo, hi].  U: [V][nb][n_ev] orthonormal
+        eigenvectors (device), lam: their n_ev eigenvalues (host sequence),
+        B: [V][nb][nrhs]; element type complex128 for fp64/df32, complex64
+        otherwise."""
+        dt = _lib.vec_dtype(prec)
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(-1))
+        n_ev = int(lam.size)
+        if n_ev and (U.shape[:2] != (self.V, self.nb) or U.shape[2] != n_ev):
+            raise ValueError("U must be [V][nb][n_ev]")
+        X = torch.empty_like(B) if out is None else out
+        uptr = _lib.dev_ptr(U, dt, "U") if n_ev else ctypes.c_void_p(None)
+        _lib.check(_lib.lib().coarse_solve_defl_cheby(
+            self._h, PREC[prec], uptr, lam.ctypes.data_as(ctypes.c_void_p), n_ev, float(lo),
+            float(hi), int(order), _lib.dev_ptr(B, dt, "B"), _lib.dev_ptr(X, dt, "X"),
+            int(B.shape[2]), _lib.stream_ptr()))
+        return X
+
     def solve(self, B, X0=None, mode="fp64", raise_on_fail=True, **kw):
         """Block CG (Fig. 2) for H X = B; returns (X, info dict).
 

@@ -1,6 +1,7 @@
 // C ABI entry points of libmrhs: argument checks, operator construction and
 // dispatch to the kernels (see include/mrhs.h for the contract).
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -278,6 +279,7 @@ int mrhs_op_destroy(mrhs_op op) {
     cudaFree(op->tc_dag[i].diag);
   }
   op->ws_xpack.release();
+  op->ws_defl.release();
   op->ws_cheb.release();
   op->ws_small.release();
   op->ws_solve.release();
@@ -382,6 +384,37 @@ int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, c
   if (order < 0 || order > 10000) return fail(MRHS_ERR_INVALID_ARG, "order");
   if (X == P) return fail(MRHS_ERR_INVALID_ARG, "X and P must differ");
   return cheby(op, prec, lo, hi, order, X, P, nrhs, (cudaStream_t)stream);
+}
+
+int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const double* lambda,
+                            int32_t n_ev, double lo, double hi, int32_t order, const void* B,
+                            void* X, int32_t nrhs, void* stream) {
+  MRHS_TRY(check_op(op));
+  MRHS_TRY(check_prec(op, prec));
+  MRHS_TRY(check_vec(B, "B"));
+  MRHS_TRY(check_vec(X, "X"));
+  if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
+  if (!(lo > 0.0 && lo < hi)) return fail(MRHS_ERR_INVALID_ARG, "need 0 < lo < hi");
+  if (order < 0 || order > 10000) return fail(MRHS_ERR_INVALID_ARG, "order");
+  if (n_ev < 0 || n_ev > 65536) return fail(MRHS_ERR_INVALID_ARG, "n_ev must be in 0..65536");
+  if (n_ev > 0) {
+    MRHS_TRY(check_vec(U, "U"));
+    if (!lambda) return fail(MRHS_ERR_INVALID_ARG, "lambda is null");
+    for (int i = 0; i < n_ev; ++i)
+      if (!(lambda[i] > 0.0) || !std::isfinite(lambda[i]))
+        return fail(MRHS_ERR_INVALID_ARG, "lambda must be positive and finite");
+    const size_t es = (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32) ? 16 : 8;
+    const size_t ub = es * (size_t)op->V * op->nb * n_ev, vb = es * (size_t)op->V * op->nb * nrhs;
+    const char* u = (const char*)U;
+    for (const void* v : {B, (const void*)X}) {
+      const char* c = (const char*)v;
+      if (u < c + vb && c < u + ub) return fail(MRHS_ERR_INVALID_ARG, "U overlaps B or X");
+    }
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != op->device) return fail(MRHS_ERR_INVALID_ARG, "operator lives on another device");
+  return defl_cheby(op, prec, U, lambda, n_ev, lo, hi, order, B, X, nrhs, (cudaStream_t)stream);
 }
 
 int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,

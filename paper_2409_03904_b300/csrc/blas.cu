@@ -35,7 +35,7 @@ constexpr int kFlushRows = 64;
 template <typename C, int T>
 __global__ void __launch_bounds__(kThreads)
     k_gram_partial(const C* __restrict__ X, const C* __restrict__ Y, double2* __restrict__ part,
-                   int64_t N, int rx, int ry, int64_t rows_per_block) {
+                   int64_t N, int rx, int ry, int64_t rows_per_block, int64_t ldx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sX = reinterpret_cast<C*>(smem_raw);
   C* sY = sX + kTile * rx;
@@ -62,7 +62,11 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t t0 = n0; t0 < n1; t0 += kTile) {
     const int rows = (int)((n1 - t0) < kTile ? (n1 - t0) : kTile);
     __syncthreads();
-    for (int i = tid; i < rows * rx; i += kThreads) sX[i] = X[t0 * rx + i];
+    if (ldx == rx) {
+      for (int i = tid; i < rows * rx; i += kThreads) sX[i] = X[t0 * rx + i];
+    } else {      // a column block of a wider matrix
+      for (int i = tid; i < rows * rx; i += kThreads) sX[i] = X[(t0 + i / rx) * ldx + i % rx];
+    }
     for (int i = tid; i < rows * ry; i += kThreads) sY[i] = Y[t0 * ry + i];
     __syncthreads();
     if (!worker) continue;
@@ -163,7 +167,7 @@ __device__ inline float2 from_c128<float2>(double2 v) {
 template <typename C>
 __global__ void __launch_bounds__(kThreads)
     k_axpy(C* Y, const C* X, const double2* __restrict__ M, double beta, int64_t N, int rin,
-           int rout) {
+           int rout, int64_t ldx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sM = reinterpret_cast<C*>(smem_raw);
   C* sX = sM + rin * rout;
@@ -173,7 +177,12 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t t0 = (int64_t)blockIdx.x * kTile; t0 < N; t0 += (int64_t)gridDim.x * kTile) {
     const int rows = (int)((N - t0) < kTile ? (N - t0) : kTile);
     __syncthreads();
-    for (int i = threadIdx.x; i < rows * rin; i += kThreads) sX[i] = X[t0 * rin + i];
+    if (ldx == rin) {
+      for (int i = threadIdx.x; i < rows * rin; i += kThreads) sX[i] = X[t0 * rin + i];
+    } else {      // a column block of a wider matrix
+      for (int i = threadIdx.x; i < rows * rin; i += kThreads)
+        sX[i] = X[(t0 + i / rin) * ldx + i % rin];
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < rows * rout; e += kThreads) {
       const int n = e / rout, j = e % rout;
@@ -243,7 +252,7 @@ int gram_tile(int rx, int ry) {
 
 template <typename C, int T>
 int launch_gram(const void* X, const void* Y, double2* part, int64_t N, int rx, int ry,
-                int nblk, int64_t per, cudaStream_t s) {
+                int nblk, int64_t per, int64_t ldx, cudaStream_t s) {
   const int nt = ((rx + T - 1) / T) * ((ry + T - 1) / T);
   const int G = kThreads / nt;
   const size_t stage = sizeof(C) * kTile * (rx + ry);
@@ -252,17 +261,17 @@ int launch_gram(const void* X, const void* Y, double2* part, int64_t N, int rx, 
   MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_partial<C, T>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   { k_gram_partial<C, T><<<nblk, kThreads, smem, s>>>((const C*)X, (const C*)Y, part, N, rx, ry,
-                                                      per); ::mrhs::count_launch(); }
+                                                      per, ldx); ::mrhs::count_launch(); }
   return MRHS_OK;
 }
 
 template <typename C>
 int launch_gram(const void* X, const void* Y, double2* part, int64_t N, int rx, int ry,
-                int nblk, int64_t per, cudaStream_t s) {
+                int nblk, int64_t per, int64_t ldx, cudaStream_t s) {
   switch (gram_tile(rx, ry)) {
-    case 1: return launch_gram<C, 1>(X, Y, part, N, rx, ry, nblk, per, s);
-    case 2: return launch_gram<C, 2>(X, Y, part, N, rx, ry, nblk, per, s);
-    default: return launch_gram<C, 4>(X, Y, part, N, rx, ry, nblk, per, s);
+    case 1: return launch_gram<C, 1>(X, Y, part, N, rx, ry, nblk, per, ldx, s);
+    case 2: return launch_gram<C, 2>(X, Y, part, N, rx, ry, nblk, per, ldx, s);
+    default: return launch_gram<C, 4>(X, Y, part, N, rx, ry, nblk, per, ldx, s);
   }
 }
 
@@ -275,7 +284,8 @@ int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry,
 // partial Grams fit a buffer of `max_entries` complex128 values (the entry
 // point that must not allocate passes its own static buffer).
 int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
-                   double2* part, int64_t max_entries, cudaStream_t s) {
+                   double2* part, int64_t max_entries, cudaStream_t s, int64_t ldx) {
+  if (ldx <= 0) ldx = rx;
   const int ne = rx * ry;
   int nblk = gram_blocks(N);
   if ((int64_t)nblk * ne > max_entries) nblk = (int)(max_entries / ne);
@@ -286,8 +296,8 @@ int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, 
     MRHS_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double2) * ne, s));
     return MRHS_OK;
   }
-  if (dtype == MRHS_C128) MRHS_TRY(launch_gram<double2>(X, Y, part, N, rx, ry, nblk, per, s));
-  else MRHS_TRY(launch_gram<float2>(X, Y, part, N, rx, ry, nblk, per, s));
+  if (dtype == MRHS_C128) MRHS_TRY(launch_gram<double2>(X, Y, part, N, rx, ry, nblk, per, ldx, s));
+  else MRHS_TRY(launch_gram<float2>(X, Y, part, N, rx, ry, nblk, per, ldx, s));
   MRHS_CUDA_TRY(cudaGetLastError());
   { k_gram_final<<<(unsigned)((ne * 32 + 255) / 256), 256, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
@@ -305,7 +315,8 @@ int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, in
 }
 
 int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int rin, int rout,
-         int dtype, cudaStream_t s) {
+         int dtype, cudaStream_t s, int64_t ldx) {
+  if (ldx <= 0) ldx = rin;
   if (N == 0) return MRHS_OK;
   int64_t grid = (N + kTile - 1) / kTile;
   const int64_t cap = (int64_t)num_sms() * 16;
@@ -315,11 +326,11 @@ int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int r
     MRHS_CUDA_TRY(cudaFuncSetAttribute(k_axpy<double2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     { k_axpy<double2><<<(unsigned)grid, kThreads, smem, s>>>((double2*)Y, (const double2*)X, M, beta,
-                                                            N, rin, rout); ::mrhs::count_launch(); }
+                                                            N, rin, rout, ldx); ::mrhs::count_launch(); }
   } else {
     const size_t smem = sizeof(float2) * ((size_t)rin * rout + (size_t)kTile * rin);
     { k_axpy<float2><<<(unsigned)grid, kThreads, smem, s>>>((float2*)Y, (const float2*)X, M, beta, N,
-                                                          rin, rout); ::mrhs::count_launch(); }
+                                                          rin, rout, ldx); ::mrhs::count_launch(); }
   }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;

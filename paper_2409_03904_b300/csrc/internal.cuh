@@ -98,6 +98,7 @@ struct mrhs_op_s {
   mrhs::TcImage tc[3];          // BF16, FP16 (also FP16X), TC32: forward stencil
   mrhs::TcImage tc_dag[3];      // the same for the daggered stencil (on demand)
   mrhs::Workspace ws_xpack;     // packed input vectors for the tensor path
+  mrhs::Workspace ws_defl;      // deflated Chebyshev solve: Grams, B_perp, p(H) B_perp
   mrhs::Workspace ws_cheb;      // Chebyshev recurrence vectors
   mrhs::Workspace ws_small;     // column scales etc.
   mrhs::Workspace ws_solve;     // block CG vectors and state
@@ -138,7 +139,7 @@ int tc_supported(const mrhs_op_s* op, int prec, int nrhs);
 int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
          cudaStream_t s);
 int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int rin, int rout,
-         int dtype, cudaStream_t s);
+         int dtype, cudaStream_t s, int64_t ldx = 0);   // ldx: X's row stride (0: rin)
 // small.cu
 int factor(const double2* G, double2* S, double2* W, int32_t* rank, int r, double tau,
            cudaStream_t s);
@@ -146,13 +147,16 @@ int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry,
             double2* part, cudaStream_t s);
 size_t gram_workspace_bytes(int64_t N, int rx, int ry);
 int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
-                   double2* part, int64_t max_entries, cudaStream_t s);
+                   double2* part, int64_t max_entries, cudaStream_t s,
+                   int64_t ldx = 0);   // ldx: X's row stride (0: rx)
 
 // solver.cu
 int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
           mrhs_solve_info* info, cudaStream_t s);
 int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* X, void* P,
           int R, cudaStream_t s);
+int defl_cheby(mrhs_op_s* op, int prec, const void* U, const double* lam_host, int n_ev,
+               double lo, double hi, int order, const void* B, void* X, int R, cudaStream_t s);
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam);
 int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* const* X,
                 const int32_t* nrhs, const mrhs_solve_params& p, mrhs_solve_info* infos,
