@@ -73,6 +73,11 @@ def parse():
     ap.add_argument("--defl-order", type=int, default=120)
     ap.add_argument("--defl-prec", default="fp16",
                     choices=["fp64", "df32", "fp32", "bf16", "fp16", "fp16x", "tc32"])
+    ap.add_argument("--blocking", action="store_true",
+                    help="time block project / promote (Sec. 3.4) at the Table 6 shape")
+    ap.add_argument("--blocks", default="4096,256,64",
+                    help="n_blocks,v_block,n_basis for --blocking (nrhs from --nrhs, default 12)")
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run before the timed region)")
     return ap.parse_args()
@@ -437,6 +442,51 @@ def run_defl(a, w, shift):
     print(json.dumps(out), flush=True)
 
 
+def run_blocking(a):
+    """Block project and promote (one GEMM per coarse site): K applications
+    of each on a random basis, inputs resident in HBM."""
+    import torch
+    import paper_2409_03904_b300 as mrhs
+    nblk, vb, nbasis = (int(v) for v in a.blocks.split(","))
+    R = a.nrhs or 12
+    dt = torch.complex128 if a.dtype == "c128" else torch.complex64
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(2409)
+    B = torch.randn((nblk, vb, nbasis), dtype=dt, device=dev, generator=g)
+    F = torch.randn((nblk, vb, R), dtype=dt, device=dev, generator=g)
+    C = torch.randn((nblk, nbasis, R), dtype=dt, device=dev, generator=g)
+    stream = torch.cuda.current_stream()
+    res = {}
+    es = 16 if a.dtype == "c128" else 8
+    flops = 8.0 * nblk * vb * nbasis * R
+    hbm, _, kind = peaks()
+    for name, fn in (("project", lambda: mrhs.block_project(B, F)),
+                     ("promote", lambda: mrhs.block_promote(B, C))):
+        for _ in range(a.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        byts = es * nblk * (vb * nbasis + vb * R + nbasis * R)
+        res[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                     "gbs": byts / (ms * 1e-3) / 1e9, "hbm_frac": byts / (ms * 1e-3) / 1e9 / hbm}
+    ms = res["project"]["ms"] + res["promote"]["ms"]
+    out = {"metric": "block project + promote time", "value": ms, "unit": "ms",
+           "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": a.dtype, "data": "synthetic",
+           "config": {"workload": f"block project/promote, {nblk} blocks of {vb} x {nbasis}, "
+                                  f"{R} RHS", "l2": f"basis {es * nblk * vb * nbasis / 1e9:.2f} GB"},
+           "project": res["project"], "promote": res["promote"],
+           "peak_kind": f"{kind} copy bandwidth"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     from synth import WORKLOADS, load_shift
@@ -448,6 +498,8 @@ def main():
         return run_op(a, w, shift)
     if a.defl is not None:
         return run_defl(a, w, shift)
+    if a.blocking:
+        return run_blocking(a)
 
     import torch
     import torch.distributed as dist

@@ -184,6 +184,22 @@ int herm_factor(const void* G, void* S, void* W, int32_t* rank, int32_t r, doubl
 int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, const void* X,
                 void* P, int32_t nrhs, void* stream);
 
+/* Block project and promote between fine and coarse degrees of freedom
+ * (Sec. 3.4): one GEMM per coarse site x,
+ *   block_project:  C(x) = B(x)^dagger F(x)   (n_basis x nrhs)
+ *   block_promote:  F(x) = B(x) C(x)          (v_block x nrhs)
+ * basis: device [n_blocks][v_block][n_basis]; F: device
+ * [n_blocks][v_block][nrhs]; C: device [n_blocks][n_basis][nrhs] (the coarse
+ * vector layout [V][nb][nrhs] with V = n_blocks, nb = n_basis).  dtype
+ * MRHS_C128 (FP64 arithmetic) or MRHS_C64 (FP32) for all three arrays.
+ * 1 <= v_block, 1 <= n_basis <= 256, 1 <= nrhs <= 64 (project also needs
+ * nrhs <= 16 * (256 / n_basis)); n_blocks = 0 does nothing.  The output
+ * must not overlap the inputs.  Asynchronous on `stream`. */
+int block_project(const void* basis, const void* F, void* C, int64_t n_blocks, int32_t v_block,
+                  int32_t n_basis, int32_t nrhs, int32_t dtype, void* stream);
+int block_promote(const void* basis, const void* C, void* F, int64_t n_blocks, int32_t v_block,
+                  int32_t n_basis, int32_t nrhs, int32_t dtype, void* stream);
+
 /* Deflated Chebyshev coarse solve Q^{Cheby+defl} (Sec. 2.3, the "two step
  * deflated/Chebyshev coarse solve"):
  *   X = U Lambda^-1 U^dagger B + p(H) (B - U U^dagger B),

@@ -16,6 +16,7 @@ from ._lib import C64, C128, PREC, SOLVE_FP64, SOLVE_MIXED, MrhsError, SolveInfo
 
 __all__ = ["CoarseOp", "coarse_apply", "coarse_solve", "batch_apply", "batch_solve", "autotune",
            "autotune_save", "autotune_load", "autotune_entries", "autotune_clear", "block_inner",
+           "block_project", "block_promote",
            "block_axpy", "herm_factor", "MrhsError", "PREC",
            "SOLVE_FP64", "SOLVE_MIXED", "device_error", "version"]
 
@@ -277,6 +278,36 @@ def _dtype_code(t):
     if t.dtype == torch.complex64:
         return C64
     raise TypeError("vectors must be complex128 or complex64")
+
+
+def block_project(basis, F):
+    """C[x] = basis[x]^dagger F[x] per coarse site x (Sec. 3.4): basis
+    [n_blocks][v_block][n_basis], F [n_blocks][v_block][nrhs] -> C
+    [n_blocks][n_basis][nrhs]; complex128 (FP64) or complex64 (FP32)."""
+    nblk, vb, nbasis = (int(v) for v in basis.shape)
+    if F.dtype != basis.dtype or F.shape[:2] != (nblk, vb):
+        raise ValueError("F must be [n_blocks][v_block][nrhs] of the basis dtype")
+    R = int(F.shape[2])
+    C = torch.empty((nblk, nbasis, R), dtype=F.dtype, device=F.device)
+    _lib.check(_lib.lib().block_project(_lib.dev_ptr(basis, None, "basis"), _lib.dev_ptr(F, None, "F"),
+                                        _lib.dev_ptr(C), nblk, vb, nbasis, R, _dtype_code(F),
+                                        _lib.stream_ptr()))
+    return C
+
+
+def block_promote(basis, C):
+    """F[x] = basis[x] C[x] per coarse site x (Sec. 3.4): basis
+    [n_blocks][v_block][n_basis], C [n_blocks][n_basis][nrhs] -> F
+    [n_blocks][v_block][nrhs]; complex128 (FP64) or complex64 (FP32)."""
+    nblk, vb, nbasis = (int(v) for v in basis.shape)
+    if C.dtype != basis.dtype or C.shape[:2] != (nblk, nbasis):
+        raise ValueError("C must be [n_blocks][n_basis][nrhs] of the basis dtype")
+    R = int(C.shape[2])
+    F = torch.empty((nblk, vb, R), dtype=C.dtype, device=C.device)
+    _lib.check(_lib.lib().block_promote(_lib.dev_ptr(basis, None, "basis"), _lib.dev_ptr(C, None, "C"),
+                                        _lib.dev_ptr(F), nblk, vb, nbasis, R, _dtype_code(C),
+                                        _lib.stream_ptr()))
+    return F
 
 
 def block_inner(X, Y):

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "internal.cuh"
 
@@ -384,6 +385,40 @@ int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, c
   if (order < 0 || order > 10000) return fail(MRHS_ERR_INVALID_ARG, "order");
   if (X == P) return fail(MRHS_ERR_INVALID_ARG, "X and P must differ");
   return cheby(op, prec, lo, hi, order, X, P, nrhs, (cudaStream_t)stream);
+}
+
+static int blocking_common(bool project, const void* basis, const void* in, void* out,
+                           int64_t nblk, int32_t vb, int32_t nbasis, int32_t nrhs, int32_t dtype,
+                           void* stream) {
+  const char* name = project ? "block_project" : "block_promote";
+  if (nblk < 0 || vb < 1 || nbasis < 1 || nbasis > 256 || nrhs < 1 || nrhs > MRHS_MAX_RHS)
+    return fail(MRHS_ERR_INVALID_ARG, std::string(name) + ": sizes");
+  if (dtype != MRHS_C128 && dtype != MRHS_C64) return fail(MRHS_ERR_INVALID_ARG, "dtype");
+  if (project && nrhs > 16 * (256 / nbasis))
+    return fail(MRHS_ERR_INVALID_ARG, "block_project: nrhs > 16 x (256 / n_basis)");
+  if (nblk == 0) return MRHS_OK;
+  MRHS_TRY(check_vec(basis, "basis"));
+  MRHS_TRY(check_vec(in, project ? "F" : "C"));
+  MRHS_TRY(check_vec(out, project ? "C" : "F"));
+  const size_t es = dtype == MRHS_C128 ? 16 : 8;
+  const size_t nF = es * (size_t)nblk * vb * nrhs, nC = es * (size_t)nblk * nbasis * nrhs;
+  const size_t nB = es * (size_t)nblk * vb * nbasis;
+  const size_t in_b = project ? nF : nC, out_b = project ? nC : nF;
+  const char* o = (const char*)out;
+  for (auto pr : {std::make_pair((const char*)in, in_b), std::make_pair((const char*)basis, nB)})
+    if (o < pr.first + pr.second && pr.first < o + out_b)
+      return fail(MRHS_ERR_INVALID_ARG, std::string(name) + ": output overlaps an input");
+  return blocking(project, basis, in, out, nblk, vb, nbasis, nrhs, dtype, (cudaStream_t)stream);
+}
+
+int block_project(const void* basis, const void* F, void* C, int64_t n_blocks, int32_t v_block,
+                  int32_t n_basis, int32_t nrhs, int32_t dtype, void* stream) {
+  return blocking_common(true, basis, F, C, n_blocks, v_block, n_basis, nrhs, dtype, stream);
+}
+
+int block_promote(const void* basis, const void* C, void* F, int64_t n_blocks, int32_t v_block,
+                  int32_t n_basis, int32_t nrhs, int32_t dtype, void* stream) {
+  return blocking_common(false, basis, C, F, n_blocks, v_block, n_basis, nrhs, dtype, stream);
 }
 
 int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const double* lambda,

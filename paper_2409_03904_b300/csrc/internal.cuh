@@ -157,6 +157,8 @@ int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* 
           int R, cudaStream_t s);
 int defl_cheby(mrhs_op_s* op, int prec, const void* U, const double* lam_host, int n_ev,
                double lo, double hi, int order, const void* B, void* X, int R, cudaStream_t s);
+int blocking(bool project, const void* basis, const void* in, void* out, int64_t nblk, int vb,
+             int nbasis, int R, int dtype, cudaStream_t s);
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam);
 int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* const* X,
                 const int32_t* nrhs, const mrhs_solve_params& p, mrhs_solve_info* infos,
