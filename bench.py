@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--blocks", default="4096,256,64",
                     help="n_blocks,v_block,n_basis for --blocking (nrhs from --nrhs, default 12)")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--batch", default=None, choices=["config4", "small"],
+                    help="batched solve of independent problems against one-at-a-time solves: "
+                         "the twelve config-4 problems, or twelve 4^4 problems")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run before the timed region)")
     return ap.parse_args()
@@ -487,6 +490,68 @@ def run_blocking(a):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(a):
+    """Lockstep batched mixed solve (mrhs_batch_solve) against the same
+    problems solved one after another (block_cg_solve), to tol 1e-8, plus
+    one batched operator application against the single ones."""
+    import torch
+    import paper_2409_03904_b300 as mrhs
+    import synth.device as sdev
+    from synth import BATCH, load_shift, stencil
+    if a.batch == "config4":
+        probs = [(w, 0) for w in BATCH]
+    else:      # the four 4^4 problems of the list, three sources each
+        small = [w for w in BATCH if w["L"] == (4, 4, 4, 4)]
+        probs = [(w, c) for c in range(3) for w in small]
+    ops, Bs = [], []
+    for w, c in probs:
+        disp, _ = stencil(w["npts"])
+        A = sdev.coarse_op(w["L"], w["nb"], w["npts"], w["seed"], load_shift(w["name"]))
+        ops.append(mrhs.CoarseOp(A, w["L"], disp, ("fp64", "fp16x", "tc32")))
+        del A
+        Bs.append(sdev.vectors(w["L"], w["nb"], w["nrhs"], w["seed"] + 101 * c))
+    for o in ops:
+        o.lambda_max("fp16x", 40)
+
+    def timed(f):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = f()
+        torch.cuda.synchronize()
+        return r, (time.perf_counter() - t) * 1e3
+
+    tb, ts = [], []
+    for i in range(a.warmup + a.steps):
+        (Xs, infos), t1 = timed(lambda: mrhs.batch_solve(ops, Bs, tol=1e-8))
+        res, t2 = timed(lambda: [o.solve(B, mode="mixed", tol=1e-8) for o, B in zip(ops, Bs)])
+        if i >= a.warmup:
+            tb.append(t1)
+            ts.append(t2)
+    Xc = [B.to(torch.complex64) for B in Bs]
+    apply = {}
+    for p in ("fp16x", "tc32"):
+        for _ in range(3):
+            mrhs.batch_apply(ops, Xc, p)
+        _, t1 = timed(lambda: [mrhs.batch_apply(ops, Xc, p) for _ in range(20)])
+        for _ in range(3):
+            [o.apply(X, p) for o, X in zip(ops, Xc)]
+        _, t2 = timed(lambda: [[o.apply(X, p) for o, X in zip(ops, Xc)] for _ in range(20)])
+        apply[p] = {"batched_ms": t1 / 20, "one_by_one_ms": t2 / 20}
+    nrhs = sum(int(B.shape[2]) for B in Bs)
+    bt, st = statistics.median(tb), statistics.median(ts)
+    out = {"metric": "batched block-CG time-to-1e-8 per RHS", "value": bt / nrhs, "unit": "ms/RHS",
+           "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": bt,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+df32+tc32+fp16x", "data": "synthetic",
+           "config": {"workload": f"{len(probs)} independent problems ({a.batch})",
+                      "problems": [w["name"] for w, _ in probs], "nrhs_total": nrhs, "tol": 1e-8},
+           "one_by_one_ms": st, "batched_over_one_by_one": st / bt,
+           "iters": [i["iters"] for i in infos],
+           "max_true_resid": max(max(i["resid"]) for i in infos),
+           "apply": apply}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     from synth import WORKLOADS, load_shift
@@ -500,6 +565,8 @@ def main():
         return run_defl(a, w, shift)
     if a.blocking:
         return run_blocking(a)
+    if a.batch:
+        return run_batch(a)
 
     import torch
     import torch.distributed as dist
