@@ -953,6 +953,43 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
   }
   MRHS_CUDA_TRY(cudaStreamSynchronize(s));
 
+  // one side stream per problem: the per-problem block algebra of an
+  // iteration forks onto them (event fork / join), so inside a captured graph
+  // the problems' small kernels are parallel branches instead of a chain
+  struct Side {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    ~Side() {
+      for (cudaStream_t x : st) if (x) cudaStreamDestroy(x);
+      for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
+      if (fork) cudaEventDestroy(fork);
+    }
+  } side;
+  side.st.assign(n, nullptr);
+  side.join.assign(n, nullptr);
+  MRHS_CUDA_TRY(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+  for (int i = 0; i < n; ++i) {
+    MRHS_CUDA_TRY(cudaStreamCreateWithFlags(&side.st[i], cudaStreamNonBlocking));
+    MRHS_CUDA_TRY(cudaEventCreateWithFlags(&side.join[i], cudaEventDisableTiming));
+  }
+  // run fn(k, stream) for every problem idx[k] on its side stream, joined back
+  auto fork_each = [&](const std::vector<int>& ids, auto&& fn) -> int {
+    MRHS_CUDA_TRY(cudaEventRecord(side.fork, s));
+    for (int k = 0; k < (int)ids.size(); ++k) {
+      const int i = ids[k];
+      MRHS_CUDA_TRY(cudaStreamWaitEvent(side.st[i], side.fork, 0));
+      P[i].cx.s = side.st[i];
+      const int st = fn(k, side.st[i]);
+      P[i].cx.s = s;
+      if (st != MRHS_OK) return st;
+      MRHS_CUDA_TRY(cudaEventRecord(side.join[i], side.st[i]));
+    }
+    for (int k = 0; k < (int)ids.size(); ++k)
+      MRHS_CUDA_TRY(cudaStreamWaitEvent(s, side.join[ids[k]], 0));
+    return MRHS_OK;
+  };
+
   auto residual_in = [&](BatchProb& b, int i, int rp) -> int {
     Ctx& cx = b.cx;
     const int64_t nn = cx.N * cx.R;
@@ -1066,31 +1103,33 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
         out[k] = P[idx[k]].sb.b32.cw;
       }
       MRHS_TRY(bapply(pp));
-      for (int k = 0; k < m; ++k) {
+      MRHS_TRY(fork_each(idx, [&](int k, cudaStream_t ss) -> int {
         BatchProb& b = P[idx[k]];
         const std::vector<double>& c = coef[idx[k]];
         const double a = 2.0 / (b.hi - b.lo), bb = -(b.hi + b.lo) / (b.hi - b.lo);
         const int64_t nn = b.cx.N * b.cx.R;
-        { k_cheb_first<float2><<<grid_for(nn), kThreads, 0, s>>>(b.sb.b32.c1, Ps[k], b.sb.b32.cw, Xs[k], a, bb, c[0], order > 0 ? c[1] : 0.0, nn); ::mrhs::count_launch(); }
+        { k_cheb_first<float2><<<grid_for(nn), kThreads, 0, ss>>>(b.sb.b32.c1, Ps[k], b.sb.b32.cw, Xs[k], a, bb, c[0], order > 0 ? c[1] : 0.0, nn); ::mrhs::count_launch(); }
         Tprev[k] = Xs[k];
         Tcur[k] = b.sb.b32.c1;
-      }
+        return MRHS_OK;
+      }));
       for (int j = 2; j <= order; ++j) {
         for (int k = 0; k < m; ++k) {
           in[k] = Tcur[k];
           out[k] = P[idx[k]].sb.b32.cw;
         }
         MRHS_TRY(bapply(pp));
-        for (int k = 0; k < m; ++k) {
+        MRHS_TRY(fork_each(idx, [&](int k, cudaStream_t ss) -> int {
           BatchProb& b = P[idx[k]];
           const std::vector<double>& c = coef[idx[k]];
           const double a = 2.0 / (b.hi - b.lo), bb = -(b.hi + b.lo) / (b.hi - b.lo);
           const int64_t nn = b.cx.N * b.cx.R;
           float2* dst = (Tprev[k] == Xs[k]) ? b.sb.b32.c2 : const_cast<float2*>(Tprev[k]);
-          { k_cheb_step<float2><<<grid_for(nn), kThreads, 0, s>>>(dst, Ps[k], b.sb.b32.cw, Tcur[k], Tprev[k], a, bb, c[j], nn); ::mrhs::count_launch(); }
+          { k_cheb_step<float2><<<grid_for(nn), kThreads, 0, ss>>>(dst, Ps[k], b.sb.b32.cw, Tcur[k], Tprev[k], a, bb, c[j], nn); ::mrhs::count_launch(); }
           Tprev[k] = Tcur[k];
           Tcur[k] = dst;
-        }
+          return MRHS_OK;
+        }));
       }
       MRHS_CUDA_TRY(cudaGetLastError());
       return MRHS_OK;
@@ -1104,15 +1143,16 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
         Ps[k] = P[idx[k]].sb.b32.Q;
       }
       MRHS_TRY(bcheb(Xs.data(), Ps.data()));
-      for (int k = 0; k < m; ++k) {
+      MRHS_TRY(fork_each(idx, [&](int k, cudaStream_t ss) -> int {
         BatchProb& b = P[idx[k]];
         Ctx& cx = b.cx;
         MRHS_TRY(cx.gram<float2>(b.sb.b32.Q, b.sb.b32.q, cx.st->G));
         MRHS_TRY(cx.small_launch(0));
-        MRHS_CUDA_TRY(cudaMemsetAsync(b.sb.b32.D, 0, sizeof(float2) * cx.N * cx.R, s));
-        MRHS_CUDA_TRY(cudaMemsetAsync(cx.st->S, 0, sizeof(double2) * 64 * 64, s));
+        MRHS_CUDA_TRY(cudaMemsetAsync(b.sb.b32.D, 0, sizeof(float2) * cx.N * cx.R, ss));
+        MRHS_CUDA_TRY(cudaMemsetAsync(cx.st->S, 0, sizeof(double2) * 64 * 64, ss));
         MRHS_TRY(cx.rotate<float2>(b.sb.b32.q, b.sb.b32.Q, b.sb.b32.D));
-      }
+        return MRHS_OK;
+      }));
     }
     auto body = [&]() -> int {
       for (int k = 0; k < m; ++k) {
@@ -1126,21 +1166,21 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
         Ps[k] = P[idx[k]].sb.b32.Zz;
       }
       MRHS_TRY(bcheb(Xs.data(), Ps.data()));                         // Z = M^-1 z
-      for (int k = 0; k < m; ++k) {
+      return fork_each(idx, [&](int k, cudaStream_t ss) -> int {
         BatchProb& b = P[idx[k]];
         Ctx& cx = b.cx;
         BcgBufs<float2>& q = b.sb.b32;
         MRHS_TRY(cx.gram<float2>(q.D, q.z, cx.st->G));
         MRHS_TRY(cx.small_launch(1));
-        MRHS_TRY(axpy(b.sb.e32, q.D, cx.st->MC, 1.0, cx.N, cx.R, cx.R, MRHS_C64, s));
-        MRHS_TRY(axpy(q.q, q.z, cx.st->negM, 1.0, cx.N, cx.R, cx.R, MRHS_C64, s));
-        MRHS_TRY(axpy(q.Q, q.Zz, cx.st->negM, 1.0, cx.N, cx.R, cx.R, MRHS_C64, s));
+        MRHS_TRY(axpy(b.sb.e32, q.D, cx.st->MC, 1.0, cx.N, cx.R, cx.R, MRHS_C64, ss));
+        MRHS_TRY(axpy(q.q, q.z, cx.st->negM, 1.0, cx.N, cx.R, cx.R, MRHS_C64, ss));
+        MRHS_TRY(axpy(q.Q, q.Zz, cx.st->negM, 1.0, cx.N, cx.R, cx.R, MRHS_C64, ss));
         MRHS_TRY(cx.gram<float2>(q.Q, q.q, cx.st->G));
         MRHS_TRY(cx.gram<float2>(q.q, q.q, cx.st->G2));
         MRHS_TRY(cx.small_launch(2, 1));
         MRHS_TRY(cx.rotate<float2>(q.q, q.Q, q.D));
-      }
-      return MRHS_OK;
+        return MRHS_OK;
+      });
     };
 
     cudaGraphExec_t exec = nullptr;
