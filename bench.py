@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cheb-order", type=int, default=8)
     ap.add_argument("--cheb-ratio", type=float, default=400.0, help="hi / lo")
     ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--check-every", type=int, default=2,
+                    help="block-CG iterations between convergence checks (one graph chunk)")
     ap.add_argument("--fp64-iters", type=int, default=3,
                     help="FP64 block-CG iterations timed for the plain-FP64 comparison")
     ap.add_argument("--fp64-full", action="store_true",
@@ -601,7 +603,8 @@ def main():
     params = dict(mode="mixed", tol=1e-8, precond=1, precond_prec=a.precond,
                   krylov_prec=a.krylov,
                   cheb_order=a.cheb_order, cheb_hi=hi, cheb_lo=hi / a.cheb_ratio,
-                  inner_tol=a.inner_tol, maxiter=20000, max_cycles=20, check_every=4)
+                  inner_tol=a.inner_tol, maxiter=20000, max_cycles=20,
+                  check_every=a.check_every)
 
     stream = torch.cuda.current_stream()
     # launch shapes of the two tensor-core forms, tuned once for this shape
