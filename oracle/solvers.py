@@ -255,3 +255,37 @@ def lanczos_extremes(apply_H, v0, steps):
     bmin = abs(betas[-1] * evecs[-1, 0])
     bmax = abs(betas[-1] * evecs[-1, -1])
     return float(evals[0]), float(evals[-1]), float(bmin), float(bmax)
+
+
+def cg5d(apply_H, B, X0=None, tol=1e-10, maxiter=1000, history=None):
+    """Conjugate gradients on the enlarged system (Sec. 2.2: the coarse solve
+    treated as one five-dimensional system with a single Krylov space, block
+    diagonal in the right-hand-side index).  The vector is the whole block
+    [V][nb][R]; alpha and beta come from inner products summed over all
+    right-hand sides; the iteration stops when every column's recurrence
+    residual satisfies |r_j| <= tol |b_j|, and the result carries the true
+    residuals."""
+    shape = B.shape
+    Bm = as_matrix(np.asarray(B, dtype=np.complex128))
+    R = Bm.shape[1]
+    H = lambda M: as_matrix(apply_H(M.reshape(shape)))
+    X = np.zeros_like(Bm) if X0 is None else as_matrix(np.asarray(X0, dtype=np.complex128)).copy()
+    r = Bm - H(X)
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    bn = np.linalg.norm(Bm, axis=0)
+    k = 0
+    for k in range(1, maxiter + 1):
+        w = H(p)
+        alpha = rr / np.vdot(p, w).real
+        X = X + alpha * p
+        r = r - alpha * w
+        rr_new = np.vdot(r, r).real
+        if history is not None:
+            history.append(dict(X=X.copy(), r=r.copy(), alpha=alpha))
+        if np.all(np.linalg.norm(r, axis=0) <= tol * np.where(bn > 0, bn, 1.0)):
+            break
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    res = np.linalg.norm(Bm - H(X), axis=0) / np.where(bn > 0, bn, 1.0)
+    return X.reshape(shape), dict(iters=k, resid=res)
