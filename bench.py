@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--batch", default=None, choices=["config4", "small"],
                     help="batched solve of independent problems against one-at-a-time solves: "
                          "the twelve config-4 problems, or twelve 4^4 problems")
+    ap.add_argument("--cg5d", action="store_true",
+                    help="one CG on the enlarged 5D system (Sec. 2.2) against FP64 block CG")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run before the timed region)")
     return ap.parse_args()
@@ -554,6 +556,38 @@ def run_batch(a):
     print(json.dumps(out), flush=True)
 
 
+def run_cg5d(a, w, shift):
+    """Unpreconditioned FP64 solves to 1e-8 of the workload: BlockCGrQ
+    (Fig. 2 left) against one CG on the enlarged five-dimensional system with
+    the FP64 and the DF32 operator; iterations and wall time."""
+    import torch
+    import paper_2409_03904_b300 as mrhs
+    import synth.device as sdev
+    from synth import stencil
+    R, nb = w["nrhs"], w["nb"]
+    disp, _ = stencil(w["npts"])
+    dev = torch.device("cuda", 0)
+    A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
+    op = mrhs.CoarseOp(A, w["L"], disp, ("fp64",))
+    del A
+    torch.cuda.empty_cache()
+    B = sdev.vectors(w["L"], nb, R, w["seed"], device=dev)
+    runs = {"block_cg_fp64": dict(mode="fp64"), "cg5d_fp64": dict(mode="cg5d"),
+            "cg5d_df32": dict(mode="cg5d", krylov_prec="df32")}
+    res = {}
+    for name, kw in runs.items():
+        for i in range(a.warmup + 1):
+            X, info = op.solve(B, tol=1e-8, maxiter=20000, raise_on_fail=False, **kw)
+        res[name] = {"iters": info["iters"], "ms": info["ms_total"], "ms_per_rhs": info["ms_total"] / R,
+                     "max_true_resid": max(info["resid"]), "ms_per_iter": info["ms_total"] / max(info["iters"], 1)}
+    out = {"metric": "unpreconditioned FP64 solve time per RHS: block CG vs 5D CG",
+           "value": res["cg5d_fp64"]["ms_per_rhs"], "unit": "ms/RHS", "n_gpus": 1,
+           "steps": 1, "warmup": a.warmup, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w["name"], "tol": 1e-8, "nrhs": R}, "solves": res}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     from synth import WORKLOADS, load_shift
@@ -569,6 +603,8 @@ def main():
         return run_blocking(a)
     if a.batch:
         return run_batch(a)
+    if a.cg5d:
+        return run_cg5d(a, w, shift)
 
     import torch
     import torch.distributed as dist

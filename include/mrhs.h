@@ -232,7 +232,7 @@ int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, voi
 typedef struct {
   double tol;           /* per-RHS relative true residual |b_r - H x_r| / |b_r| */
   int32_t maxiter;      /* cap on Krylov iterations (all cycles together) */
-  int32_t mode;         /* MRHS_SOLVE_FP64 or MRHS_SOLVE_MIXED */
+  int32_t mode;         /* MRHS_SOLVE_FP64, MRHS_SOLVE_MIXED or MRHS_SOLVE_CG5D */
   int32_t precond;      /* 0: BlockCGrQ (Fig. 2 left); 1: Chebyshev-preconditioned
                            BlockCGrQ (Fig. 2 right) */
   int32_t precond_prec; /* MRHS_PREC_* of the Chebyshev operator applications;
@@ -263,10 +263,17 @@ typedef struct {
 
 enum {
   MRHS_SOLVE_FP64 = 0,  /* everything FP64 (plain FP64 block CG) */
-  MRHS_SOLVE_MIXED = 1  /* FP64 outer defect correction (true residual, Gram
+  MRHS_SOLVE_MIXED = 1, /* FP64 outer defect correction (true residual, Gram
                            accumulation, Cholesky, solution update); inner block
-                           CG on complex64 vectors with the FP32 operator and
-                           the low-precision Chebyshev preconditioner */
+                           CG on complex64 vectors with the TC32 (or FP32)
+                           operator and the low-precision Chebyshev
+                           preconditioner */
+  MRHS_SOLVE_CG5D = 2   /* Sec. 2.2's "enlarged five dimensional system": plain
+                           CG on the whole block, alpha and beta from inner
+                           products summed over all right-hand sides, no
+                           preconditioner; operator krylov_prec = FP64 (default,
+                           -1) or DF32; stops when every column's recurrence
+                           residual meets tol, info reports FP64 true residuals */
 };
 
 typedef struct {

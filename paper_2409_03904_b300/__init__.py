@@ -12,7 +12,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import C64, C128, PREC, SOLVE_FP64, SOLVE_MIXED, MrhsError, SolveInfo, SolveParams
+from ._lib import (C64, C128, PREC, SOLVE_CG5D, SOLVE_FP64, SOLVE_MIXED, MrhsError, SolveInfo,
+                   SolveParams)
 
 __all__ = ["CoarseOp", "coarse_apply", "coarse_solve", "batch_apply", "batch_solve", "autotune",
            "autotune_save", "autotune_load", "autotune_entries", "autotune_clear", "block_inner",
@@ -174,12 +175,17 @@ class CoarseOp:
 
         mode "fp64": plain FP64 BlockCGrQ (precond=1 with precond_prec "fp64"
         for the FP64 Chebyshev-preconditioned form); mode "mixed": FP64-outer
-        defect correction around a complex64 preconditioned block CG.
+        defect correction around a complex64 preconditioned block CG; mode
+        "cg5d": one CG on the enlarged five-dimensional system (krylov_prec
+        "fp64" or "df32").
         Keyword arguments override mrhs_solve_params fields.
         """
         l = _lib.lib()
         p = SolveParams()
-        l.mrhs_solve_params_default(ctypes.byref(p), SOLVE_MIXED if mode == "mixed" else SOLVE_FP64)
+        modes = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED, "cg5d": SOLVE_CG5D}
+        if mode not in modes:
+            raise ValueError(f"mode must be one of {sorted(modes)}")
+        l.mrhs_solve_params_default(ctypes.byref(p), modes[mode])
         for k, v in kw.items():
             if k in ("precond_prec", "krylov_prec", "residual_prec") and isinstance(v, str):
                 v = PREC[v]

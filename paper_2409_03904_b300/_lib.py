@@ -21,7 +21,7 @@ NUM_PREC = 7
 NAMES = {v: k for k, v in PREC.items()}
 C128, C64 = 0, 1
 MAX_RHS = 64
-SOLVE_FP64, SOLVE_MIXED = 0, 1
+SOLVE_FP64, SOLVE_MIXED, SOLVE_CG5D = 0, 1, 2
 
 
 class MrhsError(RuntimeError):

@@ -461,10 +461,19 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
   if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
   const mrhs_solve_params& p = *params;
   if (!(p.tol > 0.0) || p.maxiter < 1) return fail(MRHS_ERR_INVALID_ARG, "tol / maxiter");
-  if (p.mode != MRHS_SOLVE_FP64 && p.mode != MRHS_SOLVE_MIXED)
+  if (p.mode != MRHS_SOLVE_FP64 && p.mode != MRHS_SOLVE_MIXED && p.mode != MRHS_SOLVE_CG5D)
     return fail(MRHS_ERR_INVALID_ARG, "mode");
   if (!(op->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)))
     return fail(MRHS_ERR_UNSUPPORTED, "block_cg_solve needs the FP64 operator");
+  if (p.mode == MRHS_SOLVE_CG5D) {
+    mrhs_solve_params q = p;
+    if (q.krylov_prec < 0) q.krylov_prec = MRHS_PREC_FP64;
+    if (q.krylov_prec != MRHS_PREC_FP64 && q.krylov_prec != MRHS_PREC_DF32)
+      return fail(MRHS_ERR_INVALID_ARG, "CG5D runs the FP64 or DF32 operator");
+    if (q.precond) return fail(MRHS_ERR_INVALID_ARG, "CG5D takes no preconditioner");
+    if (X == B) return fail(MRHS_ERR_INVALID_ARG, "X and B must differ");
+    return cg5d(op, (const double2*)B, (double2*)X, nrhs, q, info, (cudaStream_t)stream);
+  }
   mrhs_solve_params q = p;   // resolve the automatic precision choices
   auto built = [&](int pr) { return (op->prec_mask & MRHS_PREC_BIT(pr)) != 0; };
   auto fits = [&](int pr) {

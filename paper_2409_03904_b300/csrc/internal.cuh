@@ -153,6 +153,8 @@ int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, 
 // solver.cu
 int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
           mrhs_solve_info* info, cudaStream_t s);
+int cg5d(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
+         mrhs_solve_info* info, cudaStream_t s);
 int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* X, void* P,
           int R, cudaStream_t s);
 int defl_cheby(mrhs_op_s* op, int prec, const void* U, const double* lam_host, int n_ev,

@@ -22,6 +22,7 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -1333,6 +1334,196 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
   }
   if (worst != MRHS_OK) set_error(worst == MRHS_ERR_NONFINITE ? "non-finite value in a batched solve" : "a batched problem did not converge");
   return worst;
+}
+
+}  // namespace mrhs
+
+// ---------------------------------------------------------------- 5D CG
+// The coarse solve as one enlarged five-dimensional system (Sec. 2.2): plain
+// CG on the whole [V][nb][R] block, alpha and beta from inner products summed
+// over every right-hand side, so the block algebra is two scalar reductions
+// and three vector updates per iteration instead of Grams and a Hermitian
+// factorisation.  The scalars stay on the device; the host reads per-column
+// residual norms every check_every iterations to stop.
+namespace mrhs {
+namespace {
+
+// per-block partial sums of Re <x, y> over a row range, fixed order
+__global__ void k_dot5d_partial(const double2* __restrict__ x, const double2* __restrict__ y,
+                                double* part, int64_t n, int64_t per) {
+  __shared__ double sm[kThreads];
+  const int64_t i0 = (int64_t)blockIdx.x * per;
+  const int64_t i1 = (i0 + per) < n ? (i0 + per) : n;
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+    const double2 a = x[i], b = y[i];
+    acc = fma(a.x, b.x, fma(a.y, b.y, acc));
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+__global__ void k_dot5d_final(const double* __restrict__ part, int nblk, double* out) {
+  __shared__ double sm[kThreads];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += kThreads) acc += part[b];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+// sc = {rr, pw, rr_new}: X += a p, r -= a w with a = rr / pw, and the
+// partial sums of |r|^2 of the updated residual
+__global__ void k_cg5d_update(double2* X, double2* r, const double2* __restrict__ p,
+                              const double2* __restrict__ w, const double* __restrict__ sc,
+                              double* part, int64_t n, int64_t per) {
+  __shared__ double sm[kThreads];
+  const double a = sc[0] / sc[1];
+  const int64_t i0 = (int64_t)blockIdx.x * per;
+  const int64_t i1 = (i0 + per) < n ? (i0 + per) : n;
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+    const double2 pv = p[i], wv = w[i];
+    double2 xv = X[i], rv = r[i];
+    xv.x = fma(a, pv.x, xv.x);
+    xv.y = fma(a, pv.y, xv.y);
+    rv.x = fma(-a, wv.x, rv.x);
+    rv.y = fma(-a, wv.y, rv.y);
+    X[i] = xv;
+    r[i] = rv;
+    acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int wd = kThreads / 2; wd > 0; wd >>= 1) {
+    if (threadIdx.x < wd) sm[threadIdx.x] += sm[threadIdx.x + wd];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// p = r + b p with b = rr_new / rr
+__global__ void k_cg5d_dir(double2* p, const double2* __restrict__ r,
+                           const double* __restrict__ sc, int64_t n) {
+  const double b = sc[2] / sc[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 rv = r[i];
+    double2 pv = p[i];
+    pv.x = fma(b, pv.x, rv.x);
+    pv.y = fma(b, pv.y, rv.y);
+    p[i] = pv;
+  }
+}
+
+__global__ void k_cg5d_roll(double* sc) { sc[0] = sc[2]; }
+
+}  // namespace
+
+int cg5d(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_params& p,
+         mrhs_solve_info* info, cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int prec = p.krylov_prec >= 0 ? p.krylov_prec : MRHS_PREC_FP64;
+  Ctx cx;
+  cx.op = op;
+  cx.s = s;
+  cx.R = R;
+  cx.N = op->V * op->nb;
+  const int64_t n = cx.N * R;
+  const int nblk = num_sms() * 4;
+  const int64_t per = (n + nblk - 1) / nblk;
+  double2 *r = nullptr, *pv = nullptr, *w = nullptr;
+  double *part = nullptr, *sc = nullptr, *bnorm_d = nullptr, *rnorm_d = nullptr;
+  for (int pass = 0; pass < 2; ++pass) {      // sizing, then assignment
+    cx.used = 0;
+    cx.alloc(&r, n);
+    cx.alloc(&pv, n);
+    cx.alloc(&w, n);
+    cx.alloc(&part, nblk);
+    cx.alloc(&sc, 4);
+    cx.alloc(&bnorm_d, R);
+    cx.alloc(&rnorm_d, R);
+    cx.alloc(&cx.npart, (size_t)num_sms() * 2 * R + R);
+    if (pass == 0) {
+      MRHS_TRY(op->ws_solve.ensure(cx.used));
+      cx.base = (char*)op->ws_solve.ptr;
+    }
+  }
+  const int g = grid_for(n);
+  std::vector<double> bnorm(R), rnorm(R);
+  MRHS_TRY(cx.colnorms<double2>(B, bnorm_d));
+  { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, bnorm_d, cx.N, R); ::mrhs::count_launch(); }
+  MRHS_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), bnorm_d, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  // r = B - H X (X = 0: r = B)
+  MRHS_TRY(cx.apply(prec, X, r));
+  { k_sub<double2><<<g, kThreads, 0, s>>>(r, B, r, n); ::mrhs::count_launch(); }
+  MRHS_CUDA_TRY(cudaMemcpyAsync(pv, r, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+  { k_dot5d_partial<<<nblk, kThreads, 0, s>>>(r, r, part, n, per); ::mrhs::count_launch(); }
+  { k_dot5d_final<<<1, kThreads, 0, s>>>(part, nblk, sc); ::mrhs::count_launch(); }
+  MRHS_CUDA_TRY(cudaGetLastError());
+  auto all_done = [&]() {
+    for (int j = 0; j < R; ++j)
+      if (bnorm[j] > 0 && !(rnorm[j] <= p.tol * bnorm[j])) return false;
+    return true;
+  };
+  const int every = p.check_every > 0 ? p.check_every : 1;
+  int it = 0;
+  bool done = false;
+  while (it < p.maxiter && !done) {
+    const int chunk = (p.maxiter - it) < every ? (p.maxiter - it) : every;
+    for (int j = 0; j < chunk; ++j) {
+      MRHS_TRY(cx.apply(prec, pv, w));                                            // w = H p
+      { k_dot5d_partial<<<nblk, kThreads, 0, s>>>(pv, w, part, n, per); ::mrhs::count_launch(); }
+      { k_dot5d_final<<<1, kThreads, 0, s>>>(part, nblk, sc + 1); ::mrhs::count_launch(); }
+      { k_cg5d_update<<<nblk, kThreads, 0, s>>>(X, r, pv, w, sc, part, n, per); ::mrhs::count_launch(); }
+      { k_dot5d_final<<<1, kThreads, 0, s>>>(part, nblk, sc + 2); ::mrhs::count_launch(); }
+      { k_cg5d_dir<<<g, kThreads, 0, s>>>(pv, r, sc, n); ::mrhs::count_launch(); }
+      { k_cg5d_roll<<<1, 1, 0, s>>>(sc); ::mrhs::count_launch(); }
+    }
+    MRHS_CUDA_TRY(cudaGetLastError());
+    it += chunk;
+    MRHS_TRY(cx.colnorms<double2>(r, rnorm_d));
+    MRHS_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), rnorm_d, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    bool finite = true;
+    for (double v : rnorm) finite = finite && std::isfinite(v);
+    if (!finite) break;
+    done = all_done();
+  }
+  // true residual with the FP64 operator
+  MRHS_TRY(cx.apply(MRHS_PREC_FP64, X, w));
+  { k_sub<double2><<<g, kThreads, 0, s>>>(w, B, w, n); ::mrhs::count_launch(); }
+  MRHS_TRY(cx.colnorms<double2>(w, rnorm_d));
+  MRHS_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), rnorm_d, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  bool finite = true;
+  for (double v : rnorm) finite = finite && std::isfinite(v);
+  const int status = !finite ? MRHS_ERR_NONFINITE : (all_done() ? MRHS_OK : MRHS_ERR_NOT_CONVERGED);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->iters = it;
+    info->cycles = 1;
+    info->nrhs = R;
+    for (int i = 0; i < MRHS_NUM_PREC; ++i) info->applies[i] = cx.applies[i];
+    for (int j = 0; j < R; ++j) info->resid[j] = bnorm[j] > 0 ? rnorm[j] / bnorm[j] : 0.0;
+    info->krylov_prec = prec;
+    info->precond_prec = -1;
+    info->ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (status != MRHS_OK)
+    set_error(status == MRHS_ERR_NONFINITE ? "non-finite value in CG" : "not converged");
+  return status;
 }
 
 }  // namespace mrhs
