@@ -656,7 +656,7 @@ def main():
         X, info = op.solve(B, **params)
     # ---------------- timed region: K complete solves
     op.kernel_timing(True)
-    launches0 = mrhs.launch_count()
+    launches0 = mrhs.launch_count()      # library kernels before the timed region
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     with ClockSampler(local) as clk:
@@ -773,7 +773,8 @@ def main():
                          "cycle_iters": inf["cycle_iters"], "cycle_resid": inf["cycle_resid"],
                          "cycle_flag": inf["cycle_flag"],
                          "max_true_resid": resid, "lambda_max_est": lam, "setup_s": setup_s},
-               "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
+               "roofline": roof, "gpu_launches": launches, "launches_before_timed": launches0,
+               "clocks": clk.summary(),
                "kernel_time_ms": {p: {"launches": n, "ms": t} for p, (n, t) in kt.items()}}
         out.update(extras)
         print(json.dumps(out), flush=True)
