@@ -85,6 +85,9 @@ def parse():
                          "the twelve config-4 problems, or twelve 4^4 problems")
     ap.add_argument("--cg5d", action="store_true",
                     help="one CG on the enlarged 5D system (Sec. 2.2) against FP64 block CG")
+    ap.add_argument("--coarsen", default=None, metavar="LF,BLOCK,NBF,NBASIS",
+                    help="time coarsening an 81-point fine operator, e.g. 8,2,12,24: fine "
+                         "lattice 8^4, 2^4 blocks, 12 fine components, 24 basis vectors")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-shape autotuner (run before the timed region)")
     return ap.parse_args()
@@ -588,6 +591,50 @@ def run_cg5d(a, w, shift):
     print(json.dumps(out), flush=True)
 
 
+def run_coarsen(a):
+    """Coarse operator of a synthetic 81-point fine operator on a random
+    block-orthonormal basis (momentum-phase method, 81 multi-RHS FP64 fine
+    applications): K coarsenings, CUDA events."""
+    import torch
+    import paper_2409_03904_b300 as mrhs
+    import synth.device as sdev
+    from synth import stencil
+    lf, blk, nbf, nbasis = (int(v) for v in a.coarsen.split(","))
+    Lf, block = (lf,) * 4, (blk,) * 4
+    Lc = tuple(l // b for l, b in zip(Lf, block))
+    disp, _ = stencil(81)
+    dev = torch.device("cuda", 0)
+    A = sdev.coarse_op(Lf, nbf, 81, 2409, 6.0, device=dev)
+    fine = mrhs.CoarseOp(A, Lf, disp, ("fp64",))
+    del A
+    Vc, vb = int(np.prod(Lc)), blk ** 4 * nbf
+    g = torch.Generator(device=dev).manual_seed(2410)
+    basis = torch.linalg.qr(torch.randn((Vc, vb, nbasis), dtype=torch.complex128, device=dev,
+                                        generator=g))[0].contiguous()
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        fine.coarsen(block, basis, disp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        Ac = fine.coarsen(block, basis, disp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    Vf = int(np.prod(Lf))
+    fine_flops = 81 * 8.0 * nbf ** 2 * nbasis * 81 * Vf          # 81 fine applications
+    proj_flops = 81 * 8.0 * vb * nbasis * nbasis * Vc            # 81 block projections
+    out = {"metric": "coarsening time (81 stencil points)", "value": ms, "unit": "ms",
+           "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"fine {Lf} x {nbf}, 81-point; blocks {block}; coarse {Lc} x {nbasis}"},
+           "fine_apply_tflops": fine_flops / (ms * 1e-3) / 1e12,
+           "flops_fine": fine_flops, "flops_project": proj_flops}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     from synth import WORKLOADS, load_shift
@@ -605,6 +652,8 @@ def main():
         return run_batch(a)
     if a.cg5d:
         return run_cg5d(a, w, shift)
+    if a.coarsen:
+        return run_coarsen(a)
 
     import torch
     import torch.distributed as dist

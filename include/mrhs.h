@@ -200,6 +200,23 @@ int block_project(const void* basis, const void* F, void* C, int64_t n_blocks, i
 int block_promote(const void* basis, const void* C, void* F, int64_t n_blocks, int32_t v_block,
                   int32_t n_basis, int32_t nrhs, int32_t dtype, void* stream);
 
+/* Coarse operator of a fine one on a blocked basis (Sec. 3.4, "Coarse
+ * operator"): A_p(b)[j][k] = <phi_j^b | M | phi_k^(b + delta_p)> for the npts
+ * coarse displacements disp (host int8 [npts][4] in {-1,0,1}, distinct; they
+ * must cover every coarse coupling of M, which holds for the full 81-point
+ * set when M's own stencil lies inside {-1,0,1}^4).  fine: an operator with
+ * FP64 built (lattice L_f, nb_f components); block[4] divides L_f, and every
+ * coarse extent L_f / block is >= 3.  basis: device complex128
+ * [V_c][v_block][n_basis], v_block = prod(block) * nb_f, row s = i * nb_f + a
+ * for fine component a of the site at position i inside the block (first
+ * direction fastest); 1 <= n_basis <= min(64, v_block).  A: device complex128
+ * [V_c][npts][n_basis][n_basis], the layout mrhs_op_create takes.  Method
+ * (momentum phases): one multi-RHS FP64 application of M per displacement to
+ * the phased basis, block projections, and the inverse of the npts x npts
+ * phase matrix.  Uses workspace of `fine`; asynchronous on `stream`. */
+int coarsen_op(mrhs_op fine, const int32_t block[4], const void* basis, int32_t nbasis,
+               const int8_t* disp, int32_t npts, void* A, void* stream);
+
 /* Deflated Chebyshev coarse solve Q^{Cheby+defl} (Sec. 2.3, the "two step
  * deflated/Chebyshev coarse solve"):
  *   X = U Lambda^-1 U^dagger B + p(H) (B - U U^dagger B),

@@ -150,6 +150,26 @@ class CoarseOp:
                                           int(X.shape[2]), _lib.stream_ptr()))
         return P
 
+    def coarsen(self, block, basis, disp):
+        """Coarse operator of this (fine) operator on a blocked basis (Sec.
+        3.4): A[b][p][j][k] = <phi_j^b | M | phi_k^(b + disp[p])> by the
+        momentum-phase method.  block: 4 ints dividing L; basis: complex128
+        [V_c][prod(block) nb][n_basis] (device); disp: [npts][4] in {-1,0,1}.
+        Returns complex128 [V_c][npts][n_basis][n_basis] (device), ready for
+        CoarseOp(A, L_c, disp)."""
+        block = (ctypes.c_int32 * 4)(*[int(v) for v in block])
+        disp = np.ascontiguousarray(np.asarray(disp, dtype=np.int8).reshape(-1, 4))
+        Vc, vb, nbasis = (int(v) for v in basis.shape)
+        bvol = int(np.prod(list(block)))
+        if Vc * bvol != self.V or vb != bvol * self.nb:
+            raise ValueError("basis must be [V / prod(block)][prod(block) * nb][n_basis]")
+        A = torch.empty((Vc, disp.shape[0], nbasis, nbasis), dtype=torch.complex128,
+                        device=basis.device)
+        _lib.check(_lib.lib().coarsen_op(self._h, block, _lib.dev_ptr(basis, torch.complex128, "basis"),
+                                         nbasis, disp.ctypes.data_as(ctypes.c_void_p), disp.shape[0],
+                                         _lib.dev_ptr(A), _lib.stream_ptr()))
+        return A
+
     def defl_cheby(self, U, lam, B, lo, hi, order, prec="fp64", out=None):
         """Deflated Chebyshev coarse solve (Sec. 2.3): U Lambda^-1 U^dagger B
         + p(H)(B - U U^dagger B), p the degree-`order` Chebyshev

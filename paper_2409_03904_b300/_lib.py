@@ -85,6 +85,7 @@ SIGNATURES = {
     "cheby_apply": [P, I32, D, D, I32, P, P, I32, P],
     "coarse_solve_defl_cheby": [P, I32, P, P, I32, D, D, I32, P, P, I32, P],
     "block_project": [P, P, P, I64, I32, I32, I32, I32, P],
+    "coarsen_op": [P, P, P, I32, P, I32, P, P],
     "block_promote": [P, P, P, I64, I32, I32, I32, I32, P],
     "block_cg_solve": [P, P, P, I32, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), P],
     "mrhs_solve_params_default": [ctypes.POINTER(SolveParams), I32],

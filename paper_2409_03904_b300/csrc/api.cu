@@ -281,6 +281,7 @@ int mrhs_op_destroy(mrhs_op op) {
   }
   op->ws_xpack.release();
   op->ws_defl.release();
+  op->ws_coarsen.release();
   op->ws_cheb.release();
   op->ws_small.release();
   op->ws_solve.release();
@@ -419,6 +420,41 @@ int block_project(const void* basis, const void* F, void* C, int64_t n_blocks, i
 int block_promote(const void* basis, const void* C, void* F, int64_t n_blocks, int32_t v_block,
                   int32_t n_basis, int32_t nrhs, int32_t dtype, void* stream) {
   return blocking_common(false, basis, C, F, n_blocks, v_block, n_basis, nrhs, dtype, stream);
+}
+
+int coarsen_op(mrhs_op fine, const int32_t block[4], const void* basis, int32_t nbasis,
+               const int8_t* disp, int32_t npts, void* A, void* stream) {
+  MRHS_TRY(check_op(fine));
+  MRHS_TRY(check_prec(fine, MRHS_PREC_FP64));
+  if (!block || !disp) return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: null argument");
+  MRHS_TRY(check_vec(basis, "basis"));
+  MRHS_TRY(check_vec(A, "A"));
+  int64_t Vc = 1, bvol = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (block[mu] < 1 || fine->L[mu] % block[mu] != 0)
+      return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: block must divide the fine lattice");
+    if (fine->L[mu] / block[mu] < 3)
+      return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: every coarse extent must be >= 3");
+    Vc *= fine->L[mu] / block[mu];
+    bvol *= block[mu];
+  }
+  if (nbasis < 1 || nbasis > MRHS_MAX_RHS || nbasis > bvol * fine->nb)
+    return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: 1 <= n_basis <= min(64, v_block)");
+  if (npts < 1 || npts > MRHS_MAX_PTS) return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: npts 1..81");
+  for (int p = 0; p < npts; ++p)
+    for (int mu = 0; mu < 4; ++mu)
+      if (disp[4 * p + mu] < -1 || disp[4 * p + mu] > 1)
+        return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: displacements must be in {-1,0,1}");
+  const size_t ab = 16 * (size_t)Vc * npts * nbasis * nbasis;
+  const size_t bb = 16 * (size_t)Vc * bvol * fine->nb * nbasis;
+  const char* a = (const char*)A;
+  const char* b = (const char*)basis;
+  if (a < b + bb && b < a + ab) return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: A overlaps basis");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != fine->device) return fail(MRHS_ERR_INVALID_ARG, "operator lives on another device");
+  return coarsen(fine, block, basis, nbasis, reinterpret_cast<const int8_t(*)[4]>(disp), npts, A,
+                 (cudaStream_t)stream);
 }
 
 int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const double* lambda,

@@ -99,6 +99,7 @@ struct mrhs_op_s {
   mrhs::TcImage tc_dag[3];      // the same for the daggered stencil (on demand)
   mrhs::Workspace ws_xpack;     // packed input vectors for the tensor path
   mrhs::Workspace ws_defl;      // deflated Chebyshev solve: Grams, B_perp, p(H) B_perp
+  mrhs::Workspace ws_coarsen;   // coarsening: phased basis, M phi, blocked copy, T
   mrhs::Workspace ws_cheb;      // Chebyshev recurrence vectors
   mrhs::Workspace ws_small;     // column scales etc.
   mrhs::Workspace ws_solve;     // block CG vectors and state
@@ -161,6 +162,8 @@ int defl_cheby(mrhs_op_s* op, int prec, const void* U, const double* lam_host, i
                double lo, double hi, int order, const void* B, void* X, int R, cudaStream_t s);
 int blocking(bool project, const void* basis, const void* in, void* out, int64_t nblk, int vb,
              int nbasis, int R, int dtype, cudaStream_t s);
+int coarsen(mrhs_op_s* op, const int32_t* block, const void* basis, int nbasis,
+            const int8_t (*disp)[4], int npts, void* A_out, cudaStream_t s);
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam);
 int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* const* X,
                 const int32_t* nrhs, const mrhs_solve_params& p, mrhs_solve_info* infos,
