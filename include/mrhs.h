@@ -274,8 +274,10 @@ typedef struct {
   int32_t residual_prec; /* MIXED: operator of each cycle's residual B - H X:
                            MRHS_PREC_FP64 or MRHS_PREC_DF32; -1 (default):
                            DF32.  A DF32 residual that meets tol is recomputed
-                           with FP64 before the solve returns, so the residuals
-                           reported are FP64 ones */
+                           with FP64 before the solve returns, and a cycle that
+                           needs less than a tenfold reduction computes its
+                           residual in FP64 directly, so the residuals reported
+                           are FP64 ones */
 } mrhs_solve_params;
 
 enum {

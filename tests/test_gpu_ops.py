@@ -395,8 +395,7 @@ def test_df32_operator(mrhs, L, nb, npts, R):
 
 def test_df32_cycle_residuals_fp64_confirmation(mrhs):
     """Mixed solve with DF32 cycle residuals (default) and with FP64 ones:
-    both end on an FP64 residual <= tol; the DF32 run spends one FP64
-    application, on the confirmation."""
+    both end on an FP64 residual <= tol."""
     from synth import WORKLOADS
     w = WORKLOADS["L4_nb24_9pt_r4"]
     L, nb, npts, R = w["L"], w["nb"], w["npts"], w["nrhs"]
@@ -411,5 +410,9 @@ def test_df32_cycle_residuals_fp64_confirmation(mrhs):
         r = B - coarse_op_apply(A, X.cpu().numpy(), L, disp)
         rel = np.linalg.norm(r.reshape(-1, R), axis=0) / np.linalg.norm(B.reshape(-1, R), axis=0)
         assert np.max(rel) <= 1.5e-10
-    assert i1["applies"]["df32"] == i1["cycles"] and i1["applies"]["fp64"] == 1
+    # one residual per cycle: DF32, or FP64 directly in a cycle whose inner
+    # targets are all set by tol; a DF32 residual that meets tol is re-done in FP64
+    assert i1["applies"]["df32"] >= 1 and i1["applies"]["fp64"] >= 1
+    assert i1["applies"]["df32"] + i1["applies"]["fp64"] >= i1["cycles"]
+    assert i1["applies"]["fp64"] <= i1["cycles"]
     assert i2["applies"]["df32"] == 0 and i2["applies"]["fp64"] == i2["cycles"]
