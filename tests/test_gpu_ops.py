@@ -38,7 +38,7 @@ def dev(a):
 
 SHAPES = [((4, 3, 2, 3), 16, 81, 8), ((2, 2, 2, 2), 3, 9, 1), ((3, 3, 3, 3), 24, 9, 4),
           ((1, 1, 1, 1), 8, 81, 2), ((3, 2, 2, 2), 48, 81, 32), ((2, 3, 2, 2), 32, 9, 64),
-          ((2, 2, 3, 2), 5, 81, 13)]
+          ((2, 2, 3, 2), 5, 81, 13), ((2, 2, 2, 3), 64, 81, 64)]
 
 
 @pytest.mark.parametrize("L,nb,npts,R", SHAPES)
@@ -63,7 +63,8 @@ def test_fp64_fp32_op_and_dag(mrhs, L, nb, npts, R):
 
 TC_SHAPES = [((4, 3, 2, 3), 16, 81, 8), ((2, 2, 2, 2), 3, 9, 1), ((3, 3, 3, 3), 24, 9, 4),
              ((3, 2, 2, 2), 48, 81, 32), ((2, 3, 2, 2), 32, 9, 64), ((2, 2, 3, 2), 5, 81, 13),
-             ((3, 3, 2, 2), 48, 81, 12), ((2, 2, 2, 2), 64, 9, 16), ((5, 1, 1, 1), 8, 9, 3)]
+             ((3, 3, 2, 2), 48, 81, 12), ((2, 2, 2, 2), 64, 9, 16), ((5, 1, 1, 1), 8, 9, 3),
+             ((2, 2, 2, 3), 64, 81, 32), ((3, 2, 2, 2), 64, 81, 64), ((2, 2, 2, 2), 63, 9, 31)]
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp16", "fp16x", "tc32"])
@@ -377,7 +378,8 @@ def test_graph_replay_matches_eager(mrhs):
 
 
 @pytest.mark.parametrize("L,nb,npts,R", [((3, 2, 2, 3), 48, 81, 32), ((4, 3, 2, 3), 16, 9, 8),
-                                         ((2, 2, 2, 2), 5, 81, 3), ((3, 3, 2, 2), 24, 81, 64)])
+                                         ((2, 2, 2, 2), 5, 81, 3), ((3, 3, 2, 2), 24, 81, 64),
+                                         ((2, 2, 2, 3), 64, 81, 64)])
 def test_df32_operator(mrhs, L, nb, npts, R):
     """Double-float operator against the oracle's FP64 operator and adjoint:
     relative error per RHS well below 1e-11 (2^-44 arithmetic)."""
