@@ -35,6 +35,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+WIDE = ("fp64", "df32", "oz")      # precisions whose vectors are complex128
 METRIC = ("coarse-op TFLOP/s at Nrhs=32; block-CG time-to-1e-8 per RHS, mixed vs FP64")
 DEFAULT_WORKLOAD = "L12_nb48_81pt_r32"
 
@@ -48,6 +49,9 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precond", default="fp16x", choices=["fp16x", "fp16", "bf16", "fp32", "tc32"])
     ap.add_argument("--krylov", default="tc32", choices=["tc32", "fp32"])
+    ap.add_argument("--residual", default="oz", choices=["oz", "df32", "fp64"],
+                    help="operator of the refinement cycles' residuals (the one that meets "
+                         "tol is always recomputed in FP64)")
     ap.add_argument("--cheb-order", type=int, default=8)
     ap.add_argument("--cheb-ratio", type=float, default=400.0, help="hi / lo")
     ap.add_argument("--inner-tol", type=float, default=1e-3)
@@ -61,7 +65,7 @@ def parse():
                     help="skip the standalone operator, FP64 and e2e measurements")
     ap.add_argument("--cpu-sites", type=int, default=96, help="oracle sample size (sites)")
     ap.add_argument("--op", default=None,
-                    choices=["fp64", "df32", "fp32", "bf16", "fp16", "fp16x", "tc32"],
+                    choices=["fp64", "df32", "oz", "fp32", "bf16", "fp16", "fp16x", "tc32"],
                     help="time the coarse operator alone in this precision")
     ap.add_argument("--lattice", default=None, help="a,b,c,d: override the workload's lattice "
                     "(operator mode; same per-site work)")
@@ -163,9 +167,11 @@ def op_bytes(w, R, prec):
     """Algorithmic bytes of one application: coefficients once, input and
     output vectors once (neighbour re-reads not counted)."""
     V = int(np.prod(w["L"]))
-    coef = {"fp64": 16, "df32": 16, "fp32": 8, "bf16": 4, "fp16": 4, "fp16x": 4, "tc32": 8}[prec]
-    vec = 16 if prec in ("fp64", "df32") else 8
-    extra = 8 * V if prec not in ("fp64", "df32", "fp32") else 0   # site scale + diagonal
+    coef = {"fp64": 16, "df32": 16, "fp32": 8, "bf16": 4, "fp16": 4, "fp16x": 4, "tc32": 8,
+            "oz": 28}[prec]
+    vec = 16 if prec in WIDE else 8
+    # site scale + diagonal (float pair; a double pair for the digit image)
+    extra = {"fp64": 0, "df32": 0, "fp32": 0, "oz": 16 * V}.get(prec, 8 * V)
     return w["npts"] * V * w["nb"] ** 2 * coef + extra + 2 * V * w["nb"] * R * vec
 
 
@@ -291,12 +297,12 @@ def run_op(a, w, shift):
     op = mrhs.CoarseOp(A, w["L"], disp, (prec,))
     del A
     torch.cuda.empty_cache()
-    vdt = torch.complex128 if prec in ("fp64", "df32") else torch.complex64
+    vdt = torch.complex128 if prec in WIDE else torch.complex64
     X = sdev.vectors(w["L"], nb, R, w["seed"], device=dev).to(vdt)
     Y = torch.empty_like(X)
     stream = torch.cuda.current_stream()
     tuned = None
-    if not a.no_autotune and prec not in ("fp64", "fp32", "df32"):
+    if not a.no_autotune and prec not in ("fp64", "fp32", "df32", "oz"):
         try:
             tuned = mrhs.autotune(op, prec, R, reps=3)
         except mrhs.MrhsError:
@@ -375,7 +381,7 @@ def run_defl(a, w, shift):
     op = mrhs.CoarseOp(A, w["L"], disp, tuple(dict.fromkeys(("fp64", prec))))
     del A
     torch.cuda.empty_cache()
-    wide = prec in ("fp64", "df32")
+    wide = prec in WIDE
     vdt = torch.complex128 if wide else torch.complex64
     B = sdev.vectors(w["L"], nb, R, w["seed"], device=dev)
     lam_max = op.lambda_max("fp64", 60)
@@ -677,7 +683,11 @@ def main():
 
     t0 = time.time()
     A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
-    precs = tuple(dict.fromkeys(("fp64", "df32", "fp32", "bf16", "fp16", a.precond, a.krylov)))
+    # the solve's operator holds the precisions the solve uses (at 12^4, nb 48:
+    # FP64 62 GB, digit image 108 GB, TC32 31 GB, FP16 16 GB); the others are
+    # timed afterwards on a second operator
+    precs = tuple(dict.fromkeys(("fp64", "df32", a.residual, a.precond, a.krylov)))
+    other_precs = tuple(p for p in ("fp32", "bf16", "fp16") if p not in precs)
     op = mrhs.CoarseOp(A, w["L"], disp, precs)
     del A
     torch.cuda.empty_cache()
@@ -689,7 +699,7 @@ def main():
                   krylov_prec=a.krylov,
                   cheb_order=a.cheb_order, cheb_hi=hi, cheb_lo=hi / a.cheb_ratio,
                   inner_tol=a.inner_tol, maxiter=20000, max_cycles=20,
-                  check_every=a.check_every)
+                  check_every=a.check_every, residual_prec=a.residual)
 
     stream = torch.cuda.current_stream()
     # launch shapes of the two tensor-core forms, tuned once for this shape
@@ -747,20 +757,23 @@ def main():
     if not a.no_extras and rank == 0:
         # standalone coarse-operator throughput at this RHS count, per precision
         cop = {}
-        for p in precs:
-            Xp = B if p in ("fp64", "df32") else B.to(torch.complex64)
-            reps = 2 if p in ("fp64", "df32", "fp32") else 10
-            op.apply(Xp, p)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                op.apply(Xp, p)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / reps
-            cop[p] = {"ms": t, "tflops": op_flops(w, R) / (t * 1e-3) / 1e12,
-                      "gbs": op_bytes(w, R, p) / (t * 1e-3) / 1e9}
+
+        def time_ops(o, ps):
+            for p in ps:
+                Xp = B if p in WIDE else B.to(torch.complex64)
+                reps = 2 if p in ("fp64", "df32", "fp32") else 10
+                o.apply(Xp, p)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    o.apply(Xp, p)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / reps
+                cop[p] = {"ms": t, "tflops": op_flops(w, R) / (t * 1e-3) / 1e12,
+                          "gbs": op_bytes(w, R, p) / (t * 1e-3) / 1e9}
+        time_ops(op, precs)
         extras["coarse_op"] = cop
         # plain FP64 block CG: time per iteration, extrapolated when not run to the end
         if a.fp64_full:
@@ -802,19 +815,29 @@ def main():
                                   "sample": meta["sample"] + ("" if n_it else
                                                               "; FP64 iteration count unknown"),
                                   "full_apply_ms": meta["full_apply_ms"]}
+        # the remaining precisions' operator throughput, on an operator of their own
+        if other_precs:
+            del op
+            torch.cuda.empty_cache()
+            A2 = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
+            op2 = mrhs.CoarseOp(A2, w["L"], disp, other_precs)
+            del A2
+            torch.cuda.empty_cache()
+            time_ops(op2, other_precs)
+            del op2
 
     if rank == 0:
         inf = infos[-1]
         out = {"metric": METRIC, "value": value, "unit": "ms/RHS", "n_gpus": world,
                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step,
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-               "dtype": f"f64+df32+{a.krylov}+{a.precond}", "data": "synthetic",
+               "dtype": f"f64+{a.residual}+{a.krylov}+{a.precond}", "data": "synthetic",
                "config": {"workload": w["name"], "L": list(w["L"]), "nb": nb, "npts": w["npts"],
                           "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
                           "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
                                      f"[{hi / a.cheb_ratio:.4g}, {hi:.4g}]",
                           "inner_tol": a.inner_tol, "parallelism": f"replicas x{world}",
-                          "residuals": "df32 per cycle, fp64 for the one that meets tol",
+                          "residuals": f"{a.residual} per cycle, fp64 for the one that meets tol",
                           "launch_shapes": tuned,
                           "l2": "inputs larger than L2 (coefficients "
                                 f"{op_bytes(w, R, a.precond) / 1e9:.1f} GB per application)"},

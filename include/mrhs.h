@@ -58,13 +58,25 @@ enum {
   MRHS_PREC_TC32 = 5, /* coefficients and input in two fp16 terms, lo x lo
                           dropped: FP32-class accuracy on the tensor cores,
                           8 bytes per complex coefficient; nrhs <= 32 */
-  MRHS_PREC_DF32 = 6  /* the FP64 coefficients and complex128 vectors in
+  MRHS_PREC_DF32 = 6, /* the FP64 coefficients and complex128 vectors in
                           double-float arithmetic (FP32 pairs, error-free
                           products and sums) on the FP32 pipes: about 2^-44
                           relative; built whenever FP64 is */
+  MRHS_PREC_OZ = 7    /* FP64-class operator on the tensor cores by digit
+                          slicing (Ozaki scheme): coefficients (per site) and
+                          input (per column) as seven signed 6-bit fixed-point
+                          digits held exactly in fp16, digit products with
+                          s + t <= 8 summed exactly in FP32 tensor memory,
+                          recombined in int64 and FP64; vectors complex128;
+                          about 2^-42 of the site and column scales per term;
+                          nrhs <= 32; 28 bytes per complex coefficient;
+                          implies FP64 (and DF32) */
 };
-#define MRHS_NUM_PREC 7
+#define MRHS_NUM_PREC 8
 #define MRHS_PREC_IS_TC(p) ((p) >= MRHS_PREC_BF16 && (p) <= MRHS_PREC_TC32)
+/* precisions whose vectors are complex128 (the others: complex64) */
+#define MRHS_PREC_IS_WIDE(p) \
+  ((p) == MRHS_PREC_FP64 || (p) == MRHS_PREC_DF32 || (p) == MRHS_PREC_OZ)
 #define MRHS_PREC_BIT(p) (1u << (p))
 
 /* The four tensor-core forms share one design (op_tc.cu): per site, the
@@ -82,8 +94,8 @@ enum { MRHS_C128 = 0, MRHS_C64 = 1 };
 
 typedef struct mrhs_op_s* mrhs_op;
 
-/* Create a coarse operator (Sec. 2.6: "the coarse matrix coefficients are
- * stored entirely internal to this object").
+/* Create a coarse operator (Sec. 2.6: the object holds the coarse matrix
+ * coefficients itself).
  *   L      host int32[4], each >= 1
  *   nb     basis size per site, 1..64
  *   npts   stencil points, 1..81; disp host int8[npts][4] in {-1,0,1}, disp[0]=0
@@ -91,7 +103,9 @@ typedef struct mrhs_op_s* mrhs_op;
  *   prec_mask  OR of MRHS_PREC_BIT(p): the precisions to build.  The operator
  *          owns a packed copy of A for each (complex128, complex64, or
  *          16-bit codes with a float scale and diagonal per site; FP16 and
- *          FP16X share one image); A may be freed after the call returns.
+ *          FP16X share one image; OZ keeps seven fp16 digit tiles per
+ *          coefficient tile, 28 bytes per complex coefficient, with double
+ *          scales and diagonals); A may be freed after the call returns.
  * On success *out holds the handle.  Synchronises `stream`. */
 int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts,
                    const int8_t* disp, const void* A, uint32_t prec_mask, void* stream);
@@ -102,7 +116,8 @@ int mrhs_op_destroy(mrhs_op op);
 /* Y = H X,  Y(x) = sum_p A_p(x) X(x + delta_p)   (Sec. 2.6, "Applying the
  * coarse operator", the per-stencil-point batched GEMM summed over p).
  *   prec   MRHS_PREC_*; must be in the operator's prec_mask
- *   X, Y   device [V][nb][nrhs]: complex128 for FP64, complex64 otherwise;
+ *   X, Y   device [V][nb][nrhs]: complex128 for FP64, DF32 and OZ (see
+ *          MRHS_PREC_IS_WIDE), complex64 otherwise;
  *          X and Y must not overlap
  *   nrhs   1..MRHS_MAX_RHS */
 int coarse_op_apply(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
@@ -110,8 +125,9 @@ int coarse_op_apply(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nr
 
 /* Y = H^dagger X,  Y(x) = sum_p A_p(x - delta_p)^dagger X(x - delta_p): the
  * adjoint of the operator above (the reversed, daggered stencil).  Same
- * arguments.  For the BF16/FP16 precisions the first call builds a packed
- * image of the daggered coefficients inside the operator. */
+ * arguments.  For the tensor-core precisions (BF16 ... TC32, OZ) the first
+ * call builds a packed image of the daggered coefficients inside the
+ * operator. */
 int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_t nrhs,
                         void* stream);
 
@@ -237,8 +253,8 @@ int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const doubl
                             void* X, int32_t nrhs, void* stream);
 
 /* Largest-eigenvalue estimate of a Hermitian positive operator by the power
- * method (Sec. 2.3: the upper end of the Chebyshev interval is obtained
- * "with a cheap application of the power method"): Rayleigh quotient after
+ * method (Sec. 2.3 takes the upper end of the Chebyshev interval from a
+ * few power-method steps): Rayleigh quotient after
  * `iters` applications in precision `prec` to one deterministic start vector.
  * The estimate lies below the true maximum; it is cached on the operator and
  * block_cg_solve uses 1.08 x the cached value when cheb_hi <= 0.  Uses
@@ -272,12 +288,13 @@ typedef struct {
                            chunk of check_every block-CG iterations is captured
                            once as a CUDA graph and replayed */
   int32_t residual_prec; /* MIXED: operator of each cycle's residual B - H X:
-                           MRHS_PREC_FP64 or MRHS_PREC_DF32; -1 (default):
-                           DF32.  A DF32 residual that meets tol is recomputed
-                           with FP64 before the solve returns, and a cycle that
-                           needs less than a tenfold reduction computes its
-                           residual in FP64 directly, so the residuals reported
-                           are FP64 ones */
+                           MRHS_PREC_FP64, MRHS_PREC_DF32 or MRHS_PREC_OZ;
+                           -1 (default): OZ if built and nrhs <= 32, else
+                           DF32.  A non-FP64 residual that meets tol is
+                           recomputed with FP64 before the solve returns, and
+                           a cycle that needs less than a tenfold reduction
+                           computes its residual in FP64 directly, so the
+                           residuals reported are FP64 ones */
 } mrhs_solve_params;
 
 enum {
@@ -287,7 +304,7 @@ enum {
                            CG on complex64 vectors with the TC32 (or FP32)
                            operator and the low-precision Chebyshev
                            preconditioner */
-  MRHS_SOLVE_CG5D = 2   /* Sec. 2.2's "enlarged five dimensional system": plain
+  MRHS_SOLVE_CG5D = 2   /* Sec. 2.2's single five-dimensional system: plain
                            CG on the whole block, alpha and beta from inner
                            products summed over all right-hand sides, no
                            preconditioner; operator krylov_prec = FP64 (default,
@@ -356,7 +373,8 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode);
 
 /* Returns and clears the sticky error word of the tensor-core kernels: 0 if
  * none, else a bit set by a bounded wait that expired inside a kernel (1 the
- * TMA producer, 2 the MMA issuer, 4 the epilogue); such a kernel records the
+ * TMA producer, 2 the MMA issuer, 4 the epilogue of the BF16 ... TC32 kernel;
+ * 8, 16, 32 the same roles in the OZ kernel); such a kernel records the
  * bit, drains its own copies, frees its tensor memory and returns, leaving
  * its output undefined.  Synchronises the current device. */
 int32_t mrhs_device_error(void);

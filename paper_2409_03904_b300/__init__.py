@@ -41,8 +41,9 @@ class CoarseOp:
 
     A: CUDA complex128 tensor [V][npts][nb][nb]; L: 4 lattice extents; disp:
     int8 [npts][4] displacements (disp[0] = 0); precisions: any of "fp64",
-    "fp32", "bf16", "fp16", "fp16x", "tc32", "df32" ("df32" comes with
-    "fp64" and implies it).  The operator keeps its own packed copies.
+    "fp32", "bf16", "fp16", "fp16x", "tc32", "df32", "oz" ("df32" comes with
+    "fp64" and implies it; "oz", the digit-sliced tensor-core form, implies
+    both).  The operator keeps its own packed copies.
     """
 
     def __init__(self, A, L, disp, precisions=("fp64", "fp32")):
@@ -56,6 +57,8 @@ class CoarseOp:
         self.nb = int(A.shape[2])
         self.N = self.V * self.nb
         precisions = tuple(precisions)
+        if "oz" in precisions and "fp64" not in precisions:
+            precisions = ("fp64",) + precisions
         if "fp64" in precisions and "df32" not in precisions:
             precisions += ("df32",)
         if "df32" in precisions and "fp64" not in precisions:

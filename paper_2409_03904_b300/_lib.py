@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(HERE, "libmrhs.so")
 MRHS_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NOT_CONVERGED", -4: "BREAKDOWN", -5: "NONFINITE",
           -6: "UNSUPPORTED", -7: "NO_MEMORY", -8: "DEVICE"}
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "fp16x": 4, "tc32": 5, "df32": 6}
-NUM_PREC = 7
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "fp16x": 4, "tc32": 5, "df32": 6, "oz": 7}
+NUM_PREC = 8
+WIDE = ("fp64", "df32", "oz")    # precisions whose vectors are complex128
 NAMES = {v: k for k, v in PREC.items()}
 C128, C64 = 0, 1
 MAX_RHS = 64
@@ -149,4 +150,4 @@ def dev_ptr(t, dtype=None, name="tensor"):
 
 
 def vec_dtype(prec):
-    return torch.complex128 if prec in ("fp64", "df32") else torch.complex64
+    return torch.complex128 if prec in WIDE else torch.complex64

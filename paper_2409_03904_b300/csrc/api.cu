@@ -103,10 +103,21 @@ int check_prec(const mrhs_op_s* op, int prec) {
   return MRHS_OK;
 }
 
+// Operator of the refinement cycles' residuals: FP64, DF32 or (when built and
+// the shape fits) the digit-sliced tensor-core form.
+int check_residual_prec(int rp, bool oz_ok) {
+  if (rp == MRHS_PREC_FP64 || rp == MRHS_PREC_DF32) return MRHS_OK;
+  if (rp == MRHS_PREC_OZ)
+    return oz_ok ? MRHS_OK
+                 : fail(MRHS_ERR_UNSUPPORTED, "residual_prec OZ: not built or nrhs > 32");
+  return fail(MRHS_ERR_INVALID_ARG, "residual_prec must be FP64, DF32 or OZ");
+}
+
 }  // namespace
 
 int op_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
              cudaStream_t s) {
+  if (prec == MRHS_PREC_OZ) return oz_apply(op, dag, X, Y, nrhs, s);
   if (!MRHS_PREC_IS_TC(prec)) return simt_apply(op, prec, dag, X, Y, nrhs, s);
   return tc_apply(op, prec, dag, X, Y, nrhs, s);
 }
@@ -123,7 +134,7 @@ const char* mrhs_version(void) { return "mrhs 0.1 (sm_103a)"; }
 
 int32_t mrhs_device_error(void) {
   cudaDeviceSynchronize();
-  return (int32_t)tc_read_and_clear_error();
+  return (int32_t)(tc_read_and_clear_error() | oz_read_and_clear_error());
 }
 
 int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, const int8_t* disp,
@@ -133,8 +144,11 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   if (nb < 1 || nb > 64) return fail(MRHS_ERR_INVALID_ARG, "nb must be in 1..64");
   if (npts < 1 || npts > MRHS_MAX_PTS) return fail(MRHS_ERR_INVALID_ARG, "npts must be in 1..81");
   if (prec_mask == 0 || (prec_mask >> MRHS_NUM_PREC))
-    return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..6");
-  // DF32 runs on the FP64 coefficients; with them it comes for free
+    return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..7");
+  // DF32 runs on the FP64 coefficients; with them it comes for free.  The
+  // digit-sliced form keeps FP64 beside it (its adjoint image and the FP64
+  // confirmation of residuals are built from those coefficients)
+  if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_OZ)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_FP64);
   if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_DF32)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_FP64);
   if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_DF32);
   if (!aligned16(A)) return fail(MRHS_ERR_INVALID_ARG, "A not 16-byte aligned");
@@ -205,6 +219,13 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
         return bail(st);
       }
     }
+  if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_OZ)) {
+    int st = oz_build(op, false, (const double2*)A, s);
+    if (st != MRHS_OK) {
+      cudaFree(d_disp);
+      return bail(st);
+    }
+  }
   cudaError_t e = cudaStreamSynchronize(s);
   cudaFree(d_disp);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -279,7 +300,13 @@ int mrhs_op_destroy(mrhs_op op) {
     cudaFree(op->tc_dag[i].scale);
     cudaFree(op->tc_dag[i].diag);
   }
+  for (mrhs::OzImage* im : {&op->oz, &op->oz_dag}) {
+    cudaFree(im->digits);
+    cudaFree(im->scale);
+    cudaFree(im->diag);
+  }
   op->ws_xpack.release();
+  op->ws_ozpack.release();
   op->ws_defl.release();
   op->ws_coarsen.release();
   op->ws_cheb.release();
@@ -296,7 +323,7 @@ static int apply_common(mrhs_op op, int32_t prec, const void* X, void* Y, int32_
   MRHS_TRY(check_vec(X, "X"));
   MRHS_TRY(check_vec(Y, "Y"));
   if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
-  const size_t es = (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32) ? 16 : 8;
+  const size_t es = MRHS_PREC_IS_WIDE(prec) ? 16 : 8;
   const size_t bytes = es * (size_t)op->V * op->nb * nrhs;
   const char* x = (const char*)X;
   const char* y = (const char*)Y;
@@ -474,7 +501,7 @@ int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const doubl
     for (int i = 0; i < n_ev; ++i)
       if (!(lambda[i] > 0.0) || !std::isfinite(lambda[i]))
         return fail(MRHS_ERR_INVALID_ARG, "lambda must be positive and finite");
-    const size_t es = (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32) ? 16 : 8;
+    const size_t es = MRHS_PREC_IS_WIDE(prec) ? 16 : 8;
     const size_t ub = es * (size_t)op->V * op->nb * n_ev, vb = es * (size_t)op->V * op->nb * nrhs;
     const char* u = (const char*)U;
     for (const void* v : {B, (const void*)X}) {
@@ -516,9 +543,9 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
     return !MRHS_PREC_IS_TC(pr) || tc_supported(op, pr, nrhs) != 0;
   };
   if (q.mode == MRHS_SOLVE_MIXED) {
-    if (q.residual_prec < 0) q.residual_prec = MRHS_PREC_DF32;
-    if (q.residual_prec != MRHS_PREC_FP64 && q.residual_prec != MRHS_PREC_DF32)
-      return fail(MRHS_ERR_INVALID_ARG, "residual_prec must be FP64 or DF32");
+    const bool oz = built(MRHS_PREC_OZ) && oz_supported(op, nrhs);
+    if (q.residual_prec < 0) q.residual_prec = oz ? MRHS_PREC_OZ : MRHS_PREC_DF32;
+    MRHS_TRY(check_residual_prec(q.residual_prec, oz));
     if (q.krylov_prec < 0)
       q.krylov_prec = (built(MRHS_PREC_TC32) && fits(MRHS_PREC_TC32)) ? MRHS_PREC_TC32 : MRHS_PREC_FP32;
     if (q.krylov_prec != MRHS_PREC_FP32 && q.krylov_prec != MRHS_PREC_TC32)
@@ -544,7 +571,7 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
       return fail(MRHS_ERR_UNSUPPORTED, "preconditioner precision not built");
     if (pp.mode == MRHS_SOLVE_FP64 && pp.precond_prec != MRHS_PREC_FP64)
       return fail(MRHS_ERR_INVALID_ARG, "FP64 mode takes an FP64 preconditioner");
-    if (pp.mode == MRHS_SOLVE_MIXED && pp.precond_prec == MRHS_PREC_FP64)
+    if (pp.mode == MRHS_SOLVE_MIXED && MRHS_PREC_IS_WIDE(pp.precond_prec))
       return fail(MRHS_ERR_INVALID_ARG, "mixed mode takes a low-precision preconditioner");
     if (pp.cheb_order < 0) return fail(MRHS_ERR_INVALID_ARG, "cheb_order");
   }
@@ -632,9 +659,11 @@ int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* 
   // the batched path: TC32 in the Krylov loop and a tensor-core preconditioner
   // shared by all problems; otherwise each problem is solved in turn
   if (batched) {
-    if (q.residual_prec < 0) q.residual_prec = MRHS_PREC_DF32;
-    if (q.residual_prec != MRHS_PREC_FP64 && q.residual_prec != MRHS_PREC_DF32)
-      return fail(MRHS_ERR_INVALID_ARG, "residual_prec must be FP64 or DF32");
+    bool oz = true;
+    for (int i = 0; i < n; ++i)
+      oz = oz && (ops[i]->prec_mask & MRHS_PREC_BIT(MRHS_PREC_OZ)) && oz_supported(ops[i], nrhs[i]);
+    if (q.residual_prec < 0) q.residual_prec = oz ? MRHS_PREC_OZ : MRHS_PREC_DF32;
+    MRHS_TRY(check_residual_prec(q.residual_prec, oz));
     if (q.krylov_prec < 0) q.krylov_prec = MRHS_PREC_TC32;
     if (q.precond_prec < 0) {
       const int order[] = {MRHS_PREC_FP16X, MRHS_PREC_FP16, MRHS_PREC_BF16, MRHS_PREC_TC32};

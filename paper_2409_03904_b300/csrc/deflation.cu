@@ -49,7 +49,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 int defl_cheby(mrhs_op_s* op, int prec, const void* U, const double* lam_host, int n_ev,
                double lo, double hi, int order, const void* B, void* X, int R, cudaStream_t s) {
-  const bool wide = prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32;
+  const bool wide = MRHS_PREC_IS_WIDE(prec);
   const int dtype = wide ? MRHS_C128 : MRHS_C64;
   const size_t es = wide ? sizeof(double2) : sizeof(float2);
   const int64_t N = op->V * op->nb;

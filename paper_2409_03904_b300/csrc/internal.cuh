@@ -60,6 +60,13 @@ struct TcImage {             // tensor-core packed coefficients (BF16/FP16)
   size_t bytes = 0;
 };
 
+struct OzImage {             // digit-sliced coefficients (op_oz.cu)
+  void* digits = nullptr;    // [V][npts][nb16/16] slabs of 7 fp16 digit tiles
+  double* scale = nullptr;   // [V] power-of-two site scales s_x
+  double* diag = nullptr;    // [V] mean real self diagonal d_x (FP64)
+  size_t bytes = 0;
+};
+
 // CUDA-event timing of an operator's main kernel, one (start, stop) pair per
 // launch while enabled; read and cleared by mrhs_op_kernel_time.
 struct KernelTimer {
@@ -97,7 +104,10 @@ struct mrhs_op_s {
   float2* a32 = nullptr;        // [V][npts][nb][nb]
   mrhs::TcImage tc[3];          // BF16, FP16 (also FP16X), TC32: forward stencil
   mrhs::TcImage tc_dag[3];      // the same for the daggered stencil (on demand)
+  mrhs::OzImage oz;             // digit-sliced image, forward stencil
+  mrhs::OzImage oz_dag;         // the same for the daggered stencil (on demand)
   mrhs::Workspace ws_xpack;     // packed input vectors for the tensor path
+  mrhs::Workspace ws_ozpack;    // input digits of the digit-sliced operator
   mrhs::Workspace ws_defl;      // deflated Chebyshev solve: Grams, B_perp, p(H) B_perp
   mrhs::Workspace ws_coarsen;   // coarsening: phased basis, M phi, blocked copy, T
   mrhs::Workspace ws_cheb;      // Chebyshev recurrence vectors
@@ -136,6 +146,11 @@ int tune_load(const char* path);
 int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
              cudaStream_t s);
 int tc_supported(const mrhs_op_s* op, int prec, int nrhs);
+// op_oz.cu
+int oz_build(mrhs_op_s* op, bool dag, const double2* A, cudaStream_t s);
+int oz_apply(mrhs_op_s* op, bool dag, const void* X, void* Y, int nrhs, cudaStream_t s);
+int oz_supported(const mrhs_op_s* op, int nrhs);
+unsigned oz_read_and_clear_error();
 // blas.cu
 int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
          cudaStream_t s);

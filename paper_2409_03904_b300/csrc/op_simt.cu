@@ -7,7 +7,7 @@
 // B300 design: one CTA per site (grid-stride), the stencil point's nb x nb
 // block and the neighbour's nb x nrhs block staged in shared memory, so every
 // coefficient is read from HBM once per application and reused for all nrhs
-// right-hand sides (the "fictitious fifth dimension" of Sec. 2).  Thread t
+// right-hand sides (the extra dimension over right-hand sides of Sec. 2).  Thread t
 // owns one RHS column r = t % nrhs and rows a = t / nrhs + k * (T / nrhs), so
 // the neighbour value X[b][r] is loaded once per b and reused for all its
 // rows while A[a][b] is a warp-wide broadcast.  On B300 the FP64 variant is

@@ -691,10 +691,10 @@ int power_run(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
 }  // namespace
 
 // Largest-eigenvalue estimate by the power method (Sec. 2.3 obtains the
-// Chebyshev upper bound "with a cheap application of the power method"):
+// Chebyshev upper bound from a few power-method steps):
 // Rayleigh quotient of H^k v0, one right-hand side, operator in `prec`.
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
-  if (prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32)
+  if (MRHS_PREC_IS_WIDE(prec))
     return power_run<double2>(op, prec, iters, s, lam);
   return power_run<float2>(op, prec, iters, s, lam);
 }
@@ -877,7 +877,7 @@ int cheby(mrhs_op_s* op, int prec, double lo, double hi, int order, const void* 
   cx.R = R;
   cx.N = op->V * op->nb;
   const int64_t n = cx.N * R;
-  const bool wide = prec == MRHS_PREC_FP64 || prec == MRHS_PREC_DF32;
+  const bool wide = MRHS_PREC_IS_WIDE(prec);
   const size_t es = wide ? sizeof(double2) : sizeof(float2);
   MRHS_TRY(op->ws_cheb.ensure(3 * (n * es + 256)));
   char* base = (char*)op->ws_cheb.ptr;

@@ -96,6 +96,12 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// Makes this thread's ordinary shared-memory stores visible to the async
+// proxy (TMA, tcgen05.mma operand reads); a barrier must follow.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor, canonical K-major layout without swizzle:
 // 8-row x 16-byte core matrices (128 contiguous bytes); `lbo` = byte step
 // between core matrices along K, `sbo` = byte step between 8-row groups.

@@ -1,0 +1,142 @@
+"""GPU parity of the digit-sliced tensor-core operator (precision "oz") and of
+the mixed solve that takes its cycle residuals from it.
+
+Tolerance: relative L2 per right-hand side <= 1e-11 against the oracle's FP64
+operator.  Derivation: each operand is held to 2^-42 of its scale (site scale
+s_x for the coefficients, column scale sigma_r for the input), the dropped
+digit products (s + t > 8) are below 2^-42 s_x sigma_r per term as well, and
+the kept level sums are exact (or 2^-24 below their level), so an output
+element is off by a few 2^-42 s_x sigma_r times the root of the number of
+terms -- about 1e-12 of its own size for these inputs; 1e-11 leaves a margin
+of ten.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.ops import coarse_op_apply, coarse_op_apply_dag
+from synth import WORKLOADS, coarse_op, load_shift, stencil, vectors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrhs():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2409_03904_b300 as m
+    return m
+
+
+def rel_per_rhs(Y, ref):
+    Y = np.asarray(Y).reshape(-1, ref.shape[-1])
+    ref = ref.reshape(-1, ref.shape[-1])
+    num = np.linalg.norm(Y - ref, axis=0)
+    den = np.maximum(np.linalg.norm(ref, axis=0), 1e-300)
+    return np.max(num / den)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+OZ_SHAPES = [((3, 2, 2, 2), 48, 81, 32), ((4, 3, 2, 3), 16, 81, 8), ((2, 2, 2, 2), 3, 9, 1),
+             ((3, 3, 3, 3), 24, 9, 4), ((2, 2, 3, 2), 5, 81, 13), ((2, 2, 2, 3), 64, 81, 32),
+             ((2, 2, 2, 2), 63, 9, 31), ((5, 1, 1, 1), 8, 9, 3), ((1, 1, 1, 1), 8, 81, 2)]
+
+
+@pytest.mark.parametrize("L,nb,npts,R", OZ_SHAPES)
+def test_oz_operator_and_adjoint(mrhs, L, nb, npts, R):
+    """Forward and adjoint against the FP64 oracle, on the synthetic operator
+    (diagonal shift, Hermitian pairs) and on a plain Gaussian one."""
+    disp, _ = stencil(npts)
+    X = vectors(L, nb, R, 909)
+    rng = np.random.default_rng(nb * 31 + R)
+    V = int(np.prod(L))
+    gauss = rng.standard_normal((V, npts, nb, nb)) + 1j * rng.standard_normal((V, npts, nb, nb))
+    for A in (coarse_op(L, nb, npts, 7070 + nb, 12.0), gauss):
+        op = mrhs.CoarseOp(dev(A), L, disp, ("oz",))
+        Y = op.apply(dev(X), "oz").cpu().numpy()
+        assert rel_per_rhs(Y, coarse_op_apply(A, X, L, disp)) <= 1e-11
+        Yd = op.apply_dag(dev(X), "oz").cpu().numpy()
+        assert rel_per_rhs(Yd, coarse_op_apply_dag(A, X, L, disp)) <= 1e-11
+        assert mrhs.device_error() == 0
+
+
+def test_oz_columns_of_very_different_size(mrhs):
+    """Column scales are per right-hand side: a column 1e12 times smaller
+    than its neighbours keeps its own relative accuracy; a zero column gives
+    an exact zero."""
+    L, nb, npts, R = (3, 2, 2, 2), 24, 81, 6
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 515, 12.0)
+    X = vectors(L, nb, R, 516)
+    X[..., 1] *= 1e-12
+    X[..., 4] *= 1e9
+    X[..., 5] = 0
+    op = mrhs.CoarseOp(dev(A), L, disp, ("oz",))
+    Y = op.apply(dev(X), "oz").cpu().numpy()
+    ref = coarse_op_apply(A, X, L, disp)
+    assert rel_per_rhs(Y[..., :5], ref[..., :5]) <= 1e-11
+    assert np.all(Y[..., 5] == 0)
+
+
+def test_oz_nonfinite_column_stays_in_its_column(mrhs):
+    """A NaN in one input column makes that output column non-finite and
+    leaves the others exact to the tolerance."""
+    L, nb, npts, R = (2, 2, 2, 2), 16, 9, 4
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 616, 12.0)
+    X = vectors(L, nb, R, 617)
+    X[3, 2, 1] = np.nan
+    op = mrhs.CoarseOp(dev(A), L, disp, ("oz",))
+    Y = op.apply(dev(X), "oz").cpu().numpy()
+    assert not np.all(np.isfinite(Y[..., 1]))
+    keep = [0, 2, 3]
+    ref = coarse_op_apply(A, X[..., keep], L, disp)
+    assert rel_per_rhs(Y[..., keep], ref) <= 1e-11
+
+
+def test_oz_shape_limits(mrhs):
+    L, nb, npts = (2, 2, 2, 2), 8, 9
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 717, 12.0)
+    op = mrhs.CoarseOp(dev(A), L, disp, ("oz",))
+    assert "fp64" in op.precisions and "df32" in op.precisions
+    with pytest.raises(mrhs.MrhsError):
+        op.apply(dev(vectors(L, nb, 33, 718)), "oz")
+    # an operator without the digit image refuses the precision
+    plain = mrhs.CoarseOp(dev(A), L, disp, ("fp64",))
+    with pytest.raises(mrhs.MrhsError):
+        plain.apply(dev(vectors(L, nb, 4, 719)), "oz")
+
+
+def test_oz_repeat_is_bitwise(mrhs):
+    """Integer level sums and a fixed combination order: two applications
+    give the same bits."""
+    L, nb, npts, R = (3, 2, 2, 2), 48, 81, 32
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, 818, 12.0)
+    X = dev(vectors(L, nb, R, 819))
+    op = mrhs.CoarseOp(dev(A), L, disp, ("oz",))
+    Y1 = op.apply(X, "oz")
+    Y2 = op.apply(X, "oz")
+    assert torch.equal(Y1, Y2)
+
+
+def test_mixed_solve_with_oz_cycle_residuals(mrhs):
+    """With the digit image built the mixed solve takes its cycle residuals
+    from it by default and still ends on an FP64 residual <= tol."""
+    w = WORKLOADS["L4_nb24_9pt_r4"]
+    L, nb, npts, R = w["L"], w["nb"], w["npts"], w["nrhs"]
+    disp, _ = stencil(npts)
+    A = coarse_op(L, nb, npts, w["seed"], load_shift(w["name"]))
+    B = vectors(L, nb, R, w["seed"])
+    op = mrhs.CoarseOp(dev(A), L, disp, ("oz", "fp16x", "tc32"))
+    X, info = op.solve(dev(B), mode="mixed", tol=1e-10)
+    assert info["status"] == 0 and max(info["resid"]) <= 1e-10
+    r = B - coarse_op_apply(A, X.cpu().numpy(), L, disp)
+    rel = np.linalg.norm(r.reshape(-1, R), axis=0) / np.linalg.norm(B.reshape(-1, R), axis=0)
+    assert np.max(rel) <= 1.5e-10
+    assert info["applies"]["oz"] >= 1 and info["applies"]["df32"] == 0
+    assert 1 <= info["applies"]["fp64"] <= info["cycles"]
+    assert info["applies"]["oz"] + info["applies"]["fp64"] >= info["cycles"]
