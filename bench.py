@@ -331,6 +331,22 @@ def run_op(a, w, shift):
             "frac": byts / (per * 1e-3) / 1e9 / hbm, "traffic": None,
             "kernel": f"coarse operator ({prec})", "algorithmic_bytes": byts, "launch_ms": per,
             "launches": nk, "peak_kind": f"{kind} copy bandwidth"}
+    if prec == "oz":
+        # digit-sliced form: bound by the fp16 tensor pipe.  Algorithmic work =
+        # the 28 digit-pair products (s + t <= 8) of the complex operator;
+        # issued = 19 MMAs of M = 128 per point and K step (two digit levels
+        # per accumulator, 10 of the 38 half-MMAs have a zero or dropped half)
+        pairs = sum(range(1, 8))
+        alg = pairs * flops
+        issued = 19 * 2 * 128 * (2 * ((nb + 7) // 8 * 8)) * ((nb + 15) // 16 * 16) \
+            * w["npts"] * V
+        roof = {"bound": "tensor", "achieved": alg / (per * 1e-3) / 1e12, "peak": bf16_peak,
+                "unit": "TFLOP/s", "frac": alg / (per * 1e-3) / 1e12 / bf16_peak,
+                "traffic": None if over else dram_traffic(prec, w["name"]), "kernel": "coarse operator (oz, tcgen05 fp16 digit MMAs)",
+                "algorithmic_flops": alg, "issued_flops": issued,
+                "issued_tflops": issued / (per * 1e-3) / 1e12,
+                "hbm_gbs": byts / (per * 1e-3) / 1e9, "launch_ms": per, "launches": nk,
+                "peak_kind": f"{kind} dense bf16 (fp16 runs at the same rate)"}
     # end to end: host input -> device, apply, device -> host result
     Xh = X.cpu().pin_memory()
     Yh = torch.empty_like(Xh).pin_memory()
