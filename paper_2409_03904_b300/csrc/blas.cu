@@ -198,6 +198,170 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ---- complex64 blocks of at most 32 columns: one row per warp step
+// The two kernels above stage row tiles for the whole CTA and spend two
+// shared-memory loads per complex product.  For complex64 blocks of up to 32
+// columns (the mixed solve's Krylov blocks) a lane owns one output column and
+// keeps what it multiplies with in registers: the column M[:, j] for the block
+// update, its Gram column's partial sums for the Gram.  Each warp stages its
+// own kWarpRows rows of X (no block barrier) and reads them back as 16-byte
+// broadcasts, so the FP32 pipes, not shared memory, set the pace.
+constexpr int kWarpRows = 4;
+constexpr int kWarpsW = 4;            // 128 threads (153 registers: three CTAs per SM)
+
+// Y = beta Y + X M, rin, rout <= 32.  A warp reads its rows of X completely
+// before it writes the same rows of Y, so Y may alias X.  The next step's rows
+// are loaded into registers while the current ones are multiplied.
+template <int MAXI>
+__global__ void __launch_bounds__(kWarpsW * 32)
+    k_axpy_w(float2* Y, const float2* X, const double2* __restrict__ M, float beta, int64_t N,
+             int rin, int rout, int64_t ldx) {
+  __shared__ __align__(16) float2 sx[kWarpsW][kWarpRows][MAXI];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 m[MAXI];
+#pragma unroll
+  for (int i = 0; i < MAXI; ++i) {
+    m[i] = make_float2(0.f, 0.f);
+    if (i < rin && lane < rout) {
+      const double2 v = M[i * rout + lane];
+      m[i] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+  const int64_t step = (int64_t)gridDim.x * kWarpsW * kWarpRows;
+  int64_t n0 = ((int64_t)blockIdx.x * kWarpsW + warp) * kWarpRows;
+  float2 xn[kWarpRows], yn[kWarpRows];
+  auto load = [&](int64_t base) {
+#pragma unroll
+    for (int r = 0; r < kWarpRows; ++r) {
+      const int64_t n = base + r;
+      xn[r] = yn[r] = make_float2(0.f, 0.f);
+      if (n < N) {
+        if (lane < rin) xn[r] = X[n * ldx + lane];
+        if (beta != 0.f && lane < rout) yn[r] = Y[n * rout + lane];
+      }
+    }
+  };
+  load(n0);
+  for (; n0 < N; n0 += step) {
+    float2 acc[kWarpRows];
+#pragma unroll
+    for (int r = 0; r < kWarpRows; ++r) {
+      if (lane < MAXI) sx[warp][r][lane] = xn[r];
+      acc[r] = make_float2(beta * yn[r].x, beta * yn[r].y);
+    }
+    __syncwarp();
+    load(n0 + step);
+#pragma unroll
+    for (int i = 0; i < MAXI; i += 2) {
+#pragma unroll
+      for (int r = 0; r < kWarpRows; ++r) {
+        const float4 xx = *reinterpret_cast<const float4*>(&sx[warp][r][i]);
+        acc[r] = cfma(make_float2(xx.x, xx.y), m[i], acc[r]);
+        acc[r] = cfma(make_float2(xx.z, xx.w), m[i + 1], acc[r]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kWarpRows; ++r) {
+      const int64_t n = n0 + r;
+      if (lane < rout && n < N) Y[n * rout + lane] = acc[r];
+    }
+  }
+}
+
+// Partial Gram X^dagger Y of one row range per CTA, rx, ry <= 32: lane j keeps
+// column j of the partial Gram (rx complex64 sums over at most kFlushRowsW rows
+// of its warp, then added into the warp's FP64 row of shared memory; on B300
+// an FP64 add costs about as much as sixty FP32 FMAs, so the flushes are kept
+// rare); the warps' FP64 partials are summed in a fixed order at the end.  The
+// next step's rows are loaded into registers while the current ones are used.
+constexpr int kWarpsG = 4;            // 128 threads
+constexpr int kGramRows = 8;          // rows per warp step
+constexpr int kFlushRowsW = 256;
+template <int MAXI>
+__global__ void __launch_bounds__(kWarpsG * 32)
+    k_gram_w(const float2* __restrict__ X, const float2* __restrict__ Y, double2* __restrict__ part,
+             int64_t N, int rx, int ry, int64_t rows_per_block, int64_t ldx) {
+  __shared__ __align__(16) float2 sx[kWarpsG][kGramRows][MAXI];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the warps' FP64 partials [kWarpsG][MAXI][32] (dynamic: 64 KB at MAXI = 32)
+  double2 (*sg)[MAXI][32] = reinterpret_cast<double2 (*)[MAXI][32]>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = 0; i < MAXI; ++i) sg[warp][i][lane] = make_double2(0.0, 0.0);
+  float2 acc[MAXI];
+#pragma unroll
+  for (int i = 0; i < MAXI; ++i) acc[i] = make_float2(0.f, 0.f);
+  const int64_t b0 = (int64_t)blockIdx.x * rows_per_block;
+  int64_t b1 = b0 + rows_per_block;
+  if (b1 > N) b1 = N;
+  const int64_t step = kWarpsG * kGramRows;
+  float2 xn[kGramRows], yn[kGramRows];
+  auto load = [&](int64_t base) {
+#pragma unroll
+    for (int r = 0; r < kGramRows; ++r) {
+      const int64_t n = base + r;
+      xn[r] = yn[r] = make_float2(0.f, 0.f);
+      if (n < b1) {
+        if (lane < rx) xn[r] = X[n * ldx + lane];
+        if (lane < ry) yn[r] = Y[n * ry + lane];
+      }
+    }
+  };
+  int pending = 0;
+  int64_t n0 = b0 + warp * kGramRows;
+  load(n0);
+  for (; n0 < b1; n0 += step) {
+    float2 yv[kGramRows];
+#pragma unroll
+    for (int r = 0; r < kGramRows; ++r) {
+      if (lane < MAXI) sx[warp][r][lane] = xn[r];
+      yv[r] = yn[r];
+    }
+    __syncwarp();
+    load(n0 + step);
+#pragma unroll
+    for (int i = 0; i < MAXI; i += 2) {
+#pragma unroll
+      for (int r = 0; r < kGramRows; ++r) {
+        const float4 xx = *reinterpret_cast<const float4*>(&sx[warp][r][i]);
+        acc[i] = cfma_conj(make_float2(xx.x, xx.y), yv[r], acc[i]);
+        acc[i + 1] = cfma_conj(make_float2(xx.z, xx.w), yv[r], acc[i + 1]);
+      }
+    }
+    __syncwarp();
+    pending += kGramRows;
+    if (pending >= kFlushRowsW) {
+#pragma unroll
+      for (int i = 0; i < MAXI; ++i) {
+        double2 g = sg[warp][i][lane];
+        g.x += (double)acc[i].x;
+        g.y += (double)acc[i].y;
+        sg[warp][i][lane] = g;
+        acc[i] = make_float2(0.f, 0.f);
+      }
+      pending = 0;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MAXI; ++i) {
+    double2 g = sg[warp][i][lane];
+    g.x += (double)acc[i].x;
+    g.y += (double)acc[i].y;
+    sg[warp][i][lane] = g;
+  }
+  __syncthreads();
+  double2* out = part + (int64_t)blockIdx.x * rx * ry;
+  for (int e = threadIdx.x; e < rx * ry; e += blockDim.x) {
+    const int i = e / ry, j = e % ry;
+    double2 v = sg[0][i][j];
+    for (int w = 1; w < kWarpsG; ++w) {
+      v.x += sg[w][i][j].x;
+      v.y += sg[w][i][j].y;
+    }
+    out[e] = v;
+  }
+}
+
 struct WsKey {
   int dev;
   cudaStream_t s;
@@ -275,6 +439,24 @@ int launch_gram(const void* X, const void* Y, double2* part, int64_t N, int rx, 
   }
 }
 
+template <int MAXI>
+int launch_gram_w_t(const void* X, const void* Y, double2* part, int64_t N, int rx, int ry,
+                    int nblk, int64_t per, int64_t ldx, cudaStream_t s) {
+  const size_t smem = sizeof(double2) * kWarpsG * MAXI * 32;
+  MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_w<MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  { k_gram_w<MAXI><<<nblk, kWarpsG * 32, smem, s>>>((const float2*)X, (const float2*)Y, part, N,
+                                                    rx, ry, per, ldx); ::mrhs::count_launch(); }
+  return MRHS_OK;
+}
+
+int launch_gram_w(const void* X, const void* Y, double2* part, int64_t N, int rx, int ry,
+                  int nblk, int64_t per, int64_t ldx, cudaStream_t s) {
+  if (rx <= 8) return launch_gram_w_t<8>(X, Y, part, N, rx, ry, nblk, per, ldx, s);
+  if (rx <= 16) return launch_gram_w_t<16>(X, Y, part, N, rx, ry, nblk, per, ldx, s);
+  return launch_gram_w_t<32>(X, Y, part, N, rx, ry, nblk, per, ldx, s);
+}
+
 int gram_ws(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
             double2* part, cudaStream_t s) {
   return gram_ws_capped(X, Y, G, N, rx, ry, dtype, part, (int64_t)gram_blocks(N) * rx * ry, s);
@@ -297,6 +479,7 @@ int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, 
     return MRHS_OK;
   }
   if (dtype == MRHS_C128) MRHS_TRY(launch_gram<double2>(X, Y, part, N, rx, ry, nblk, per, ldx, s));
+  else if (rx <= 32 && ry <= 32) MRHS_TRY(launch_gram_w(X, Y, part, N, rx, ry, nblk, per, ldx, s));
   else MRHS_TRY(launch_gram<float2>(X, Y, part, N, rx, ry, nblk, per, ldx, s));
   MRHS_CUDA_TRY(cudaGetLastError());
   { k_gram_final<<<(unsigned)((ne * 32 + 255) / 256), 256, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
@@ -327,6 +510,20 @@ int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int r
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     { k_axpy<double2><<<(unsigned)grid, kThreads, smem, s>>>((double2*)Y, (const double2*)X, M, beta,
                                                             N, rin, rout, ldx); ::mrhs::count_launch(); }
+  } else if (rin <= 32 && rout <= 32) {
+    int64_t g = (N + kWarpsW * kWarpRows - 1) / (kWarpsW * kWarpRows);
+    const int64_t capw = (int64_t)num_sms() * 3;   // the resident CTAs
+    if (g > capw) g = capw;
+    const float b = (float)beta;
+    if (rin <= 8)
+      { k_axpy_w<8><<<(unsigned)g, kWarpsW * 32, 0, s>>>((float2*)Y, (const float2*)X, M, b, N, rin,
+                                                          rout, ldx); ::mrhs::count_launch(); }
+    else if (rin <= 16)
+      { k_axpy_w<16><<<(unsigned)g, kWarpsW * 32, 0, s>>>((float2*)Y, (const float2*)X, M, b, N, rin,
+                                                           rout, ldx); ::mrhs::count_launch(); }
+    else
+      { k_axpy_w<32><<<(unsigned)g, kWarpsW * 32, 0, s>>>((float2*)Y, (const float2*)X, M, b, N, rin,
+                                                           rout, ldx); ::mrhs::count_launch(); }
   } else {
     const size_t smem = sizeof(float2) * ((size_t)rin * rout + (size_t)kTile * rin);
     { k_axpy<float2><<<(unsigned)grid, kThreads, smem, s>>>((float2*)Y, (const float2*)X, M, beta, N,

@@ -296,7 +296,10 @@ __global__ void k_colscale(const __grid_constant__ PackBatch pb) {
 // Packed input tiles, one [xrows][K] canonical tile per site: row group 0
 // holds Re X[:,r] / sigma_r in row r, group 1 Im X[:,r] / sigma_r (groups
 // round8(R) rows apart, K = nb16 columns over b); XSPLIT: groups 0, 1 the hi
-// terms, groups 2, 3 the lo terms.
+// terms, groups 2, 3 the lo terms.  A thread takes one (site, 8-column group,
+// column r): it reads the eight complex values once and writes the 16-byte
+// unit of every row group (consecutive threads: consecutive r, so both the
+// reads and the 8-row core-matrix writes are coalesced).
 template <bool BF16, bool XSPLIT>
 __global__ void k_pack_xb(const __grid_constant__ PackBatch pb) {
   const int k = blockIdx.y;
@@ -306,42 +309,44 @@ __global__ void k_pack_xb(const __grid_constant__ PackBatch pb) {
   const float2* __restrict__ X = pp.X;
   const float* __restrict__ sigma = pp.sigma;
   uint8_t* xb = pp.xb;
-  const int nb = g.nb, R = g.R;
-  const int units = g.xrows * (g.K / 8);   // 16-byte units per site
-  const int64_t total = pp.V * units;
+  const int nb = g.nb, R = g.R, rb = g.rb;
+  const int nkc = g.K / 8;
+  const int64_t total = pp.V * nkc * rb;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total;
        u += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t x = u / units;
-    const int w = (int)(u % units);
-    const int kc = w / g.xrows, mrow = w % g.xrows;
-    const int grp = mrow / g.rb, r = mrow % g.rb;
-    const bool lo_term = XSPLIT && grp >= 2;
-    const bool imag = (grp & 1) != 0;
+    const int r = (int)(u % rb);
+    const int64_t t = u / rb;
+    const int kc = (int)(t % nkc);
+    const int64_t x = t / nkc;
     const bool live = r < R;
     const float inv = live ? 1.0f / sigma[r] : 0.f;
-    uint16_t h[8];
+    uint16_t h[4][8];        // row groups: Re hi, Im hi, Re lo, Im lo
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int b = kc * 8 + e;
-      float v = 0.f;
+      float2 v = make_float2(0.f, 0.f);
       if (live && b < nb) {
         const float2 xv = X[(x * nb + b) * R + r];
-        v = (imag ? xv.y : xv.x) * inv;
+        v = make_float2(xv.x * inv, xv.y * inv);
       }
       if (XSPLIT) {
-        uint16_t hi, lo;
-        split16(v, hi, lo);
-        h[e] = lo_term ? lo : hi;
+        split16(v.x, h[0][e], h[2][e]);
+        split16(v.y, h[1][e], h[3][e]);
       } else {
-        h[e] = code16<BF16>(v);
+        h[0][e] = code16<BF16>(v.x);
+        h[1][e] = code16<BF16>(v.y);
       }
     }
-    uint4 pk;
-    pk.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-    pk.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
-    pk.z = (uint32_t)h[4] | ((uint32_t)h[5] << 16);
-    pk.w = (uint32_t)h[6] | ((uint32_t)h[7] << 16);
-    *reinterpret_cast<uint4*>(xb + (uint64_t)x * g.xb_bytes + canon_off(mrow, kc * 8, g.K)) = pk;
+    uint8_t* tile = xb + (uint64_t)x * g.xb_bytes;
+#pragma unroll
+    for (int grp = 0; grp < (XSPLIT ? 4 : 2); ++grp) {
+      uint4 pk;
+      pk.x = (uint32_t)h[grp][0] | ((uint32_t)h[grp][1] << 16);
+      pk.y = (uint32_t)h[grp][2] | ((uint32_t)h[grp][3] << 16);
+      pk.z = (uint32_t)h[grp][4] | ((uint32_t)h[grp][5] << 16);
+      pk.w = (uint32_t)h[grp][6] | ((uint32_t)h[grp][7] << 16);
+      *reinterpret_cast<uint4*>(tile + canon_off(grp * rb + r, kc * 8, g.K)) = pk;
+    }
   }
 }
 

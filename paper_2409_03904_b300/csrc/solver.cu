@@ -201,6 +201,91 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// The same for complex64 blocks of at most 32 columns: lane j keeps W[:, j]
+// and S^dagger[:, j] in registers and each warp stages its own kRotRows rows
+// of P1, P2 and D (no block barrier), read back as 16-byte broadcasts; the
+// next rows are loaded into registers while the current ones are multiplied.
+// A warp reads its rows completely before it writes them.
+constexpr int kRotRows = 2;
+constexpr int kRotWarps = 4;
+template <int MAXI>
+__global__ void __launch_bounds__(kRotWarps * 32)
+    k_rotate_w(float2* P1, float2* P2, float2* D, const double2* __restrict__ Wm,
+               const double2* __restrict__ Sm, int64_t N, int R) {
+  __shared__ __align__(16) float2 sp[3][kRotWarps][kRotRows][MAXI];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 w[MAXI], sh[MAXI];
+#pragma unroll
+  for (int i = 0; i < MAXI; ++i) {
+    w[i] = sh[i] = make_float2(0.f, 0.f);
+    if (i < R && lane < R) {
+      const double2 a = Wm[i * R + lane];
+      const double2 b = Sm[lane * R + i];      // S^dagger[i][j] = conj(S[j][i])
+      w[i] = make_float2((float)a.x, (float)a.y);
+      sh[i] = make_float2((float)b.x, -(float)b.y);
+    }
+  }
+  const bool two = P2 != nullptr;
+  const int64_t step = (int64_t)gridDim.x * kRotWarps * kRotRows;
+  int64_t n0 = ((int64_t)blockIdx.x * kRotWarps + warp) * kRotRows;
+  float2 pa[kRotRows], pb[kRotRows], pd[kRotRows];
+  auto load = [&](int64_t base) {
+#pragma unroll
+    for (int r = 0; r < kRotRows; ++r) {
+      const int64_t n = base + r;
+      pa[r] = pb[r] = pd[r] = make_float2(0.f, 0.f);
+      if (lane < R && n < N) {
+        pa[r] = P1[n * R + lane];
+        if (two) pb[r] = P2[n * R + lane];
+        pd[r] = D[n * R + lane];
+      }
+    }
+  };
+  load(n0);
+  for (; n0 < N; n0 += step) {
+#pragma unroll
+    for (int r = 0; r < kRotRows; ++r)
+      if (lane < MAXI) {
+        sp[0][warp][r][lane] = pa[r];
+        sp[1][warp][r][lane] = pb[r];
+        sp[2][warp][r][lane] = pd[r];
+      }
+    __syncwarp();
+    load(n0 + step);
+    float2 a1[kRotRows], a2[kRotRows], dd[kRotRows];
+#pragma unroll
+    for (int r = 0; r < kRotRows; ++r) a1[r] = a2[r] = dd[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < MAXI; i += 2) {
+#pragma unroll
+      for (int r = 0; r < kRotRows; ++r) {
+        const float4 x1 = *reinterpret_cast<const float4*>(&sp[0][warp][r][i]);
+        const float4 xd = *reinterpret_cast<const float4*>(&sp[2][warp][r][i]);
+        a1[r] = cfma(make_float2(x1.x, x1.y), w[i], a1[r]);
+        a1[r] = cfma(make_float2(x1.z, x1.w), w[i + 1], a1[r]);
+        dd[r] = cfma(make_float2(xd.x, xd.y), sh[i], dd[r]);
+        dd[r] = cfma(make_float2(xd.z, xd.w), sh[i + 1], dd[r]);
+        if (two) {
+          const float4 x2 = *reinterpret_cast<const float4*>(&sp[1][warp][r][i]);
+          a2[r] = cfma(make_float2(x2.x, x2.y), w[i], a2[r]);
+          a2[r] = cfma(make_float2(x2.z, x2.w), w[i + 1], a2[r]);
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kRotRows; ++r) {
+      const int64_t n = n0 + r;
+      if (lane < R && n < N) {
+        P1[n * R + lane] = a1[r];
+        if (two) P2[n * R + lane] = a2[r];
+        const float2 base = two ? a2[r] : a1[r];
+        D[n * R + lane] = make_float2(dd[r].x + base.x, dd[r].y + base.y);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------- small algebra
 struct Small {           // device-resident solver state (R <= 64)
   double2 C[64 * 64];    // k x R (rows >= k zero)
@@ -413,6 +498,20 @@ struct Ctx {
   }
   template <typename C>
   int rotate(C* P1, C* P2, C* D) {
+    if (sizeof(C) == sizeof(float2) && R <= 32) {
+      float2 *p1 = (float2*)P1, *p2 = (float2*)P2, *d = (float2*)D;
+      int64_t g = (N + kRotWarps * kRotRows - 1) / (kRotWarps * kRotRows);
+      const int64_t capw = (int64_t)num_sms() * 2;   // the resident CTAs (241 registers)
+      if (g > capw) g = capw;
+      if (R <= 8)
+        { k_rotate_w<8><<<(unsigned)g, kRotWarps * 32, 0, s>>>(p1, p2, d, st->W, st->S, N, R); ::mrhs::count_launch(); }
+      else if (R <= 16)
+        { k_rotate_w<16><<<(unsigned)g, kRotWarps * 32, 0, s>>>(p1, p2, d, st->W, st->S, N, R); ::mrhs::count_launch(); }
+      else
+        { k_rotate_w<32><<<(unsigned)g, kRotWarps * 32, 0, s>>>(p1, p2, d, st->W, st->S, N, R); ::mrhs::count_launch(); }
+      MRHS_CUDA_TRY(cudaGetLastError());
+      return MRHS_OK;
+    }
     const size_t smem = sizeof(C) * (2 * (size_t)R * R + 3 * (size_t)kTile * R);
     MRHS_CUDA_TRY(cudaFuncSetAttribute(k_rotate<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t grid = (N + kTile - 1) / kTile;
