@@ -533,24 +533,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(acc_empty);
         }
+        // exchange layout [group - 1][value][row r]: consecutive lanes touch
+        // consecutive 8-byte words (no bank conflicts)
         long long* xe = ex + xbuf * (3 * rb * 2 * kChunk);
         if (live && !writer) {
-          long long* slot = xe + ((grp - 1) * rb + r) * 2 * kChunk;
+          long long* slot = xe + (grp - 1) * 2 * kChunk * rb + r;
 #pragma unroll
           for (int e = 0; e < kChunk; ++e) {
-            slot[e] = vre[e];
-            slot[kChunk + e] = vim[e];
+            slot[e * rb] = vre[e];
+            slot[(kChunk + e) * rb] = vim[e];
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (writer) {
 #pragma unroll
           for (int gg = 0; gg < 3; ++gg) {
-            const long long* slot = xe + (gg * rb + r) * 2 * kChunk;
+            const long long* slot = xe + gg * 2 * kChunk * rb + r;
 #pragma unroll
             for (int e = 0; e < kChunk; ++e) {
-              vre[e] += slot[e];
-              vim[e] += slot[kChunk + e];
+              vre[e] += slot[e * rb];
+              vim[e] += slot[(kChunk + e) * rb];
             }
           }
 #pragma unroll

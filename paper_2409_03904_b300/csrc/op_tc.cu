@@ -76,7 +76,7 @@ namespace {
 constexpr int kThreadsTc = 192;
 constexpr int kAccCols = 128;    // TMEM columns per accumulator (n_mma <= 128)
 constexpr int kChunk = 8;        // epilogue columns per tcgen05.ld
-constexpr int kExFloats = 96 * 2 * kChunk;   // one exchange buffer (3 x 32 or 64 rows)
+constexpr int kExFloats = 3 * 2 * kChunk * 32;   // one exchange buffer (3 x 16 x 32 or 1 x 16 x 64)
 constexpr int kM = 128;
 constexpr size_t kSmemBudget = 220 * 1024;   // dynamic shared memory per SM
 constexpr size_t kSmemOneCta = 120 * 1024;   // at least this much keeps a CTA alone on its SM
@@ -605,24 +605,27 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
         }
         // contribution of this row to (Re Y, Im Y)[a][r]: an Xr row gives
         // (u, w), an Xi row (-w, u); lo rows scaled by 2^-11
+        // exchange layout [group - 1][value][row r] (3 x 16 x 32 floats split,
+        // 1 x 16 x 64 otherwise): consecutive lanes touch consecutive words,
+        // so the accesses are free of bank conflicts
         float* xe = ex + xbuf * kExFloats;
         if (live && !writer) {
-          float* slot = xe + ((grp - 1) * rb + r) * 2 * kChunk;
+          float* slot = xe + (grp - 1) * 2 * kChunk * rb + r;
 #pragma unroll
           for (int e = 0; e < kChunk; ++e) {
-            slot[e] = gs * (imag ? -w[e] : u[e]);
-            slot[kChunk + e] = gs * (imag ? u[e] : w[e]);
+            slot[e * rb] = gs * (imag ? -w[e] : u[e]);
+            slot[(kChunk + e) * rb] = gs * (imag ? u[e] : w[e]);
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (writer) {
 #pragma unroll
           for (int gg = 1; gg < (XSPLIT ? 4 : 2); ++gg) {
-            const float* slot = xe + ((gg - 1) * rb + r) * 2 * kChunk;
+            const float* slot = xe + (gg - 1) * 2 * kChunk * rb + r;
 #pragma unroll
             for (int e = 0; e < kChunk; ++e) {
-              u[e] += slot[e];
-              w[e] += slot[kChunk + e];
+              u[e] += slot[e * rb];
+              w[e] += slot[(kChunk + e) * rb];
             }
           }
 #pragma unroll
