@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--lattice", default=None, help="a,b,c,d: override the workload's lattice "
                     "(operator mode; same per-site work)")
     ap.add_argument("--nrhs", type=int, default=None, help="operator mode: right-hand sides")
+    ap.add_argument("--nrhs-list", default=None, metavar="R1,R2,...",
+                    help="operator mode: one operator, one JSON line per number of right-hand sides")
     ap.add_argument("--nb", type=int, default=None, help="operator mode: basis size")
     ap.add_argument("--npts", type=int, default=None, choices=[1, 9, 81],
                     help="operator mode: stencil points")
@@ -290,89 +292,98 @@ def run_op(a, w, shift):
         if getattr(a, k) is not None:
             over[k] = getattr(a, k)
     w = dict(w, **over)
-    R, V, nb, prec = w["nrhs"], int(np.prod(w["L"])), w["nb"], a.op
+    V, nb, prec = int(np.prod(w["L"])), w["nb"], a.op
     disp, _ = stencil(w["npts"])
     dev = torch.device("cuda", 0)
     A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
     op = mrhs.CoarseOp(A, w["L"], disp, (prec,))
     del A
     torch.cuda.empty_cache()
-    vdt = torch.complex128 if prec in WIDE else torch.complex64
-    X = sdev.vectors(w["L"], nb, R, w["seed"], device=dev).to(vdt)
-    Y = torch.empty_like(X)
-    stream = torch.cuda.current_stream()
-    tuned = None
-    if not a.no_autotune and prec not in ("fp64", "fp32", "df32", "oz"):
-        try:
-            tuned = mrhs.autotune(op, prec, R, reps=3)
-        except mrhs.MrhsError:
-            tuned = None
-    for _ in range(a.warmup):
-        op.apply(X, prec, out=Y)
-    op.kernel_timing(True)
-    l0 = mrhs.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    Rs = [int(v) for v in a.nrhs_list.split(",")] if a.nrhs_list else [w["nrhs"]]
+
+    def one(R):
+        if a.nrhs_list:
+            over["nrhs"] = R
+        w["nrhs"] = R
+        vdt = torch.complex128 if prec in WIDE else torch.complex64
+        X = sdev.vectors(w["L"], nb, R, w["seed"], device=dev).to(vdt)
+        Y = torch.empty_like(X)
+        stream = torch.cuda.current_stream()
+        tuned = None
+        if not a.no_autotune and prec not in ("fp64", "fp32", "df32", "oz"):
+            try:
+                tuned = mrhs.autotune(op, prec, R, reps=3)
+            except mrhs.MrhsError:
+                tuned = None
+        for _ in range(a.warmup):
+            op.apply(X, prec, out=Y)
+        op.kernel_timing(True)
+        l0 = mrhs.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(a.steps):
+                op.apply(X, prec, out=Y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        launches = mrhs.launch_count() - l0
+        ms = e0.elapsed_time(e1) / a.steps
+        nk, kms = op.kernel_time(prec)
+        op.kernel_timing(False)
+        flops = op_flops(w, R)
+        byts = op_bytes(w, R, prec)
+        hbm, bf16_peak, kind = peaks()
+        per = kms / max(nk, 1)
+        roof = {"bound": "hbm", "achieved": byts / (per * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": byts / (per * 1e-3) / 1e9 / hbm, "traffic": None,
+                "kernel": f"coarse operator ({prec})", "algorithmic_bytes": byts, "launch_ms": per,
+                "launches": nk, "peak_kind": f"{kind} copy bandwidth"}
+        if prec == "oz":
+            # digit-sliced form: bound by the fp16 tensor pipe.  Algorithmic work =
+            # the 28 digit-pair products (s + t <= 8) of the complex operator;
+            # issued = 19 MMAs of M = 128 per point and K step (two digit levels
+            # per accumulator, 10 of the 38 half-MMAs have a zero or dropped half)
+            pairs = sum(range(1, 8))
+            alg = pairs * flops
+            issued = 19 * 2 * 128 * (2 * ((nb + 7) // 8 * 8)) * ((nb + 15) // 16 * 16) \
+                * w["npts"] * V
+            roof = {"bound": "tensor", "achieved": alg / (per * 1e-3) / 1e12, "peak": bf16_peak,
+                    "unit": "TFLOP/s", "frac": alg / (per * 1e-3) / 1e12 / bf16_peak,
+                    "traffic": None if over else dram_traffic(prec, w["name"]), "kernel": "coarse operator (oz, tcgen05 fp16 digit MMAs)",
+                    "algorithmic_flops": alg, "issued_flops": issued,
+                    "issued_tflops": issued / (per * 1e-3) / 1e12,
+                    "hbm_gbs": byts / (per * 1e-3) / 1e9, "launch_ms": per, "launches": nk,
+                    "peak_kind": f"{kind} dense bf16 (fp16 runs at the same rate)"}
+        # end to end: host input -> device, apply, device -> host result
+        Xh = X.cpu().pin_memory()
+        Yh = torch.empty_like(Xh).pin_memory()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(a.steps):
-            op.apply(X, prec, out=Y)
+            Xd = Xh.to(dev, non_blocking=True)
+            op.apply(Xd, prec, out=Y)
+            Yh.copy_(Y, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-    launches = mrhs.launch_count() - l0
-    ms = e0.elapsed_time(e1) / a.steps
-    nk, kms = op.kernel_time(prec)
-    op.kernel_timing(False)
-    flops = op_flops(w, R)
-    byts = op_bytes(w, R, prec)
-    hbm, bf16_peak, kind = peaks()
-    per = kms / max(nk, 1)
-    roof = {"bound": "hbm", "achieved": byts / (per * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": byts / (per * 1e-3) / 1e9 / hbm, "traffic": None,
-            "kernel": f"coarse operator ({prec})", "algorithmic_bytes": byts, "launch_ms": per,
-            "launches": nk, "peak_kind": f"{kind} copy bandwidth"}
-    if prec == "oz":
-        # digit-sliced form: bound by the fp16 tensor pipe.  Algorithmic work =
-        # the 28 digit-pair products (s + t <= 8) of the complex operator;
-        # issued = 19 MMAs of M = 128 per point and K step (two digit levels
-        # per accumulator, 10 of the 38 half-MMAs have a zero or dropped half)
-        pairs = sum(range(1, 8))
-        alg = pairs * flops
-        issued = 19 * 2 * 128 * (2 * ((nb + 7) // 8 * 8)) * ((nb + 15) // 16 * 16) \
-            * w["npts"] * V
-        roof = {"bound": "tensor", "achieved": alg / (per * 1e-3) / 1e12, "peak": bf16_peak,
-                "unit": "TFLOP/s", "frac": alg / (per * 1e-3) / 1e12 / bf16_peak,
-                "traffic": None if over else dram_traffic(prec, w["name"]), "kernel": "coarse operator (oz, tcgen05 fp16 digit MMAs)",
-                "algorithmic_flops": alg, "issued_flops": issued,
-                "issued_tflops": issued / (per * 1e-3) / 1e12,
-                "hbm_gbs": byts / (per * 1e-3) / 1e9, "launch_ms": per, "launches": nk,
-                "peak_kind": f"{kind} dense bf16 (fp16 runs at the same rate)"}
-    # end to end: host input -> device, apply, device -> host result
-    Xh = X.cpu().pin_memory()
-    Yh = torch.empty_like(Xh).pin_memory()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(a.steps):
-        Xd = Xh.to(dev, non_blocking=True)
-        op.apply(Xd, prec, out=Y)
-        Yh.copy_(Y, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / a.steps
-    out = {"metric": "coarse-op TFLOP/s at Nrhs=%d" % R, "value": flops / (ms * 1e-3) / 1e12,
-           "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": prec, "data": "synthetic",
-           "config": {"workload": w["name"] + ("" if not over else " with " + ", ".join(
-                          f"{k}={v}" for k, v in over.items())),
-                      "L": list(w["L"]), "nb": nb, "npts": w["npts"], "nrhs": R,
-                      "launch_shape": tuned,
-                      "l2": f"inputs larger than L2 ({byts / 1e9:.2f} GB per application)"},
-           "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
-           "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-                   "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
-                   "d2h_bytes_per_step": Yh.numel() * Yh.element_size()}}
-    print(json.dumps(out), flush=True)
+        e2e_ms = e0.elapsed_time(e1) / a.steps
+        out = {"metric": "coarse-op TFLOP/s at Nrhs=%d" % R, "value": flops / (ms * 1e-3) / 1e12,
+               "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+               "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": prec, "data": "synthetic",
+               "config": {"workload": w["name"] + ("" if not over else " with " + ", ".join(
+                              f"{k}={v}" for k, v in over.items())),
+                          "L": list(w["L"]), "nb": nb, "npts": w["npts"], "nrhs": R,
+                          "launch_shape": tuned,
+                          "l2": f"inputs larger than L2 ({byts / 1e9:.2f} GB per application)"},
+               "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
+               "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
+                       "d2h_bytes_per_step": Yh.numel() * Yh.element_size()}}
+        print(json.dumps(out), flush=True)
+
+    for R in Rs:
+        one(R)
 
 
 def run_defl(a, w, shift):
