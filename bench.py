@@ -547,7 +547,7 @@ def run_batch(a):
     for w, c in probs:
         disp, _ = stencil(w["npts"])
         A = sdev.coarse_op(w["L"], w["nb"], w["npts"], w["seed"], load_shift(w["name"]))
-        ops.append(mrhs.CoarseOp(A, w["L"], disp, ("fp64", "fp16x", "tc32")))
+        ops.append(mrhs.CoarseOp(A, w["L"], disp, ("fp64", "fp16x", "tc32", "oz")))
         del A
         Bs.append(sdev.vectors(w["L"], w["nb"], w["nrhs"], w["seed"] + 101 * c))
     for o in ops:
@@ -582,7 +582,7 @@ def run_batch(a):
     out = {"metric": "batched block-CG time-to-1e-8 per RHS", "value": bt / nrhs, "unit": "ms/RHS",
            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": bt,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64+df32+tc32+fp16x", "data": "synthetic",
+           "dtype": "f64+oz+tc32+fp16x", "data": "synthetic",
            "config": {"workload": f"{len(probs)} independent problems ({a.batch})",
                       "problems": [w["name"] for w, _ in probs], "nrhs_total": nrhs, "tol": 1e-8},
            "one_by_one_ms": st, "batched_over_one_by_one": st / bt,

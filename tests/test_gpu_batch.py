@@ -143,3 +143,26 @@ def test_autotune_single_and_batch(mrhs):
         assert torch.equal(a, b)
     assert mrhs.device_error() == 0
     mrhs.autotune_clear()
+
+
+def test_batch_solve_with_oz_residuals(mrhs):
+    """Every problem has the digit-sliced image: the lockstep solve takes its
+    cycle residuals from it (one launch per problem, on the problem's own
+    stream) and still ends on FP64 residuals <= tol."""
+    pick = [0, 2, 10]
+    ws = [BATCH[i] for i in pick]
+    ops, Bs, host = [], [], []
+    for w in ws:
+        disp, _ = stencil(w["npts"])
+        A = coarse_op(w["L"], w["nb"], w["npts"], w["seed"], load_shift(w["name"]))
+        B = vectors(w["L"], w["nb"], w["nrhs"], w["seed"])
+        ops.append(mrhs.CoarseOp(torch.from_numpy(A).cuda(), w["L"], disp,
+                                 ("fp64", "fp16x", "tc32", "oz")))
+        Bs.append(torch.from_numpy(B).cuda())
+        host.append((A, B))
+    Xs, infos = mrhs.batch_solve(ops, Bs, tol=1e-8)
+    for w, X, info, (A, B) in zip(ws, Xs, infos, host):
+        assert info["status"] == 0 and max(info["resid"]) <= 1e-8, (w["name"], info)
+        assert info["applies"]["oz"] >= 1 and info["applies"]["df32"] == 0, info["applies"]
+        assert oracle_residual(w, A, X.cpu().numpy(), B) <= 1.5e-8
+    assert mrhs.device_error() == 0
