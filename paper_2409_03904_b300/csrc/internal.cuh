@@ -82,6 +82,21 @@ struct TcTune {
   int max_stages = 32;   // ring depth cap
 };
 
+// A Chebyshev recurrence step carried out in the epilogue of the tensor-core
+// operator (op_tc.cu, ProbDesc): with W = H X (not stored),
+//   mode 1:  Tout = a W + b X,           P = c0 X + c Tout
+//   mode 2:  Tout = 2 (a W + b X) - Tp,  P = P + c Tout
+// complex64 vectors; Tout may be Tp, never X.
+struct ChebFuse {
+  int mode = 0;
+  float a = 0.f, b = 0.f, c = 0.f, c0 = 0.f;
+  void* Tout = nullptr;
+  const void* Tp = nullptr;
+  void* P = nullptr;
+  bool colmax_next = false;   // accumulate Tout's column maxima for the next application
+  bool colmax_ready = false;  // this application's input maxima are accumulated already
+};
+
 struct Workspace {           // grow-only device scratch
   void* ptr = nullptr;
   size_t bytes = 0;
@@ -134,7 +149,7 @@ int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s
 unsigned tc_read_and_clear_error();
 int tc_apply_batch(mrhs_op_s* const* ops, int n, int prec, const void* const* X,
                    void* const* Y, const int32_t* nrhs, const int32_t* active, cudaStream_t s,
-                   const TcTune* force = nullptr);
+                   const TcTune* force = nullptr, const ChebFuse* fuse = nullptr);
 // launch-shape cache (tune.cu)
 bool tune_lookup(mrhs_op_s* const* ops, const int32_t* nrhs, int n, int prec, TcTune* out);
 int autotune(mrhs_op_s* const* ops, int n, int prec, const int32_t* nrhs, int reps,

@@ -362,6 +362,18 @@ struct ProbDesc {
   int64_t V, item0;         // sites; first item of this problem in the work list
   int32_t npts, nb, nbp8, K, n_mma, R, pps, rb;
   uint32_t coef1, coef_bytes, xb_bytes, sbo, idesc, xb_off;
+  // Chebyshev step in the epilogue (cheb != 0): W = H X is not stored; with
+  // the recurrence's a, b and coefficient c (c0 too for the first step)
+  //   cheb 1:  T = a W + b X,             P = c0 X + c T
+  //   cheb 2:  T = 2 (a W + b X) - Tp,    P = P + c T
+  // T goes to Tout (may be Tp); colmax_next, when set, receives the column
+  // maxima of T for the next application's packing.
+  int32_t cheb;
+  float ca, cb, cc, c0;
+  float* Tout;
+  const float* Tp;
+  float* P;
+  unsigned* colmax_next;
   Stencil st;
 };
 
@@ -550,6 +562,10 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
     const int mrow = 32 * q + lane;              // D row = TMEM lane
     int acc = 0, xbuf = 0;
     uint32_t aph = 0;
+    // running column maximum of the Chebyshev output (writer lanes)
+    float cm = 0.f;
+    int cm_prob = -1, cm_r = -1;
+    unsigned* cm_dst = nullptr;
     for (int64_t t = blockIdx.x; t < bt.total; t += gridDim.x) {
       const int k = find_prob(bt, t);
       if (!item_live(bt, k)) continue;
@@ -558,6 +574,14 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
       const int R = pd.R, nb = pd.nb, nbp8 = pd.nbp8, rb = pd.rb;
       const float2* Xp = reinterpret_cast<const float2*>(pd.X);
       float2* Yp = reinterpret_cast<float2*>(pd.Y);
+      const int cheb = pd.cheb;
+      if (k != cm_prob) {      // a new problem: post the previous one's column maxima
+        if (cm_dst && cm_r >= 0) atomicMax(&cm_dst[cm_r], __float_as_uint(cm));
+        cm = 0.f;
+        cm_prob = k;
+        cm_dst = pd.colmax_next;
+        cm_r = -1;
+      }
       // row group of this lane: 0 Xr (writes Y), 1 Xi, 2 Xr_lo, 3 Xi_lo
       const int grp = mrow / rb, r = mrow % rb;
       const bool live = r < R && grp < (XSPLIT ? 4 : 2);
@@ -568,6 +592,7 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
       if (writer) {
         sc = __ldg(&pd.scale[x]) * __ldg(&pd.sigma[r]);
         dx = __ldg(&pd.diag[x]);
+        cm_r = r;
       }
       const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort);
       // give up together: tcgen05.ld below is .aligned per warp and the four
@@ -629,19 +654,50 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
             }
           }
 #pragma unroll
+          // every load of the chunk first, then the stores: a store may alias a
+          // later element's load as far as the compiler knows, and would
+          // otherwise serialise the loads
+          const int64_t base = (int64_t)x * nb * R + r;
+          float2 xv[kChunk], tp[kChunk], pv[kChunk];
+#pragma unroll
           for (int e = 0; e < kChunk; ++e) {
-            const int a = c0 + e;
-            if (a < nb) {
-              const int64_t idx = ((int64_t)x * nb + a) * R + r;
-              const float2 xv = __ldg(&Xp[idx]);
-              Yp[idx] = make_float2(fmaf(sc, u[e], dx * xv.x), fmaf(sc, w[e], dx * xv.y));
+            const int64_t idx = base + (int64_t)(c0 + e) * R;
+            const bool in = c0 + e < nb;
+            xv[e] = in ? __ldg(&Xp[idx]) : make_float2(0.f, 0.f);
+            tp[e] = pv[e] = make_float2(0.f, 0.f);
+            if (cheb == 2 && in) {
+              tp[e] = reinterpret_cast<const float2*>(pd.Tp)[idx];   // may be Tout: no .nc load
+              pv[e] = reinterpret_cast<const float2*>(pd.P)[idx];
             }
+          }
+#pragma unroll
+          for (int e = 0; e < kChunk; ++e) {
+            if (c0 + e >= nb) continue;
+            const int64_t idx = base + (int64_t)(c0 + e) * R;
+            const float2 y = make_float2(fmaf(sc, u[e], dx * xv[e].x), fmaf(sc, w[e], dx * xv[e].y));
+            if (cheb == 0) {
+              Yp[idx] = y;
+              continue;
+            }
+            const float ca = pd.ca, cb = pd.cb, cc = pd.cc;
+            float2 t = make_float2(ca * y.x + cb * xv[e].x, ca * y.y + cb * xv[e].y);
+            float2 p;
+            if (cheb == 1) {
+              p = make_float2(pd.c0 * xv[e].x + cc * t.x, pd.c0 * xv[e].y + cc * t.y);
+            } else {
+              t = make_float2(2.f * t.x - tp[e].x, 2.f * t.y - tp[e].y);
+              p = make_float2(pv[e].x + cc * t.x, pv[e].y + cc * t.y);
+            }
+            reinterpret_cast<float2*>(pd.Tout)[idx] = t;
+            reinterpret_cast<float2*>(pd.P)[idx] = p;
+            cm = fmaxf(cm, fmaxf(fabsf(t.x), fabsf(t.y)));
           }
         }
         xbuf ^= 1;      // the next chunk writes the other buffer
       }
       if (++acc == 2) { acc = 0; aph ^= 1u; }
     }
+    if (cm_dst && cm_r >= 0) atomicMax(&cm_dst[cm_r], __float_as_uint(cm));
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -764,6 +820,12 @@ int prepare(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
   pd->xb_bytes = g.xb_bytes;
   pd->sbo = g.sbo;
   pd->idesc = ptx::idesc_f16(kM, g.n_mma, prec == MRHS_PREC_BF16);
+  pd->cheb = 0;
+  pd->ca = pd->cb = pd->cc = pd->c0 = 0.f;
+  pd->Tout = nullptr;
+  pd->Tp = nullptr;
+  pd->P = nullptr;
+  pd->colmax_next = nullptr;
   for (int mu = 0; mu < 4; ++mu) pd->st.L[mu] = op->L[mu];
   pd->st.sign = dag ? -1 : 1;
   for (int p = 0; p < op->npts; ++p)
@@ -773,10 +835,12 @@ int prepare(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
 }
 
 // The three packing launches for every problem of `pb`.
-int pack_batch(const PackBatch& pb, int prec, cudaStream_t s) {
+// colmax_ready: the previous launch (a fused Chebyshev step) already
+// accumulated the column maxima of this input.
+int pack_batch(const PackBatch& pb, int prec, cudaStream_t s, bool colmax_ready = false) {
   const int sms = num_sms();
   const dim3 g4((unsigned)(sms * 4), (unsigned)pb.n), g8((unsigned)(sms * 8), (unsigned)pb.n);
-  { k_colmax<<<g4, 256, 0, s>>>(pb); ::mrhs::count_launch(); }
+  if (!colmax_ready) { k_colmax<<<g4, 256, 0, s>>>(pb); ::mrhs::count_launch(); }
   { k_colscale<<<pb.n, 64, 0, s>>>(pb); ::mrhs::count_launch(); }
   if (prec == MRHS_PREC_BF16)
     { k_pack_xb<true, false><<<g8, 256, 0, s>>>(pb); ::mrhs::count_launch(); }
@@ -910,7 +974,7 @@ int tc_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs
 // Many operators in one persistent launch (each with its own inputs).
 int tc_apply_batch(mrhs_op_s* const* ops, int n, int prec, const void* const* X,
                    void* const* Y, const int32_t* nrhs, const int32_t* active, cudaStream_t s,
-                   const TcTune* force) {
+                   const TcTune* force, const ChebFuse* fuse) {
   if (n < 1 || n > MRHS_MAX_BATCH) return fail(MRHS_ERR_INVALID_ARG, "batch size 1..16");
   if (image_index(prec) < 0) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core precision");
   TcTune tune = ops[0]->tc_tune;
@@ -934,7 +998,22 @@ int tc_apply_batch(mrhs_op_s* const* ops, int n, int prec, const void* const* X,
     MRHS_TRY(prepare(ops[i], prec, false, X[i], Y[i], nrhs[i], set ? tune.pps : 0, s, &bt.p[i],
                      &pb.p[i], &g[i]));
   }
-  MRHS_TRY(pack_batch(pb, prec, s));
+  bool colmax_ready = fuse != nullptr;
+  for (int i = 0; i < n && fuse; ++i) {
+    const ChebFuse& f = fuse[i];
+    ProbDesc& pd = bt.p[i];
+    pd.cheb = f.mode;
+    pd.ca = f.a;
+    pd.cb = f.b;
+    pd.cc = f.c;
+    pd.c0 = f.c0;
+    pd.Tout = (float*)f.Tout;
+    pd.Tp = (const float*)f.Tp;
+    pd.P = (float*)f.P;
+    pd.colmax_next = f.colmax_next ? pb.p[i].colmax : nullptr;
+    colmax_ready = colmax_ready && f.colmax_ready;
+  }
+  MRHS_TRY(pack_batch(pb, prec, s, colmax_ready));
   // a single problem keeps its operator's kernel timer
   return run_batch(bt, g, prec, tune, set, prec, n == 1 ? ops[0] : nullptr, s);
 }

@@ -552,6 +552,42 @@ int cheb_run(Ctx& cx, int prec, double lo, double hi, int order, const C* X, C* 
     MRHS_CUDA_TRY(cudaGetLastError());
     return MRHS_OK;
   }
+  if (MRHS_PREC_IS_TC(prec) && sizeof(C) == sizeof(float2)) {
+    // each step inside the operator's epilogue: W is never stored, and the
+    // step's output column maxima are ready for the next application's packing
+    ChebFuse f;
+    f.mode = 1;
+    f.a = (float)a;
+    f.b = (float)b;
+    f.c0 = (float)c[0];
+    f.c = (float)c[1];
+    f.Tout = T1;
+    f.P = P;
+    f.colmax_next = order >= 2;
+    const void* in = X;
+    void* none = nullptr;
+    int32_t R = cx.R;
+    mrhs_op_s* op = cx.op;
+    cx.applies[prec]++;
+    MRHS_TRY(tc_apply_batch(&op, 1, prec, &in, &none, &R, nullptr, cx.s, nullptr, &f));
+    const C* Tprev = X;
+    C* Tcur = T1;
+    for (int j = 2; j <= order; ++j) {
+      C* dst = (Tprev == X) ? T2 : const_cast<C*>(Tprev);
+      f.mode = 2;
+      f.c = (float)c[j];
+      f.Tout = dst;
+      f.Tp = Tprev;
+      f.colmax_next = j < order;
+      f.colmax_ready = true;
+      in = Tcur;
+      cx.applies[prec]++;
+      MRHS_TRY(tc_apply_batch(&op, 1, prec, &in, &none, &R, nullptr, cx.s, nullptr, &f));
+      Tprev = Tcur;
+      Tcur = dst;
+    }
+    return MRHS_OK;
+  }
   MRHS_TRY(cx.apply(prec, X, W));
   { k_cheb_first<C><<<g, kThreads, 0, cx.s>>>(T1, P, W, X, a, b, c[0], c[1], n); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
@@ -1208,6 +1244,49 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
     auto bcheb = [&](float2* const* Xs, float2* const* Ps) -> int {
       std::vector<const float2*> Tprev(m);
       std::vector<float2*> Tcur(m);
+      if (order > 0) {
+        // every step inside the batched operator's epilogue (W never stored)
+        std::vector<ChebFuse> f(m);
+        std::vector<void*> none(m, nullptr);
+        for (int k = 0; k < m; ++k) {
+          BatchProb& b = P[idx[k]];
+          const std::vector<double>& c = coef[idx[k]];
+          const double a = 2.0 / (b.hi - b.lo), bb = -(b.hi + b.lo) / (b.hi - b.lo);
+          f[k].mode = 1;
+          f[k].a = (float)a;
+          f[k].b = (float)bb;
+          f[k].c0 = (float)c[0];
+          f[k].c = (float)c[1];
+          f[k].Tout = b.sb.b32.c1;
+          f[k].P = Ps[k];
+          f[k].colmax_next = order >= 2;
+          in[k] = Xs[k];
+          Tprev[k] = Xs[k];
+          Tcur[k] = b.sb.b32.c1;
+          b.cx.applies[pp]++;
+        }
+        MRHS_TRY(tc_apply_batch(bops.data(), m, pp, in.data(), none.data(), bR.data(), d_active,
+                                s, nullptr, f.data()));
+        for (int j = 2; j <= order; ++j) {
+          for (int k = 0; k < m; ++k) {
+            BatchProb& b = P[idx[k]];
+            float2* dst = (Tprev[k] == Xs[k]) ? b.sb.b32.c2 : const_cast<float2*>(Tprev[k]);
+            f[k].mode = 2;
+            f[k].c = (float)coef[idx[k]][j];
+            f[k].Tout = dst;
+            f[k].Tp = Tprev[k];
+            f[k].colmax_next = j < order;
+            f[k].colmax_ready = true;
+            in[k] = Tcur[k];
+            Tprev[k] = Tcur[k];
+            Tcur[k] = dst;
+            b.cx.applies[pp]++;
+          }
+          MRHS_TRY(tc_apply_batch(bops.data(), m, pp, in.data(), none.data(), bR.data(), d_active,
+                                  s, nullptr, f.data()));
+        }
+        return MRHS_OK;
+      }
       for (int k = 0; k < m; ++k) {
         in[k] = Xs[k];
         out[k] = P[idx[k]].sb.b32.cw;
