@@ -328,15 +328,25 @@ __global__ void k_small_M(Small* st, int R, double tau) {
   __shared__ int perm[64];
   const int k_in = st->rank;
   const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, nullptr, st->W);
-  // st->W now holds the inverse factor in caller order: M = W W^dagger
+  // st->W now holds the inverse factor in caller order: M = W W^dagger.  The
+  // products below run from shared memory (W stored transposed, so that a
+  // warp's lanes read consecutive words); on B300 one SM's FP64 rate makes
+  // them the bulk of this kernel.
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int j = e / R, l = e % R;
+    sA[l * R + j] = st->W[e];                       // sA[l][j] = W[j][l]
+    sW[e] = st->C[e];
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     const int i = e / R, j = e % R;
     double2 acc = make_double2(0.0, 0.0);
     for (int l = 0; l < R; ++l) {
-      const double2 a = st->W[i * R + l], b = st->W[j * R + l];
+      const double2 a = sA[l * R + i], b = sA[l * R + j];
       acc = cfma(a, make_double2(b.x, -b.y), acc);
     }
+    sS[e] = acc;
     st->M[e] = acc;
     st->negM[e] = make_double2(-acc.x, -acc.y);
   }
@@ -344,7 +354,7 @@ __global__ void k_small_M(Small* st, int R, double tau) {
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     const int i = e / R, j = e % R;
     double2 acc = make_double2(0.0, 0.0);
-    for (int l = 0; l < R; ++l) acc = cfma(st->M[i * R + l], st->C[l * R + j], acc);
+    for (int l = 0; l < R; ++l) acc = cfma(sS[i * R + l], sW[l * R + j], acc);
     st->MC[e] = acc;
   }
   if (threadIdx.x == 0 && k < k_in) st->flag |= 2;   // D^dagger H D lost rank
@@ -359,16 +369,26 @@ __global__ void k_small_S(Small* st, int R, double tau, int precond) {
   double2* sS = sA + R * R;
   double2* sW = sS + R * R;
   __shared__ int perm[64];
-  double2* sC = sA;   // the elimination scratch is free once the factor is written
   const int k_in = st->rank;
   if (precond) {
+    // est_j = |C[:, j]|_{G2}: V = G2 C from shared memory, then the columns
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      sA[e] = st->G2[e];
+      sW[e] = st->C[e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int a = e / R, j = e % R;
+      double2 v = make_double2(0.0, 0.0);
+      for (int b = 0; b < R; ++b) v = cfma(sA[a * R + b], sW[b * R + j], v);
+      sS[e] = v;
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < R; j += blockDim.x) {
       double s = 0.0;
       for (int a = 0; a < R; ++a) {
-        double2 v = make_double2(0.0, 0.0);        // (G2 C)[a][j]
-        for (int b = 0; b < R; ++b) v = cfma(st->G2[a * R + b], st->C[b * R + j], v);
-        const double2 c = st->C[a * R + j];
-        s += c.x * v.x + c.y * v.y;                 // Re(conj(C_aj) v)
+        const double2 c = sW[a * R + j], v = sS[a * R + j];
+        s += c.x * v.x + c.y * v.y;                 // Re(conj(C_aj) v_aj)
       }
       st->est[j] = sqrt(fmax(s, 0.0));
     }
@@ -376,19 +396,25 @@ __global__ void k_small_S(Small* st, int R, double tau, int precond) {
   __syncthreads();
   const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, st->S, st->W);
   __syncthreads();
+  // C <- S C from shared memory
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    sA[e] = st->S[e];
+    sW[e] = st->C[e];
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     const int i = e / R, j = e % R;
     double2 acc = make_double2(0.0, 0.0);
-    for (int l = 0; l < R; ++l) acc = cfma(st->S[i * R + l], st->C[l * R + j], acc);
-    sC[e] = acc;
+    for (int l = 0; l < R; ++l) acc = cfma(sA[i * R + l], sW[l * R + j], acc);
+    sS[e] = acc;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) st->C[e] = sC[e];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) st->C[e] = sS[e];
   __syncthreads();
   if (!precond)
     for (int j = threadIdx.x; j < R; j += blockDim.x) {
       double s = 0.0;
-      for (int a = 0; a < R; ++a) s += sC[a * R + j].x * sC[a * R + j].x + sC[a * R + j].y * sC[a * R + j].y;
+      for (int a = 0; a < R; ++a) s += sS[a * R + j].x * sS[a * R + j].x + sS[a * R + j].y * sS[a * R + j].y;
       st->est[j] = sqrt(s);
     }
   __syncthreads();
