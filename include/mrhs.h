@@ -389,6 +389,23 @@ int32_t mrhs_device_error(void);
  * in the process so far. */
 int mrhs_op_kernel_timing(mrhs_op op, int32_t enable);
 
+/* Hermitian pairing in the tensor-core kernels.  When the hop coefficients
+ * satisfy A_q(x + delta_p) = A_p(x)^dagger exactly (q the point with
+ * delta_q = -delta_p, p != 0; checked at creation, Sec. 2.6's Hermitian
+ * coarse operator) and nb is a multiple of 16, the BF16/FP16/FP16X/TC32
+ * kernels read
+ * one coefficient tile per pair of points: the tile of (x, p) serves site x
+ * directly and site x + delta_p transposed and conjugated, the second read
+ * coming from L2 when both sites are in flight.  Sites are visited in 4D
+ * blocks for that.  mode -1 queries, 0 disables, 1 enables (MRHS_ERR_UNSUPPORTED
+ * if the hop pairs are not exactly Hermitian); *active (may be null) receives
+ * the state after the call.  Off by default: at 12^4, nb 48, 32 RHS the
+ * shared reads cut DRAM traffic by 10% (FP16X) and 4% (TC32) only, and the
+ * second, transposed use costs two MMAs (N = nb) per K step that re-read the
+ * input tile, so neither form gets faster.  Results equal the unpaired
+ * kernel's up to FP32 summation order. */
+int mrhs_op_hermitian(mrhs_op op, int32_t mode, int32_t* active);
+
 /* Launch shape of this operator's BF16/FP16 tensor-core kernel (the knobs an
  * autotuner searches): stencil points per pipeline stage (1..16; 0 = built-in
  * choice of >= 16 KB of coefficients per copy), CTAs per SM (1 or 2, each

@@ -128,6 +128,15 @@ class CoarseOp:
                                                  ctypes.byref(lam), _lib.stream_ptr()))
         return float(lam.value)
 
+    def hermitian(self, enable=None):
+        """Hermitian pairing of the tensor-core kernels (one coefficient tile
+        per point pair, see mrhs_op_hermitian): None queries, True/False
+        enables/disables; returns whether it is active."""
+        act = ctypes.c_int32()
+        mode = -1 if enable is None else (1 if enable else 0)
+        _lib.check(_lib.lib().mrhs_op_hermitian(self._h, mode, ctypes.byref(act)))
+        return bool(act.value)
+
     def tc_tune(self, pts_per_stage=0, ctas_per_sm=1, max_stages=32):
         """Launch shape of the BF16/FP16 tensor-core kernel (0 = default)."""
         _lib.check(_lib.lib().mrhs_op_tc_tune(self._h, int(pts_per_stage), int(ctas_per_sm),

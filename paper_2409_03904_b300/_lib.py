@@ -98,6 +98,7 @@ SIGNATURES = {
     "mrhs_launch_count": [],
     "mrhs_op_lambda_max": [P, I32, I32, P, P],
     "mrhs_op_tc_tune": [P, I32, I32, I32],
+    "mrhs_op_hermitian": [P, I32, P],
     "mrhs_batch_apply": [P, I32, I32, P, P, P, P],
     "mrhs_batch_solve": [P, I32, P, P, P, ctypes.POINTER(SolveParams), P, P],
     "mrhs_autotune": [P, I32, I32, P, I32, ctypes.POINTER(TuneResult), P],

@@ -77,6 +77,26 @@ __global__ void k_neighbours(int32_t* fwd, int32_t* bwd, int64_t V, int npts, in
   bwd[(int64_t)p * V + x] = (int32_t)yb;
 }
 
+// Exact Hermiticity of the stencil operator, A_q(x + delta_p) = A_p(x)^dagger
+// for the partner q of every point p (delta_q = -delta_p): one block per
+// (site, point); a mismatch sets bad[0] for a hop pair, bad[1] for the self
+// term (p = q = 0).
+__global__ void k_herm_check(const double2* __restrict__ A, const int32_t* __restrict__ nbr_fwd,
+                             const int8_t* __restrict__ partner, int64_t V, int npts, int nb,
+                             int* bad) {
+  const int64_t x = blockIdx.x;
+  const int p = blockIdx.y;
+  const int q = partner[p];
+  const int64_t y = nbr_fwd[(int64_t)p * V + x];
+  const double2* Ap = A + (x * npts + p) * (int64_t)nb * nb;
+  const double2* Aq = A + (y * npts + q) * (int64_t)nb * nb;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int a = e / nb, b = e % nb;
+    const double2 u = Ap[a * nb + b], v = Aq[b * nb + a];
+    if (u.x != v.x || u.y != -v.y) atomicExch(&bad[p == 0 ? 1 : 0], 1);
+  }
+}
+
 __global__ void k_to_c64(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -211,6 +231,50 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
     }
     { k_to_c64<<<num_sms() * 8, 256, 0, s>>>((const double2*)A, op->a32, (int64_t)nA); ::mrhs::count_launch(); }
   }
+  // Hermitian stencil operators let the tensor-core kernel read one tile per
+  // pair of points (p, -p): detect exact Hermiticity once
+  {
+    int8_t partner[MRHS_MAX_PTS];
+    bool paired = true;
+    for (int p = 0; p < npts && paired; ++p) {
+      partner[p] = -1;
+      for (int q = 0; q < npts; ++q)
+        if (disp[4 * q] == -disp[4 * p] && disp[4 * q + 1] == -disp[4 * p + 1] &&
+            disp[4 * q + 2] == -disp[4 * p + 2] && disp[4 * q + 3] == -disp[4 * p + 3])
+          partner[p] = (int8_t)q;
+      paired = partner[p] >= 0;
+    }
+    if (paired) {
+      int8_t* d_partner = nullptr;
+      int* d_bad = nullptr;
+      int bad[2] = {1, 1};
+      if (cudaMalloc(&d_partner, (size_t)npts) == cudaSuccess &&
+          cudaMalloc(&d_bad, 2 * sizeof(int)) == cudaSuccess &&
+          cudaMemcpyAsync(d_partner, partner, (size_t)npts, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+          cudaMemsetAsync(d_bad, 0, 2 * sizeof(int), s) == cudaSuccess) {
+        dim3 grid((unsigned)V, (unsigned)npts);
+        { k_herm_check<<<grid, 128, 0, s>>>((const double2*)A, op->nbr_fwd, d_partner, V, npts,
+                                            nb, d_bad); ::mrhs::count_launch(); }
+        if (cudaMemcpyAsync(bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          bad[0] = bad[1] = 1;
+      }
+      cudaGetLastError();
+      cudaFree(d_partner);
+      cudaFree(d_bad);
+      // pairing needs the hop pairs only; H^dagger = H also the self term
+      op->pairable = bad[0] == 0;
+      op->herm = bad[0] == 0 && bad[1] == 0;
+      // the points with a positive first nonzero displacement, one of each pair
+      op->herm_nf = 0;
+      for (int p = 1; p < npts; ++p) {
+        int first = 0;
+        for (int mu = 0; mu < 4 && first == 0; ++mu) first = disp[4 * p + mu];
+        if (first > 0) op->herm_f[op->herm_nf++] = (int8_t)p;
+      }
+      op->herm_on = false;     // opt-in: see mrhs_op_hermitian
+    }
+  }
   for (int prec = MRHS_PREC_BF16; prec <= MRHS_PREC_TC32; ++prec)
     if (prec_mask & MRHS_PREC_BIT(prec)) {
       int st = tc_build(op, prec, false, (const double2*)A, s);
@@ -240,6 +304,17 @@ int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, voi
   if (!lam || iters < 1) return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_lambda_max: arguments");
   MRHS_TRY(lambda_max(op, prec, iters, (cudaStream_t)stream, lam));
   op->lam_max[prec] = *lam;
+  return MRHS_OK;
+}
+
+int mrhs_op_hermitian(mrhs_op op, int32_t mode, int32_t* active) {
+  MRHS_TRY(check_op(op));
+  if (mode < -1 || mode > 1) return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_hermitian: mode -1, 0 or 1");
+  if (mode == 1 && !op->pairable)
+    return fail(MRHS_ERR_UNSUPPORTED,
+                "hop pairs of the operator are not exactly Hermitian on a symmetric stencil");
+  if (mode >= 0) op->herm_on = mode == 1;
+  if (active) *active = op->herm_on ? 1 : 0;
   return MRHS_OK;
 }
 

@@ -130,6 +130,11 @@ struct mrhs_op_s {
   mrhs::Workspace ws_solve;     // block CG vectors and state
   mrhs::KernelTimer timer[MRHS_NUM_PREC];   // per precision
   double lam_max[MRHS_NUM_PREC] = {};   // cached power-method estimates
+  bool herm = false;                 // A_q(x + delta_p) = A_p(x)^dagger exactly (q: -p), all p
+  bool pairable = false;             // the same for every hop pair (p != 0)
+  bool herm_on = false;              // tensor-core kernel reads one tile per point pair
+  int32_t herm_nf = 0;               // points with a positive first displacement
+  int8_t herm_f[MRHS_MAX_PTS / 2];   // ... their indices
   mrhs::TcTune tc_tune;              // tensor-core launch shape
   bool tc_set = false;               // tc_tune set explicitly
 };

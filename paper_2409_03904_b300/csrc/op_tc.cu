@@ -158,11 +158,49 @@ int image_index(int prec) {
 // One CTA per site: d_x, s_x and the codes of the site's coefficient tiles.
 // dag: the block of stencil point p at site x is A_p(x - delta_p)^dagger.
 // ASPLIT: each point gets a hi tile followed by a lo tile.
+// Largest |Re|, |Im| of the coefficients over all sites, the mean real
+// diagonal of each site's self block removed as in k_pack_coef (double bits,
+// ordered like the values): the one scale of an image whose tiles are shared
+// between sites (Hermitian pairing).
+__global__ void __launch_bounds__(256) k_coef_gmax(const double2* __restrict__ A, int64_t V,
+                                                   int npts, int nb,
+                                                   unsigned long long* gmax) {
+  const int64_t x = blockIdx.x;
+  if (x >= V) return;
+  __shared__ double s_red[256];
+  const double2* Ax = A + x * npts * (int64_t)nb * nb;
+  double acc = 0.0;
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) acc += Ax[a * nb + a].x;
+  s_red[threadIdx.x] = acc;
+  __syncthreads();
+  __shared__ float s_d;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += s_red[i];
+    s_d = __double2float_rn(t / nb);
+  }
+  __syncthreads();
+  const double d = (double)s_d;
+  const int nn = nb * nb;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < npts * nn; i += blockDim.x) {
+    double2 v = Ax[i];
+    if (i < nn && (i / nb) == (i % nb)) v.x -= d;
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  atomicMax(gmax, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_coef_gscale(const unsigned long long* gmax, double* gscale) {
+  *gscale = pow2_ceil(__longlong_as_double((long long)*gmax));
+}
+
 template <bool BF16, bool ASPLIT>
 __global__ void __launch_bounds__(256) k_pack_coef(const double2* __restrict__ A, uint8_t* codes,
                                                    float* scale, float* diag,
                                                    const int32_t* __restrict__ nbr_bwd, int64_t V,
-                                                   int npts, int nb, Geom g, int dag) {
+                                                   int npts, int nb, Geom g, int dag,
+                                                   const double* __restrict__ gscale) {
   const int64_t x = blockIdx.x;
   if (x >= V) return;
   __shared__ double s_red[256];
@@ -199,7 +237,7 @@ __global__ void __launch_bounds__(256) k_pack_coef(const double2* __restrict__ A
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < (int)blockDim.x; ++i) t = fmax(t, s_red[i]);
-    s_scale = pow2_ceil(t);
+    s_scale = gscale ? *gscale : pow2_ceil(t);   // one scale for all sites, or the site's own
     scale[x] = (float)s_scale;
     diag[x] = s_d;
   }
@@ -374,6 +412,14 @@ struct ProbDesc {
   const float* Tp;
   float* P;
   unsigned* colmax_next;
+  // Hermitian pairing (herm != 0): one stage per pair (p, -p) of the nf
+  // points fpts[] plus the self term; sites visited in blocks bl[4]; the
+  // partner tile A_p(x - delta_p) is read transposed (idesc_t: Re half,
+  // idesc_tn: Im half negated) to give A_{-p}(x) = A_p(x - delta_p)^dagger
+  int32_t herm, nf;
+  int32_t bl[4];
+  uint32_t idesc_t, idesc_tn;
+  int8_t fpts[MRHS_MAX_PTS / 2];
   Stencil st;
 };
 
@@ -392,6 +438,33 @@ __device__ __forceinline__ int find_prob(const Batch& bt, int64_t t) {
     if (t >= bt.p[i].item0) k = i;
   return k;
 }
+// Site of a problem's i-th work item: linear order, or (paired mode) blocks
+// of bl[0] x .. x bl[3] sites, so that the sites in flight together are
+// neighbours and share their coefficient tiles through L2.
+__device__ __forceinline__ int64_t site_of(const ProbDesc& pd, int64_t i) {
+  if (!pd.herm) return i;
+  const int b0 = pd.bl[0], b1 = pd.bl[1], b2 = pd.bl[2], b3 = pd.bl[3];
+  const int64_t bvol = (int64_t)b0 * b1 * b2 * b3;
+  int64_t blk = i / bvol;
+  int in = (int)(i - blk * bvol);
+  const int c0 = in % b0;
+  in /= b0;
+  const int c1 = in % b1;
+  in /= b1;
+  const int c2 = in % b2;
+  const int c3 = in / b2;
+  const int n0 = pd.st.L[0] / b0, n1 = pd.st.L[1] / b1, n2 = pd.st.L[2] / b2;
+  const int q0 = (int)(blk % n0);
+  blk /= n0;
+  const int q1 = (int)(blk % n1);
+  blk /= n1;
+  const int q2 = (int)(blk % n2);
+  const int q3 = (int)(blk / n2);
+  (void)b3;
+  const int64_t x0 = q0 * b0 + c0, x1 = q1 * b1 + c1, x2 = q2 * b2 + c2, x3 = q3 * b3 + c3;
+  return x0 + pd.st.L[0] * (x1 + (int64_t)pd.st.L[1] * (x2 + (int64_t)pd.st.L[2] * x3));
+}
+
 __device__ __forceinline__ bool item_live(const Batch& bt, int k) {
   return bt.active == nullptr || bt.active[k] != 0;
 }
@@ -443,6 +516,7 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
     if (lane == 0) {
       // ---------------- producer
       const uint64_t pol_stream = ptx::policy_evict_first();
+      const uint64_t pol_shared = ptx::policy_evict_normal();
       const uint64_t pol_keep = ptx::policy_evict_last();
       int s = 0;
       uint32_t ph = 0;
@@ -454,7 +528,7 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
         // the problem's fields in registers: the waits and copies below
         // clobber memory, and would otherwise reload them from the parameters
         const ProbDesc& pd = bt.p[k];
-        const int64_t x = t - pd.item0;
+        const int64_t x = site_of(pd, t - pd.item0);
         const uint8_t* coef = pd.coef;
         const uint8_t* xbp = pd.xb;
         const int npts = pd.npts, pps = pd.pps, sign = pd.st.sign;
@@ -469,6 +543,50 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
             c[mu] = (int)(r % Lm[mu]);
             r /= Lm[mu];
           }
+        }
+        if (pd.herm) {
+          // one stage per pair (p, -p): A_p(x) and X(x + delta_p), the
+          // partner tile A_p(x - delta_p) and X(x - delta_p); the self term
+          // first.  Tiles are left in L2 for the neighbour that shares them.
+          const int nf = pd.nf;
+          for (int j = 0; j <= nf && ok; ++j) {
+            if (!ptx::mbar_wait(&empty[s], ph ^ 1u, &s_abort)) { ok = false; break; }
+            uint8_t* st_smem = stages + (size_t)s * stage_bytes;
+            if (j == 0) {
+              ptx::mbar_arrive_expect_tx(&full[s], cbytes + xbytes);
+              ptx::bulk_g2s(st_smem, coef + (uint64_t)x * npts * cbytes, cbytes, &full[s],
+                            pol_shared);
+              ptx::bulk_g2s(st_smem + xb_off, xbp + (uint64_t)x * xbytes, xbytes, &full[s],
+                            pol_shared);
+            } else {
+              const int p = pd.fpts[j - 1];
+              const uint32_t dw = dwords[p];
+              int64_t yf = 0, yb = 0;
+#pragma unroll
+              for (int mu = 3; mu >= 0; --mu) {
+                const int d = (int)(int8_t)(dw >> (8 * mu));
+                int vf = c[mu] + d, vb = c[mu] - d;
+                vf += (vf < 0) ? Lm[mu] : 0;
+                vf -= (vf >= Lm[mu]) ? Lm[mu] : 0;
+                vb += (vb < 0) ? Lm[mu] : 0;
+                vb -= (vb >= Lm[mu]) ? Lm[mu] : 0;
+                yf = yf * Lm[mu] + vf;
+                yb = yb * Lm[mu] + vb;
+              }
+              ptx::mbar_arrive_expect_tx(&full[s], 2u * (cbytes + xbytes));
+              ptx::bulk_g2s(st_smem, coef + ((uint64_t)x * npts + p) * cbytes, cbytes, &full[s],
+                            pol_shared);
+              ptx::bulk_g2s(st_smem + cbytes, coef + ((uint64_t)yb * npts + p) * cbytes, cbytes,
+                            &full[s], pol_shared);
+              ptx::bulk_g2s(st_smem + xb_off, xbp + (uint64_t)yf * xbytes, xbytes, &full[s],
+                            pol_shared);
+              ptx::bulk_g2s(st_smem + xb_off + xbytes, xbp + (uint64_t)yb * xbytes, xbytes,
+                            &full[s], pol_shared);
+            }
+            ++issued;
+            if (++s == nstages) { s = 0; ph ^= 1u; }
+          }
+          continue;
         }
         for (int p0 = 0; p0 < npts; p0 += pps) {
           const int np = (npts - p0) < pps ? (npts - p0) : pps;
@@ -524,6 +642,55 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
         if (!ptx::mbar_wait(&acc_empty[acc], aph ^ 1u, &s_abort)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t tmem_d = tmem_base + (uint32_t)(acc * kAccStride);
+        if (pd.herm) {
+          // stage j: forward A_p(x) X(x + delta_p) as usual, then the partner
+          // tile read transposed: its Re half into the Re-A columns, its Im
+          // half negated into the Im-A columns, giving A_p(x - delta_p)^dagger
+          // X(x - delta_p) in the same accumulator
+          const int nf = pd.nf;
+          const uint32_t idesc_t = pd.idesc_t, idesc_tn = pd.idesc_tn;
+          const uint32_t im_row = (uint32_t)(pd.nbp8 / 8) * sbo;   // Im half: row nb8
+          const uint32_t im_col = (uint32_t)pd.nbp8;                // TMEM columns of the Im half
+          for (int j = 0; j <= nf && ok; ++j) {
+            if (!ptx::mbar_wait(&full[s], ph, &s_abort)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t sb = ptx::smem_u32(stages + (size_t)s * stage_bytes);
+            const uint32_t ab = sb + xb_off;
+            for (int kk = 0; kk < nk; ++kk) {
+              const uint32_t accum = (j > 0 || kk > 0) ? 1u : 0u;
+              const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)kk * 256u, 128u, sbo);
+              ptx::mma_f16(tmem_d, adesc, ptx::smem_desc(sb + (uint32_t)kk * 256u, 128u, sbo),
+                           idesc, accum);
+              if (ASPLIT)
+                ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc,
+                             ptx::smem_desc(sb + coef1 + (uint32_t)kk * 256u, 128u, sbo), idesc,
+                             accum);
+            }
+            if (j > 0) {
+              const uint32_t cbk = sb + cbytes, abk = ab + xbytes;
+              for (int kk = 0; kk < nk; ++kk) {
+                const uint64_t adesc = ptx::smem_desc(abk + (uint32_t)kk * 256u, 128u, sbo);
+                const uint32_t rows = (uint32_t)kk * 2u * sbo;      // tile rows 16 kk ..
+                ptx::mma_f16(tmem_d, adesc, ptx::smem_desc(cbk + rows, sbo, 128u), idesc_t, 1u);
+                ptx::mma_f16(tmem_d + im_col, adesc, ptx::smem_desc(cbk + im_row + rows, sbo, 128u),
+                             idesc_tn, 1u);
+                if (ASPLIT) {
+                  ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc,
+                               ptx::smem_desc(cbk + coef1 + rows, sbo, 128u), idesc_t, 1u);
+                  ptx::mma_f16(tmem_d + (uint32_t)kAccCols + im_col, adesc,
+                               ptx::smem_desc(cbk + coef1 + im_row + rows, sbo, 128u), idesc_tn,
+                               1u);
+                }
+              }
+            }
+            ptx::mma_commit(&empty[s]);
+            if (++s == nstages) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          ptx::mma_commit(&acc_full[acc]);
+          if (++acc == 2) { acc = 0; aph ^= 1u; }
+          continue;
+        }
         for (int p0 = 0; p0 < npts; p0 += pps) {
           const int np = (npts - p0) < pps ? (npts - p0) : pps;
           if (!ptx::mbar_wait(&full[s], ph, &s_abort)) { ok = false; break; }
@@ -570,7 +737,7 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
       const int k = find_prob(bt, t);
       if (!item_live(bt, k)) continue;
       const ProbDesc& pd = bt.p[k];
-      const int64_t x = t - pd.item0;
+      const int64_t x = site_of(pd, t - pd.item0);
       const int R = pd.R, nb = pd.nb, nbp8 = pd.nbp8, rb = pd.rb;
       const float2* Xp = reinterpret_cast<const float2*>(pd.X);
       float2* Yp = reinterpret_cast<float2*>(pd.Y);
@@ -777,6 +944,7 @@ constexpr size_t kXpackHead = 1024;
 int prepare(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs, int pps_req,
             cudaStream_t s, ProbDesc* pd, PackProb* pk, Geom* gout) {
   const int i = image_index(prec);
+  if (dag && op->herm) dag = false;      // H^dagger = H exactly: the forward image serves
   if (dag && !op->tc_dag[i].codes) {
     if (!op->a64) return fail(MRHS_ERR_UNSUPPORTED, "daggered low-precision image needs FP64 coefficients");
     MRHS_TRY(tc_build(op, prec, true, op->a64, s));
@@ -820,6 +988,20 @@ int prepare(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
   pd->xb_bytes = g.xb_bytes;
   pd->sbo = g.sbo;
   pd->idesc = ptx::idesc_f16(kM, g.n_mma, prec == MRHS_PREC_BF16);
+  // Hermitian pairing: exact Hermiticity checked at creation, tiles whose
+  // row and column extents agree (nb a multiple of 16), one pair per stage
+  pd->herm = (!dag && op->herm_on && op->nb % 16 == 0 && op->herm_nf > 0) ? 1 : 0;
+  pd->nf = op->herm_nf;
+  for (int j = 0; j < op->herm_nf; ++j) pd->fpts[j] = op->herm_f[j];
+  for (int mu = 0; mu < 4; ++mu) {     // visiting blocks: largest divisor of L <= 4
+    int b = 1;
+    for (int c = 4; c >= 1; --c)
+      if (op->L[mu] % c == 0) { b = c; break; }
+    pd->bl[mu] = b;
+  }
+  pd->idesc_t = ptx::idesc_f16(kM, op->nb, prec == MRHS_PREC_BF16) | (1u << 16);
+  pd->idesc_tn = pd->idesc_t | (1u << 14);
+  if (pd->herm) pd->pps = 2;           // a stage holds two tiles and two inputs
   pd->cheb = 0;
   pd->ca = pd->cb = pd->cc = pd->c0 = 0.f;
   pd->Tout = nullptr;
@@ -870,8 +1052,8 @@ int run_batch(Batch& bt, Geom* geoms, int prec, const TcTune& tune, bool tune_se
     if (plan_ring(geoms, pps, npts, bt.n, kSmemBudget / (size_t)ctas, max_stages, &ring, xb_off) >= 2)
       break;
     bool shrunk = false;
-    for (int i = 0; i < bt.n; ++i)
-      if (pps[i] > 1) { pps[i] = (pps[i] + 1) / 2; shrunk = true; }
+    for (int i = 0; i < bt.n; ++i)       // a paired problem keeps its two tiles per stage
+      if (pps[i] > 1 && !bt.p[i].herm) { pps[i] = (pps[i] + 1) / 2; shrunk = true; }
     if (!shrunk) {
       if (ctas == 1) return fail(MRHS_ERR_UNSUPPORTED, "tensor-core ring does not fit");
       ctas = 1;
@@ -879,6 +1061,10 @@ int run_batch(Batch& bt, Geom* geoms, int prec, const TcTune& tune, bool tune_se
     }
   }
   for (int i = 0; i < bt.n; ++i) {
+    if (bt.p[i].herm) {                // plan_ring may have grown pps to fill the stage
+      pps[i] = 2;
+      xb_off[i] = 2u * geoms[i].coef_bytes;
+    }
     bt.p[i].pps = pps[i];
     bt.p[i].xb_off = xb_off[i];
   }
@@ -929,18 +1115,35 @@ int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s
     return fail(MRHS_ERR_NO_MEMORY, "tensor-core coefficient image");
   }
   const unsigned grid = (unsigned)op->V;
+  // a Hermitian operator's tiles serve two sites (pairing): one scale for all
+  double* gscale = nullptr;
+  unsigned long long* gmax = nullptr;
+  if (op->pairable && !dag) {
+    if (cudaMalloc(&gmax, sizeof(unsigned long long) + sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MRHS_ERR_NO_MEMORY, "coefficient scale");
+    }
+    gscale = (double*)(gmax + 1);
+    MRHS_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned long long), s));
+    { k_coef_gmax<<<grid, 256, 0, s>>>(A, op->V, op->npts, op->nb, gmax); ::mrhs::count_launch(); }
+    { k_coef_gscale<<<1, 1, 0, s>>>(gmax, gscale); ::mrhs::count_launch(); }
+  }
   if (i == 0)
     { k_pack_coef<true, false><<<grid, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
                                                      op->nbr_bwd, op->V, op->npts, op->nb, g,
-                                                     dag ? 1 : 0); ::mrhs::count_launch(); }
+                                                     dag ? 1 : 0, gscale); ::mrhs::count_launch(); }
   else if (i == 1)
     { k_pack_coef<false, false><<<grid, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
                                                       op->nbr_bwd, op->V, op->npts, op->nb, g,
-                                                      dag ? 1 : 0); ::mrhs::count_launch(); }
+                                                      dag ? 1 : 0, gscale); ::mrhs::count_launch(); }
   else
     { k_pack_coef<false, true><<<grid, 256, 0, s>>>(A, (uint8_t*)img.codes, img.scale, img.diag,
                                                      op->nbr_bwd, op->V, op->npts, op->nb, g,
-                                                     dag ? 1 : 0); ::mrhs::count_launch(); }
+                                                     dag ? 1 : 0, gscale); ::mrhs::count_launch(); }
+  if (gmax) {
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(gmax);
+  }
   MRHS_CUDA_TRY(cudaGetLastError());
   return MRHS_OK;
 }

@@ -53,8 +53,11 @@ __global__ void k_gen_op(double2* A, int64_t V, int nb, int npts, int L0, int L1
     if (first == 0) {
       double2 g1 = cnormal((uint32_t)(a * nb + b), (uint32_t)x, 0u, 2u, seed);
       double2 g2 = cnormal((uint32_t)(b * nb + a), (uint32_t)x, 0u, 2u, seed);
-      g1.x *= inv; g1.y *= inv; g2.x *= inv; g2.y *= inv;
-      v = make_double2(0.5 * (g1.x + g2.x), 0.5 * (g1.y - g2.y));
+      // explicit roundings: a contracted multiply-add would round the [a][b]
+      // and [b][a] entries differently and break exact Hermiticity
+      g1.x = __dmul_rn(g1.x, inv); g1.y = __dmul_rn(g1.y, inv);
+      g2.x = __dmul_rn(g2.x, inv); g2.y = __dmul_rn(g2.y, inv);
+      v = make_double2(0.5 * __dadd_rn(g1.x, g2.x), 0.5 * __dsub_rn(g1.y, g2.y));
       if (a == b) v.x += shift;
     } else if (first > 0) {
       v = cnormal((uint32_t)(a * nb + b), (uint32_t)x, (uint32_t)p, 1u, seed);
