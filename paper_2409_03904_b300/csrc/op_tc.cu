@@ -659,8 +659,8 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
             for (int kk = 0; kk < nk; ++kk) {
               const uint32_t accum = (j > 0 || kk > 0) ? 1u : 0u;
               const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)kk * 256u, 128u, sbo);
-              ptx::mma_f16(tmem_d, adesc, ptx::smem_desc(sb + (uint32_t)kk * 256u, 128u, sbo),
-                           idesc, accum);
+              const uint64_t bhi = ptx::smem_desc(sb + (uint32_t)kk * 256u, 128u, sbo);
+              ptx::mma_f16(tmem_d, adesc, bhi, idesc, accum);
               if (ASPLIT)
                 ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc,
                              ptx::smem_desc(sb + coef1 + (uint32_t)kk * 256u, 128u, sbo), idesc,
@@ -671,6 +671,8 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
               for (int kk = 0; kk < nk; ++kk) {
                 const uint64_t adesc = ptx::smem_desc(abk + (uint32_t)kk * 256u, 128u, sbo);
                 const uint32_t rows = (uint32_t)kk * 2u * sbo;      // tile rows 16 kk ..
+                // (the collector buffer is not used here: reusing the input
+                // operand across these transposed, negated MMAs gave wrong sums)
                 ptx::mma_f16(tmem_d, adesc, ptx::smem_desc(cbk + rows, sbo, 128u), idesc_t, 1u);
                 ptx::mma_f16(tmem_d + im_col, adesc, ptx::smem_desc(cbk + im_row + rows, sbo, 128u),
                              idesc_tn, 1u);
@@ -703,12 +705,15 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
             for (int j = 0; j < nk; ++j) {
               const uint32_t accum = (first || j > 0) ? 1u : 0u;
               const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)j * 256u, 128u, sbo);
-              ptx::mma_f16(tmem_d, adesc, ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, sbo),
-                           idesc, accum);
-              if (ASPLIT)
-                ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc,
-                             ptx::smem_desc(cb + coef1 + (uint32_t)j * 256u, 128u, sbo), idesc,
-                             accum);
+              const uint64_t bhi = ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, sbo);
+              if (ASPLIT) {    // hi and lo coefficient tiles share the input operand
+                ptx::mma_f16_coll<ptx::CollA::fill>(tmem_d, adesc, bhi, idesc, accum);
+                ptx::mma_f16_coll<ptx::CollA::lastuse>(
+                    tmem_d + (uint32_t)kAccCols, adesc,
+                    ptx::smem_desc(cb + coef1 + (uint32_t)j * 256u, 128u, sbo), idesc, accum);
+              } else {
+                ptx::mma_f16(tmem_d, adesc, bhi, idesc, accum);
+              }
             }
           }
           ptx::mma_commit(&empty[s]);
