@@ -72,6 +72,24 @@ constexpr size_t kSmemBudget = 220 * 1024;
 constexpr int kMaxStages = 16;
 constexpr size_t kSmemOneCta = 120 * 1024;
 
+// One MMA of a stage: input window w (digit blocks w, w + 1), coefficient
+// digit sd, accumulator acc (levels 2 acc + 2 and 2 acc + 3 = w + sd and
+// w + sd + 1); first: the accumulator's first MMA of a site; coll: 0 alone,
+// 1 fill, 2 use, 3 lastuse of the A collector.  Ordered by window.
+struct OzMma {
+  int8_t w, sd, acc, first, coll;
+};
+constexpr int kOzMmas = 19;
+__device__ __constant__ const OzMma kOzOrder[kOzMmas] = {
+    {0, 2, 0, 1, 1}, {0, 4, 1, 1, 2}, {0, 6, 2, 1, 3},
+    {1, 1, 0, 0, 1}, {1, 3, 1, 0, 2}, {1, 5, 2, 0, 2}, {1, 7, 3, 1, 3},
+    {2, 2, 1, 0, 1}, {2, 4, 2, 0, 2}, {2, 6, 3, 0, 3},
+    {3, 1, 1, 0, 1}, {3, 3, 2, 0, 2}, {3, 5, 3, 0, 3},
+    {4, 2, 2, 0, 1}, {4, 4, 3, 0, 3},
+    {5, 1, 2, 0, 1}, {5, 3, 3, 0, 3},
+    {6, 2, 3, 0, 0},
+    {7, 1, 3, 0, 0}};
+
 struct OzGeom {
   int nb, nbp8, N, K, nk;   // N = 2 nb8 (MMA N), K = nb16, nk = K / 16
   int R, rb;
@@ -445,16 +463,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sa = ptx::smem_u32(stages + (size_t)s * stage_bytes);
             const uint32_t sz = sa + aslab;           // X_0, then X_1..X_7
             const bool first = p == 0 && j == 0;
+            // the 19 MMAs grouped by input window [X_w ; X_(w+1)]: those of one
+            // window share the A operand through the tensor core's collector,
+            // so shared memory serves 8 window reads instead of 19
 #pragma unroll
-            for (int a = 0; a < kNumAcc; ++a) {
-              const int c = 2 * a + 2;                // lower level of accumulator a
-              const int smax = c < kDigits ? c : kDigits;
-              for (int sd = 1; sd <= smax; ++sd) {
-                const uint64_t adesc = ptx::smem_desc(sz + (uint32_t)(c - sd) * zb, 128u, 256u);
-                const uint64_t bdesc = ptx::smem_desc(sa + (uint32_t)(sd - 1) * aslice, 128u, 256u);
-                ptx::mma_f16(tmem_base + (uint32_t)(a * kAccCols), adesc, bdesc, idesc,
-                             (first && sd == 1) ? 0u : 1u);
-              }
+            for (int m = 0; m < kOzMmas; ++m) {
+              const OzMma& q = kOzOrder[m];
+              const uint64_t adesc = ptx::smem_desc(sz + (uint32_t)q.w * zb, 128u, 256u);
+              const uint64_t bdesc = ptx::smem_desc(sa + (uint32_t)(q.sd - 1) * aslice, 128u, 256u);
+              const uint32_t td = tmem_base + (uint32_t)(q.acc * kAccCols);
+              const uint32_t accum = (first && q.first) ? 0u : 1u;
+              if (q.coll == 0) ptx::mma_f16(td, adesc, bdesc, idesc, accum);
+              else if (q.coll == 1) ptx::mma_f16_coll<ptx::CollA::fill>(td, adesc, bdesc, idesc, accum);
+              else if (q.coll == 2) ptx::mma_f16_coll<ptx::CollA::use>(td, adesc, bdesc, idesc, accum);
+              else ptx::mma_f16_coll<ptx::CollA::lastuse>(td, adesc, bdesc, idesc, accum);
             }
             ptx::mma_commit(&empty[s]);
             if (++s == nstages) { s = 0; ph ^= 1u; }
