@@ -397,13 +397,15 @@ int mrhs_op_kernel_timing(mrhs_op op, int32_t enable);
  * one coefficient tile per pair of points: the tile of (x, p) serves site x
  * directly and site x + delta_p transposed and conjugated, the second read
  * coming from L2 when both sites are in flight.  Sites are visited in 4D
- * blocks for that.  mode -1 queries, 0 disables, 1 enables (MRHS_ERR_UNSUPPORTED
- * if the hop pairs are not exactly Hermitian); *active (may be null) receives
- * the state after the call.  Off by default: at 12^4, nb 48, 32 RHS the
- * shared reads cut DRAM traffic by 10% (FP16X) and 4% (TC32) only, and the
- * second, transposed use costs two MMAs (N = nb) per K step that re-read the
- * input tile, so neither form gets faster.  Results equal the unpaired
- * kernel's up to FP32 summation order. */
+ * blocks for that.  mode -1 queries, 0 disables, 1 enables for every
+ * tensor-core form, 2 for TC32 only (MRHS_ERR_UNSUPPORTED if the hop pairs are
+ * not exactly Hermitian); *active (may be null) receives the mode after the
+ * call.  Default 0.  At 12^4, nb 48, 32 RHS the shared reads cut DRAM
+ * traffic by 10% (FP16X) and 4% (TC32); the second, transposed use costs two
+ * MMAs (N = nb) per K step that re-read the input tile.  FP16X gets slower
+ * (2.82 against 2.66 ms); TC32 is 8-15% faster when timed alone but slower
+ * inside the mixed solve (6.85 against 5.7 ms per launch).  Results equal
+ * the unpaired kernel's up to FP32 summation order. */
 int mrhs_op_hermitian(mrhs_op op, int32_t mode, int32_t* active);
 
 /* Launch shape of this operator's BF16/FP16 tensor-core kernel (the knobs an

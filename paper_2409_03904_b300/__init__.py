@@ -128,14 +128,15 @@ class CoarseOp:
                                                  ctypes.byref(lam), _lib.stream_ptr()))
         return float(lam.value)
 
-    def hermitian(self, enable=None):
+    def hermitian(self, mode=None):
         """Hermitian pairing of the tensor-core kernels (one coefficient tile
-        per point pair, see mrhs_op_hermitian): None queries, True/False
-        enables/disables; returns whether it is active."""
+        per point pair, see mrhs_op_hermitian): None queries; 0 / False off,
+        1 / True every tensor-core form, 2 TC32 only; off by default.
+        Returns the mode after the call."""
         act = ctypes.c_int32()
-        mode = -1 if enable is None else (1 if enable else 0)
-        _lib.check(_lib.lib().mrhs_op_hermitian(self._h, mode, ctypes.byref(act)))
-        return bool(act.value)
+        m = -1 if mode is None else int(mode)
+        _lib.check(_lib.lib().mrhs_op_hermitian(self._h, m, ctypes.byref(act)))
+        return int(act.value)
 
     def tc_tune(self, pts_per_stage=0, ctas_per_sm=1, max_stages=32):
         """Launch shape of the BF16/FP16 tensor-core kernel (0 = default)."""

@@ -272,7 +272,7 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
         for (int mu = 0; mu < 4 && first == 0; ++mu) first = disp[4 * p + mu];
         if (first > 0) op->herm_f[op->herm_nf++] = (int8_t)p;
       }
-      op->herm_on = false;     // opt-in: see mrhs_op_hermitian
+      op->herm_mode = 0;       // opt-in: see mrhs_op_hermitian
     }
   }
   for (int prec = MRHS_PREC_BF16; prec <= MRHS_PREC_TC32; ++prec)
@@ -309,12 +309,13 @@ int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, voi
 
 int mrhs_op_hermitian(mrhs_op op, int32_t mode, int32_t* active) {
   MRHS_TRY(check_op(op));
-  if (mode < -1 || mode > 1) return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_hermitian: mode -1, 0 or 1");
-  if (mode == 1 && !op->pairable)
+  if (mode < -1 || mode > 2)
+    return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_hermitian: mode -1, 0, 1 or 2");
+  if (mode >= 1 && !op->pairable)
     return fail(MRHS_ERR_UNSUPPORTED,
                 "hop pairs of the operator are not exactly Hermitian on a symmetric stencil");
-  if (mode >= 0) op->herm_on = mode == 1;
-  if (active) *active = op->herm_on ? 1 : 0;
+  if (mode >= 0) op->herm_mode = (int8_t)mode;
+  if (active) *active = op->herm_mode;
   return MRHS_OK;
 }
 

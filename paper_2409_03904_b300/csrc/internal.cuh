@@ -132,7 +132,8 @@ struct mrhs_op_s {
   double lam_max[MRHS_NUM_PREC] = {};   // cached power-method estimates
   bool herm = false;                 // A_q(x + delta_p) = A_p(x)^dagger exactly (q: -p), all p
   bool pairable = false;             // the same for every hop pair (p != 0)
-  bool herm_on = false;              // tensor-core kernel reads one tile per point pair
+  int8_t herm_mode = 0;              // point-pair tile reading: 0 off (default), 1 all
+                                     // tensor-core forms, 2 TC32 only
   int32_t herm_nf = 0;               // points with a positive first displacement
   int8_t herm_f[MRHS_MAX_PTS / 2];   // ... their indices
   mrhs::TcTune tc_tune;              // tensor-core launch shape

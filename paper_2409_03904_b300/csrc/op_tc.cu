@@ -995,7 +995,9 @@ int prepare(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nrhs,
   pd->idesc = ptx::idesc_f16(kM, g.n_mma, prec == MRHS_PREC_BF16);
   // Hermitian pairing: exact Hermiticity checked at creation, tiles whose
   // row and column extents agree (nb a multiple of 16), one pair per stage
-  pd->herm = (!dag && op->herm_on && op->nb % 16 == 0 && op->herm_nf > 0) ? 1 : 0;
+  const bool pair_here =
+      op->herm_mode == 1 || (op->herm_mode == 2 && prec == MRHS_PREC_TC32);
+  pd->herm = (!dag && pair_here && op->nb % 16 == 0 && op->herm_nf > 0) ? 1 : 0;
   pd->nf = op->herm_nf;
   for (int j = 0; j < op->herm_nf; ++j) pd->fpts[j] = op->herm_f[j];
   for (int mu = 0; mu < 4; ++mu) {     // visiting blocks: largest divisor of L <= 4

@@ -45,18 +45,18 @@ def test_paired_equals_unpaired_and_oracle(mrhs, kind, L, nb, npts, R):
     A = coarse_op(L, nb, npts, 9090 + nb, 12.0)
     X = vectors(L, nb, R, 9091).astype(np.complex64)
     op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", kind))
-    assert op.hermitian() is False              # opt-in
-    assert op.hermitian(True) is True
+    assert op.hermitian() == 0                  # opt-in
+    assert op.hermitian(1) == 1
     Yp = op.apply(dev(X), kind).cpu().numpy()
     Ypd = op.apply_dag(dev(X), kind).cpu().numpy()     # H^dagger = H: the same kernel
-    assert op.hermitian(False) is False
+    assert op.hermitian(0) == 0
     Yu = op.apply(dev(X), kind).cpu().numpy()
     ref = lowprec_apply(A, X.astype(np.complex128), L, disp, kind)
     assert rel_per_rhs(Yp, Yu) <= 2e-6
     assert rel_per_rhs(Yp, ref) <= 1e-5
     assert rel_per_rhs(Yu, ref) <= 1e-5
     assert np.array_equal(Yp, Ypd)
-    assert op.hermitian(True) is True
+    assert op.hermitian(2) == 2
     assert mrhs.device_error() == 0
 
 
@@ -67,9 +67,9 @@ def test_non_hermitian_operator_is_not_paired(mrhs):
     V = int(np.prod(L))
     A = rng.standard_normal((V, npts, nb, nb)) + 1j * rng.standard_normal((V, npts, nb, nb))
     op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp16"))
-    assert op.hermitian() is False
+    assert op.hermitian() == 0
     with pytest.raises(mrhs.MrhsError):
-        op.hermitian(True)
+        op.hermitian(1)
     X = vectors(L, nb, 4, 5).astype(np.complex64)
     Y = op.apply(dev(X), "fp16").cpu().numpy()
     assert rel_per_rhs(Y, lowprec_apply(A, X.astype(np.complex128), L, disp, "fp16")) <= 1e-5
@@ -85,7 +85,7 @@ def test_batch_with_paired_and_unpaired_problems(mrhs):
         disp, _ = stencil(npts)
         A = coarse_op(L, nb, npts, 700 + i, 12.0)
         op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp16x"))
-        op.hermitian(True)                      # nb 24 is paired in the kernel only if nb % 16 == 0
+        op.hermitian(1)                         # nb 24 is paired in the kernel only if nb % 16 == 0
         X = dev(vectors(L, nb, R, 710 + i).astype(np.complex64))
         ops.append(op)
         Xs.append(X)
@@ -101,7 +101,7 @@ def test_paired_solve_matches_fp64_oracle(mrhs):
     A = coarse_op(L, nb, npts, 4411, 18.0)
     B = vectors(L, nb, R, 4412)
     op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", "fp16x", "tc32"))
-    assert op.hermitian(True)
+    assert op.hermitian(1) == 1
     X, info = op.solve(dev(B), mode="mixed", tol=1e-9)
     assert info["status"] == 0 and max(info["resid"]) <= 1e-9
     r = B - coarse_op_apply(A, X.cpu().numpy(), L, disp)
