@@ -86,9 +86,9 @@ def parse():
     ap.add_argument("--blocks", default="4096,256,64",
                     help="n_blocks,v_block,n_basis for --blocking (nrhs from --nrhs, default 12)")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
-    ap.add_argument("--batch", default=None, choices=["config4", "small"],
+    ap.add_argument("--batch", default=None, choices=["uneven12", "small"],
                     help="batched solve of independent problems against one-at-a-time solves: "
-                         "the twelve config-4 problems, or twelve 4^4 problems")
+                         "twelve problems of uneven L, nb and nrhs, or twelve 4^4 problems")
     ap.add_argument("--cg5d", action="store_true",
                     help="one CG on the enlarged 5D system (Sec. 2.2) against FP64 block CG")
     ap.add_argument("--coarsen", default=None, metavar="LF,BLOCK,NBF,NBASIS",
@@ -551,7 +551,7 @@ def run_batch(a):
     import paper_2409_03904_b300 as mrhs
     import synth.device as sdev
     from synth import BATCH, load_shift, stencil
-    if a.batch == "config4":
+    if a.batch == "uneven12":
         probs = [(w, 0) for w in BATCH]
     else:      # the four 4^4 problems of the list, three sources each
         small = [w for w in BATCH if w["L"] == (4, 4, 4, 4)]
