@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--cheb-order", type=int, default=8)
     ap.add_argument("--cheb-ratio", type=float, default=400.0, help="hi / lo")
     ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--recycle", type=int, default=0,
+                    help="sweeps of the Galerkin start over the earlier cycles' search blocks "
+                         "(0: plain restart)")
     ap.add_argument("--check-every", type=int, default=2,
                     help="block-CG iterations between convergence checks (one graph chunk)")
     ap.add_argument("--fp64-iters", type=int, default=3,
@@ -742,7 +745,7 @@ def main():
                   krylov_prec=a.krylov,
                   cheb_order=a.cheb_order, cheb_hi=hi, cheb_lo=hi / a.cheb_ratio,
                   inner_tol=a.inner_tol, maxiter=20000, max_cycles=20,
-                  check_every=a.check_every, residual_prec=a.residual)
+                  check_every=a.check_every, residual_prec=a.residual, recycle=a.recycle)
 
     stream = torch.cuda.current_stream()
     # launch shapes of the two tensor-core forms, tuned once for this shape
@@ -880,7 +883,8 @@ def main():
                           "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
                           "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
                                      f"[{hi / a.cheb_ratio:.4g}, {hi:.4g}]",
-                          "inner_tol": a.inner_tol, "parallelism": f"replicas x{world}",
+                          "inner_tol": a.inner_tol, "recycle": a.recycle,
+                          "parallelism": f"replicas x{world}",
                           "residuals": f"{a.residual} per cycle, fp64 for the one that meets tol",
                           "launch_shapes": tuned,
                           "l2": "inputs larger than L2 (coefficients "
@@ -888,6 +892,8 @@ def main():
                "solve": {"iters": inf["iters"], "cycles": inf["cycles"], "applies": inf["applies"],
                          "cycle_iters": inf["cycle_iters"], "cycle_resid": inf["cycle_resid"],
                          "cycle_flag": inf["cycle_flag"],
+                         "recycle_blocks": inf["recycle_blocks"],
+                         "recycle_projections": inf["recycle_projections"],
                          "max_true_resid": resid, "lambda_max_est": lam, "setup_s": setup_s},
                "roofline": roof, "gpu_launches": launches, "launches_before_timed": launches0,
                "clocks": clk.summary(),

@@ -295,6 +295,27 @@ typedef struct {
                            a cycle that needs less than a tenfold reduction
                            computes its residual in FP64 directly, so the
                            residuals reported are FP64 ones */
+  int32_t recycle;      /* MIXED (block_cg_solve only): every inner iteration
+                           keeps a copy of its search block D and of
+                           N = (D^dagger H D)^-1; a new refinement cycle
+                           starts from the Galerkin correction over the
+                           blocks of all earlier cycles, E_0 = sum_i D_i N_i
+                           D_i^dagger F, taken one cycle's blocks at a time
+                           (the blocks of one cycle are H-conjugate) with
+                           F - H E_0 refreshed between cycles, `recycle`
+                           sweeps over them (0, the default: plain restarts;
+                           2 is the tested setting).  A column keeps its E_0
+                           only if that lowers the energy functional
+                           e^dagger H e - 2 Re e^dagger f below zero; blocks of
+                           iterations that lost rank are not kept; a cycle
+                           that started from kept blocks and reduced some
+                           column's residual by nothing ends the recycling
+                           for the solve.  The copies are held by the
+                           operator until mrhs_op_destroy */
+  int32_t recycle_max_blocks; /* cap on kept blocks (each N x nrhs complex64);
+                           0 (default): 128.  Fewer are kept when device
+                           memory runs short (a reserve of max(4 GiB, 1/16
+                           of the device) stays free) */
 } mrhs_solve_params;
 
 enum {
@@ -329,6 +350,8 @@ typedef struct {
   int32_t cycle_iters[MRHS_MAX_CYCLES];
   double cycle_resid[MRHS_MAX_CYCLES];
   int32_t cycle_flag[MRHS_MAX_CYCLES];
+  int32_t recycle_blocks;      /* MIXED: search blocks kept (see recycle) */
+  int32_t recycle_projections; /* MIXED: block projections of cycle starts */
 } mrhs_solve_info;
 
 /* Solve H X = B for nrhs right-hand sides with block CG (Fig. 2).

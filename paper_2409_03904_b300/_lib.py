@@ -38,7 +38,8 @@ class SolveParams(ctypes.Structure):
                 ("cheb_hi", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_cycles", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("breakdown_tau", ctypes.c_double), ("krylov_prec", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("residual_prec", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("residual_prec", ctypes.c_int32),
+                ("recycle", ctypes.c_int32), ("recycle_max_blocks", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -48,7 +49,8 @@ class SolveInfo(ctypes.Structure):
                 ("cheb_hi", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("krylov_prec", ctypes.c_int32), ("precond_prec", ctypes.c_int32),
                 ("cycle_iters", ctypes.c_int32 * 16), ("cycle_resid", ctypes.c_double * 16),
-                ("cycle_flag", ctypes.c_int32 * 16)]
+                ("cycle_flag", ctypes.c_int32 * 16), ("recycle_blocks", ctypes.c_int32),
+                ("recycle_projections", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(status=self.status, iters=self.iters, cycles=self.cycles,
@@ -58,7 +60,9 @@ class SolveInfo(ctypes.Structure):
                     krylov_prec=NAMES.get(self.krylov_prec), precond_prec=NAMES.get(self.precond_prec),
                     cycle_iters=[self.cycle_iters[c] for c in range(min(self.cycles, 16))],
                     cycle_resid=[self.cycle_resid[c] for c in range(min(self.cycles, 16))],
-                    cycle_flag=[self.cycle_flag[c] for c in range(min(self.cycles, 16))])
+                    cycle_flag=[self.cycle_flag[c] for c in range(min(self.cycles, 16))],
+                    recycle_blocks=self.recycle_blocks,
+                    recycle_projections=self.recycle_projections)
 
 
 class TuneResult(ctypes.Structure):

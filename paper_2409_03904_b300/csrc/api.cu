@@ -388,6 +388,7 @@ int mrhs_op_destroy(mrhs_op op) {
   op->ws_cheb.release();
   op->ws_small.release();
   op->ws_solve.release();
+  recycle_release(op);
   delete op;
   return MRHS_OK;
 }
@@ -602,6 +603,8 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
   if (!(p.tol > 0.0) || p.maxiter < 1) return fail(MRHS_ERR_INVALID_ARG, "tol / maxiter");
   if (p.mode != MRHS_SOLVE_FP64 && p.mode != MRHS_SOLVE_MIXED && p.mode != MRHS_SOLVE_CG5D)
     return fail(MRHS_ERR_INVALID_ARG, "mode");
+  if (p.recycle < 0 || p.recycle_max_blocks < 0)
+    return fail(MRHS_ERR_INVALID_ARG, "recycle / recycle_max_blocks must be >= 0");
   if (!(op->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)))
     return fail(MRHS_ERR_UNSUPPORTED, "block_cg_solve needs the FP64 operator");
   if (p.mode == MRHS_SOLVE_CG5D) {
@@ -789,6 +792,8 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->max_cycles = 12;
   p->check_every = 4;
   p->breakdown_tau = 1e-12;
+  p->recycle = 0;
+  p->recycle_max_blocks = 0;
 }
 
 }  // extern "C"

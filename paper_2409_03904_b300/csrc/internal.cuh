@@ -128,6 +128,15 @@ struct mrhs_op_s {
   mrhs::Workspace ws_cheb;      // Chebyshev recurrence vectors
   mrhs::Workspace ws_small;     // column scales etc.
   mrhs::Workspace ws_solve;     // block CG vectors and state
+  // search blocks kept across the mixed solve's refinement cycles (solver.cu):
+  // one device allocation of rc_slot_bytes per slot, their addresses in the
+  // device table rc_table, the matching (D^dagger H D)^-1 in ws_rcn, and the
+  // device counters rc_ctr = {next slot, block ticket, slots available}
+  std::vector<void*> rc_slots;
+  size_t rc_slot_bytes = 0;
+  void** rc_table = nullptr;
+  int32_t* rc_ctr = nullptr;
+  mrhs::Workspace ws_rcn;
   mrhs::KernelTimer timer[MRHS_NUM_PREC];   // per precision
   double lam_max[MRHS_NUM_PREC] = {};   // cached power-method estimates
   bool herm = false;                 // A_q(x + delta_p) = A_p(x)^dagger exactly (q: -p), all p
@@ -201,6 +210,7 @@ int blocking(bool project, const void* basis, const void* in, void* out, int64_t
 int coarsen(mrhs_op_s* op, const int32_t* block, const void* basis, int nbasis,
             const int8_t (*disp)[4], int npts, void* A_out, cudaStream_t s);
 int lambda_max(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam);
+void recycle_release(mrhs_op_s* op);   // frees the kept search blocks
 int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* const* X,
                 const int32_t* nrhs, const mrhs_solve_params& p, mrhs_solve_info* infos,
                 cudaStream_t s);

@@ -296,6 +296,7 @@ struct Small {           // device-resident solver state (R <= 64)
   double2 negM[64 * 64];
   double2 G[64 * 64];    // Gram workspace (filled by gram kernels)
   double2 G2[64 * 64];   // second Gram (t^dagger t)
+  double2 Y[64 * 64];    // projection coefficients N_i D_i^dagger F (kept blocks)
   double est[64];        // per-column residual estimate (relative)
   double target[64];     // per-column stopping level (absolute, same units)
   int32_t rank;
@@ -454,6 +455,77 @@ __global__ void k_scale_vec(C* out, const C* in, double f, int64_t n) {
     c.y = (typename real_of<C>::type)(c.y * f);
     out[i] = c;
   }
+}
+
+// Keep this iteration's search block: D -> slot ctr[0] (if below the
+// available count ctr[2] and the block has full rank R) and
+// N = (D^dagger H D)^-1 beside it; the last block to finish advances ctr[0].  Every block reads ctr[0] before any block takes
+// its ticket, so all of them see the same slot; the counters live on the
+// device, so a captured CUDA graph replays this correctly.
+__global__ void __launch_bounds__(256) k_store_block(void* const* table, double2* nmat,
+                                                     int32_t* ctr, const float2* __restrict__ D,
+                                                     const double2* __restrict__ M,
+                                                     const int32_t* rank, int R, int64_t n) {
+  __shared__ int s_slot, s_avail, s_full;
+  if (threadIdx.x == 0) {
+    s_slot = ((volatile int32_t*)ctr)[0];
+    s_avail = ((volatile int32_t*)ctr)[2];
+    s_full = *rank == R;   // a block that lost rank is not kept
+  }
+  __syncthreads();
+  const int slot = s_slot;
+  const int RR = R * R;
+  const bool keep = slot < s_avail && s_full;
+  if (keep) {
+    float4* dst = (float4*)table[slot];
+    const float4* src = (const float4*)D;
+    const int64_t n4 = n >> 1;   // two complex64 per 16 bytes
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x)
+      dst[i] = src[i];
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) ((float2*)dst)[n - 1] = D[n - 1];
+    if (blockIdx.x == 0)
+      for (int e = threadIdx.x; e < RR; e += blockDim.x) nmat[(int64_t)slot * RR + e] = M[e];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd((unsigned*)&ctr[1], 1u);
+    if (t == gridDim.x - 1) {
+      ctr[1] = 0;
+      if (keep) ctr[0] = slot + 1;
+      __threadfence();
+    }
+  }
+}
+
+// Galerkin start accepted per column only if it lowers the energy
+// functional phi_j = e_j^dagger H e_j - 2 Re e_j^dagger f_j below its value
+// at e_j = 0 (phi = |e - e*|_H^2 - |e*|_H^2): G = E^dagger (H E), G2 =
+// E^dagger F; a rejected column of E and of H E is zeroed.
+__global__ void k_start_guard(Small* st, int R) {
+  const int j = threadIdx.x;
+  if (j < R) {
+    const double phi = st->G[j * R + j].x - 2.0 * st->G2[j * R + j].x;
+    st->est[j] = phi < 0.0 ? 1.0 : 0.0;    // est[] is free before the first iteration
+  }
+}
+__global__ void k_mask_cols(float2* E, float2* HE, const Small* st, int64_t N, int R) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N * R;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (st->est[i % R] == 0.0) {
+      E[i] = make_float2(0.f, 0.f);
+      HE[i] = make_float2(0.f, 0.f);
+    }
+}
+
+// Y = A B for R x R complex matrices (row-major): block i, thread j
+__global__ void k_small_mul(double2* Y, const double2* A, const double2* B, int R) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j >= R) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int l = 0; l < R; ++l) acc = cfma(A[i * R + l], B[l * R + j], acc);
+  Y[i * R + j] = acc;
 }
 
 int grid_for(int64_t n) {
@@ -631,6 +703,125 @@ int cheb_run(Ctx& cx, int prec, double lo, double hi, int order, const C* X, C* 
   return MRHS_OK;
 }
 
+// ---------------------------------------------------------- kept search blocks
+constexpr int kRecycleMax = 256;       // slots in the device table
+constexpr int kRecycleDefault = 128;   // cap when recycle_max_blocks = 0
+constexpr int kRecycleHeadroom = 64;   // slots made available ahead of a cycle
+
+struct RecycleStore {
+  mrhs_op_s* op = nullptr;
+  double2* nmat = nullptr;   // [kRecycleMax][R][R]
+  int64_t n = 0;             // complex64 elements per block (N R)
+  int R = 0, cap = 0;
+  int used = 0;              // slots holding blocks of finished cycles
+  int avail = 0;             // slots with memory behind them
+  std::vector<std::pair<int, int>> cycles;   // [first, end) per finished cycle
+  const float2* block(int slot) const { return (const float2*)op->rc_slots[slot]; }
+  const double2* N(int slot) const { return nmat + (int64_t)slot * R * R; }
+  // launched inside the block-CG iteration (also under graph capture)
+  int store(cudaStream_t s, const float2* D, const double2* M, const int32_t* rank) const {
+    int g = num_sms() * 4;
+    const int64_t need = (n / 2 + 255) / 256;
+    if (need < g) g = need > 0 ? (int)need : 1;
+    { k_store_block<<<g, 256, 0, s>>>(op->rc_table, nmat, op->rc_ctr, D, M, rank, R, n); ::mrhs::count_launch(); }
+    MRHS_CUDA_TRY(cudaGetLastError());
+    return MRHS_OK;
+  }
+};
+
+int recycle_setup(mrhs_op_s* op, int64_t N, int R, int max_blocks, cudaStream_t s,
+                  RecycleStore* rs) {
+  const size_t bytes = sizeof(float2) * (size_t)N * R;
+  if (op->rc_slot_bytes < bytes) {
+    recycle_release(op);
+    op->rc_slot_bytes = bytes;
+  }
+  if (!op->rc_table) MRHS_CUDA_TRY(cudaMalloc(&op->rc_table, sizeof(void*) * kRecycleMax));
+  if (!op->rc_ctr) MRHS_CUDA_TRY(cudaMalloc(&op->rc_ctr, 4 * sizeof(int32_t)));
+  MRHS_TRY(op->ws_rcn.ensure(sizeof(double2) * kRecycleMax * R * R));
+  rs->op = op;
+  rs->nmat = (double2*)op->ws_rcn.ptr;
+  rs->n = N * R;
+  rs->R = R;
+  rs->cap = max_blocks > 0 ? std::min(max_blocks, kRecycleMax) : kRecycleDefault;
+  rs->used = 0;
+  rs->avail = 0;
+  rs->cycles.clear();
+  MRHS_CUDA_TRY(cudaMemsetAsync(op->rc_ctr, 0, 4 * sizeof(int32_t), s));
+  return MRHS_OK;
+}
+
+// Before a cycle: slots up to used + headroom (within the cap), allocating
+// while free memory stays above max(4 GiB, 1/16 of the device); the table
+// and the counters {used, 0, avail} go to the device.
+int recycle_grow(RecycleStore& rs, cudaStream_t s) {
+  mrhs_op_s* op = rs.op;
+  const int want = std::min(rs.cap, rs.used + kRecycleHeadroom);
+  size_t fr = 0, tot = 0;
+  MRHS_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+  const size_t reserve = std::max<size_t>((size_t)4 << 30, tot / 16);
+  const size_t before = op->rc_slots.size();
+  while ((int)op->rc_slots.size() < want && fr >= op->rc_slot_bytes + reserve) {
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, op->rc_slot_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    op->rc_slots.push_back(ptr);
+    fr -= op->rc_slot_bytes;
+  }
+  rs.avail = std::min(want, (int)op->rc_slots.size());
+  if (op->rc_slots.size() != before || before == 0)
+    MRHS_CUDA_TRY(cudaMemcpyAsync(op->rc_table, op->rc_slots.data(),
+                                  sizeof(void*) * op->rc_slots.size(), cudaMemcpyHostToDevice, s));
+  const int32_t ctr[4] = {rs.used, 0, rs.avail, 0};
+  MRHS_CUDA_TRY(cudaMemcpyAsync(op->rc_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s));
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));   // ctr lives on this stack frame
+  return MRHS_OK;
+}
+
+// After a cycle (stream synchronised): the slots it filled.
+int recycle_close_cycle(RecycleStore& rs, cudaStream_t s) {
+  int32_t next = 0;
+  MRHS_CUDA_TRY(cudaMemcpyAsync(&next, rs.op->rc_ctr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  const int end = std::min((int)next, rs.avail);
+  if (end > rs.used) rs.cycles.push_back({rs.used, end});
+  rs.used = std::max(rs.used, end);
+  return MRHS_OK;
+}
+
+// Galerkin start of a refinement cycle from the kept blocks.  The blocks of
+// one earlier cycle are mutually H-conjugate (D_i^dagger H D_j = 0, i != j,
+// and N_i = (D_i^dagger H D_i)^-1), so the correction over that cycle's span
+// is sum_i D_i N_i D_i^dagger Fr.  Earlier cycles are taken one after
+// another, Fr = F - H E recomputed before each, `sweeps` times over all.
+int recycle_project(Ctx& cx, const RecycleStore& rs, int sweeps, int prec, const float2* F,
+                    float2* E, float2* Fr, float2* HE, int* nproj) {
+  const int64_t n = cx.N * cx.R;
+  const int g = grid_for(n);
+  bool zero = true;   // E is still zero: Fr = F
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (const auto& c : rs.cycles) {
+      const float2* fr = F;
+      if (!zero) {
+        MRHS_TRY(cx.apply(prec, E, HE));
+        { k_sub<float2><<<g, kThreads, 0, cx.s>>>(Fr, F, HE, n); ::mrhs::count_launch(); }
+        MRHS_CUDA_TRY(cudaGetLastError());
+        fr = Fr;
+      }
+      for (int slot = c.first; slot < c.second; ++slot) {
+        MRHS_TRY(cx.gram<float2>(rs.block(slot), fr, cx.st->G));            // D_i^dagger Fr
+        { k_small_mul<<<cx.R, 64, 0, cx.s>>>(cx.st->Y, rs.N(slot), cx.st->G, cx.R); ::mrhs::count_launch(); }
+        MRHS_CUDA_TRY(cudaGetLastError());
+        MRHS_TRY(axpy(E, rs.block(slot), cx.st->Y, 1.0, cx.N, cx.R, cx.R, MRHS_C64, cx.s));
+        ++*nproj;
+      }
+      zero = false;
+    }
+  return MRHS_OK;
+}
+
 template <typename C>
 struct BcgBufs {
   C *q = nullptr, *Q = nullptr, *D = nullptr, *z = nullptr, *Zz = nullptr;
@@ -656,7 +847,8 @@ struct BcgBufs {
 template <typename C>
 int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* target_host,
             bool precond, int pprec, double lo, double hi, int order, int maxiter,
-            int check_every, int* iters, int* flag_out) {
+            int check_every, int* iters, int* flag_out, const RecycleStore* keep = nullptr,
+            bool guard_start = false) {
   const int64_t n = cx.N * cx.R;
   const int g = grid_for(n);
   const int dt = sizeof(C) == 16 ? MRHS_C128 : MRHS_C64;
@@ -666,6 +858,13 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
   MRHS_CUDA_TRY(cudaMemsetAsync(&cx.st->flag, 0, sizeof(int), cx.s));
   // r0 = F - H E
   MRHS_TRY(cx.apply(prec, E, z));
+  if (guard_start && sizeof(C) == sizeof(float2)) {
+    MRHS_TRY(cx.gram<C>(E, z, cx.st->G));                                      // E^dag H E
+    MRHS_TRY(cx.gram<C>(E, F, cx.st->G2));                                     // E^dag F
+    { k_start_guard<<<1, 64, 0, cx.s>>>(cx.st, cx.R); ::mrhs::count_launch(); }
+    { k_mask_cols<<<g, kThreads, 0, cx.s>>>((float2*)E, (float2*)z, cx.st, cx.N, cx.R); ::mrhs::count_launch(); }
+    MRHS_CUDA_TRY(cudaGetLastError());
+  }
   { k_sub<C><<<g, kThreads, 0, cx.s>>>(q, F, z, n); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   if (precond) {
@@ -690,6 +889,8 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
     if (precond) MRHS_TRY(cheb_run<C>(cx, pprec, lo, hi, order, z, b.Zz, b.cw, b.c1, b.c2));
     MRHS_TRY(cx.gram<C>(D, z, cx.st->G));                                      // D^dag z
     MRHS_TRY(cx.small_launch(1));                                              // M, MC, -M
+    if (keep && sizeof(C) == sizeof(float2))                                   // D, M kept
+      MRHS_TRY(keep->store(cx.s, (const float2*)D, cx.st->M, &cx.st->rank));
     MRHS_TRY(axpy(E, D, cx.st->MC, 1.0, cx.N, cx.R, cx.R, dt, cx.s));          // E += D M C
     MRHS_TRY(axpy(q, z, cx.st->negM, 1.0, cx.N, cx.R, cx.R, dt, cx.s));        // t = q - z M
     if (precond) {
@@ -851,6 +1052,17 @@ int power_run(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
 
 }  // namespace
 
+void recycle_release(mrhs_op_s* op) {
+  for (void* ptr : op->rc_slots) cudaFree(ptr);
+  op->rc_slots.clear();
+  op->rc_slot_bytes = 0;
+  if (op->rc_table) cudaFree(op->rc_table);
+  op->rc_table = nullptr;
+  if (op->rc_ctr) cudaFree(op->rc_ctr);
+  op->rc_ctr = nullptr;
+  op->ws_rcn.release();
+}
+
 // Largest-eigenvalue estimate by the power method (Sec. 2.3 obtains the
 // Chebyshev upper bound from a few power-method steps):
 // Rayleigh quotient of H^k v0, one right-hand side, operator in `prec`.
@@ -951,6 +1163,8 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       info->cycle_resid[c] = 0.0;
       info->cycle_flag[c] = 0;
     }
+    info->recycle_blocks = 0;
+    info->recycle_projections = 0;
   }
 
   if (!mixed) {
@@ -968,6 +1182,11 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     }
   } else {
     MRHS_TRY(initial_residual());
+    // search blocks of finished cycles, for the Galerkin start of the next
+    RecycleStore keep;
+    bool recycle = p.recycle > 0;
+    int nproj = 0;
+    if (recycle) MRHS_TRY(recycle_setup(op, cx.N, R, p.recycle_max_blocks, s, &keep));
     for (cycles = 0; cycles < p.max_cycles && !all_done() && total_iters < p.maxiter; ++cycles) {
       // scale each residual column to unit norm; inner target relative to 1
       std::vector<double> rho(R);
@@ -986,21 +1205,43 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       { k_scale_to_c64<<<g, kThreads, 0, s>>>(sb.f32, sb.r64, sb.rho_d, cx.N, R); ::mrhs::count_launch(); }
       MRHS_CUDA_TRY(cudaMemsetAsync(sb.e32, 0, sizeof(float2) * n, s));
       MRHS_CUDA_TRY(cudaGetLastError());
+      const bool projected = recycle && !keep.cycles.empty();
+      if (recycle) {
+        // E_0 from the earlier cycles' blocks (the inner solve's q and z
+        // buffers serve as scratch before it starts), then room for this
+        // cycle's blocks
+        if (projected)
+          MRHS_TRY(recycle_project(cx, keep, p.recycle, p.krylov_prec, sb.f32, sb.e32,
+                                   sb.b32.q, sb.b32.z, &nproj));
+        MRHS_TRY(recycle_grow(keep, s));
+      }
+      const std::vector<double> rnorm_before = rnorm;
       int it = 0;
       MRHS_TRY(run_bcg<float2>(cx, sb.b32, p.krylov_prec, sb.f32, sb.e32, target.data(),
                                p.precond != 0, p.precond_prec, lo, hi, p.cheb_order,
-                               p.maxiter - total_iters, every, &it, &flag));
+                               p.maxiter - total_iters, every, &it, &flag,
+                               recycle && keep.avail > keep.used ? &keep : nullptr, projected));
+      if (recycle) MRHS_TRY(recycle_close_cycle(keep, s));
       total_iters += it;
       { k_update_x<<<g, kThreads, 0, s>>>(X, sb.e32, sb.rho_d, cx.N, R); ::mrhs::count_launch(); }
       MRHS_CUDA_TRY(cudaGetLastError());
       if (final_cycle) MRHS_TRY(residual_in(MRHS_PREC_FP64));
       else MRHS_TRY(true_residual());
+      // a cycle that started from kept blocks and made no progress on some
+      // column ends the recycling for this solve (plain restarts follow)
+      if (projected)
+        for (int j = 0; j < R; ++j)
+          if (rho[j] > 0 && !(rnorm[j] < rnorm_before[j])) recycle = false;
       if (info && cycles < MRHS_MAX_CYCLES) {
         info->cycle_iters[cycles] = it;
         info->cycle_resid[cycles] = max_rel();
         info->cycle_flag[cycles] = flag;
       }
       if (flag & 4) break;
+    }
+    if (info) {
+      info->recycle_blocks = keep.used;
+      info->recycle_projections = nproj;
     }
   }
   if (flag & 4) status = MRHS_ERR_NONFINITE;
@@ -1529,6 +1770,8 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
     if (status != MRHS_OK && worst == MRHS_OK) worst = status;
     if (!infos) continue;
     mrhs_solve_info& inf = infos[i];
+    inf.recycle_blocks = 0;      // lockstep batches restart each cycle afresh
+    inf.recycle_projections = 0;
     inf.status = status;
     inf.iters = b.iters;
     inf.cycles = b.cycles;
