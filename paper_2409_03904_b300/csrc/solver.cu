@@ -848,7 +848,7 @@ template <typename C>
 int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* target_host,
             bool precond, int pprec, double lo, double hi, int order, int maxiter,
             int check_every, int* iters, int* flag_out, const RecycleStore* keep = nullptr,
-            bool guard_start = false) {
+            bool guard_start = false, bool e_zero = false) {
   const int64_t n = cx.N * cx.R;
   const int g = grid_for(n);
   const int dt = sizeof(C) == 16 ? MRHS_C128 : MRHS_C64;
@@ -856,17 +856,21 @@ int run_bcg(Ctx& cx, BcgBufs<C>& b, int prec, const C* F, C* E, const double* ta
   MRHS_CUDA_TRY(cudaMemcpyAsync(cx.st->target, target_host, sizeof(double) * cx.R,
                                 cudaMemcpyHostToDevice, cx.s));
   MRHS_CUDA_TRY(cudaMemsetAsync(&cx.st->flag, 0, sizeof(int), cx.s));
-  // r0 = F - H E
-  MRHS_TRY(cx.apply(prec, E, z));
-  if (guard_start && sizeof(C) == sizeof(float2)) {
-    MRHS_TRY(cx.gram<C>(E, z, cx.st->G));                                      // E^dag H E
-    MRHS_TRY(cx.gram<C>(E, F, cx.st->G2));                                     // E^dag F
-    { k_start_guard<<<1, 64, 0, cx.s>>>(cx.st, cx.R); ::mrhs::count_launch(); }
-    { k_mask_cols<<<g, kThreads, 0, cx.s>>>((float2*)E, (float2*)z, cx.st, cx.N, cx.R); ::mrhs::count_launch(); }
+  // r0 = F - H E; with E known to be zero (H 0 = 0 exactly) r0 = F
+  if (e_zero) {
+    MRHS_CUDA_TRY(cudaMemcpyAsync(q, F, sizeof(C) * n, cudaMemcpyDeviceToDevice, cx.s));
+  } else {
+    MRHS_TRY(cx.apply(prec, E, z));
+    if (guard_start && sizeof(C) == sizeof(float2)) {
+      MRHS_TRY(cx.gram<C>(E, z, cx.st->G));                                    // E^dag H E
+      MRHS_TRY(cx.gram<C>(E, F, cx.st->G2));                                   // E^dag F
+      { k_start_guard<<<1, 64, 0, cx.s>>>(cx.st, cx.R); ::mrhs::count_launch(); }
+      { k_mask_cols<<<g, kThreads, 0, cx.s>>>((float2*)E, (float2*)z, cx.st, cx.N, cx.R); ::mrhs::count_launch(); }
+      MRHS_CUDA_TRY(cudaGetLastError());
+    }
+    { k_sub<C><<<g, kThreads, 0, cx.s>>>(q, F, z, n); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaGetLastError());
   }
-  { k_sub<C><<<g, kThreads, 0, cx.s>>>(q, F, z, n); ::mrhs::count_launch(); }
-  MRHS_CUDA_TRY(cudaGetLastError());
   if (precond) {
     MRHS_TRY(cheb_run<C>(cx, pprec, lo, hi, order, q, Q, b.cw, b.c1, b.c2));   // Z0 = M^-1 r0
     MRHS_TRY(cx.gram<C>(Q, q, cx.st->G));                                      // Z0^dag r0
@@ -1137,6 +1141,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     return MRHS_OK;
   };
   // a zero initial guess needs no operator application: r = B
+  bool x0_zero = false;
   auto initial_residual = [&]() -> int {
     std::vector<double> xn(R);
     MRHS_TRY(cx.colnorms<double2>(X, sb.rnorm_d));
@@ -1145,6 +1150,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     MRHS_CUDA_TRY(cudaStreamSynchronize(s));
     bool zero = true;
     for (double v : xn) zero = zero && v == 0.0;
+    x0_zero = zero;
     if (!zero) return true_residual();
     MRHS_CUDA_TRY(cudaMemcpyAsync(sb.r64, B, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
     rnorm = bnorm;
@@ -1175,7 +1181,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       int it = 0;
       MRHS_TRY(run_bcg<double2>(cx, sb.b64, MRHS_PREC_FP64, B, X, target.data(), p.precond != 0,
                                 p.precond_prec, lo, hi, p.cheb_order, p.maxiter, every, &it,
-                                &flag));
+                                &flag, nullptr, false, x0_zero));
       total_iters = it;
       cycles = 1;
       MRHS_TRY(true_residual());
@@ -1220,7 +1226,8 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       MRHS_TRY(run_bcg<float2>(cx, sb.b32, p.krylov_prec, sb.f32, sb.e32, target.data(),
                                p.precond != 0, p.precond_prec, lo, hi, p.cheb_order,
                                p.maxiter - total_iters, every, &it, &flag,
-                               recycle && keep.avail > keep.used ? &keep : nullptr, projected));
+                               recycle && keep.avail > keep.used ? &keep : nullptr, projected,
+                               !projected));
       if (recycle) MRHS_TRY(recycle_close_cycle(keep, s));
       total_iters += it;
       { k_update_x<<<g, kThreads, 0, s>>>(X, sb.e32, sb.rho_d, cx.N, R); ::mrhs::count_launch(); }
