@@ -459,9 +459,10 @@ __global__ void k_scale_vec(C* out, const C* in, double f, int64_t n) {
 
 // Keep this iteration's search block: D -> slot ctr[0] (if below the
 // available count ctr[2] and the block has full rank R) and
-// N = (D^dagger H D)^-1 beside it; the last block to finish advances ctr[0].  Every block reads ctr[0] before any block takes
-// its ticket, so all of them see the same slot; the counters live on the
-// device, so a captured CUDA graph replays this correctly.
+// N = (D^dagger H D)^-1 beside it; the last block to finish advances
+// ctr[0].  Every block reads ctr[0] before any block takes its ticket, so
+// all of them see the same slot; the counters live on the device, so a
+// captured CUDA graph replays this correctly.
 __global__ void __launch_bounds__(256) k_store_block(void* const* table, double2* nmat,
                                                      int32_t* ctr, const float2* __restrict__ D,
                                                      const double2* __restrict__ M,
