@@ -51,7 +51,11 @@ def parse():
     ap.add_argument("--krylov", default="tc32", choices=["tc32", "fp32"])
     ap.add_argument("--residual", default="oz", choices=["oz", "df32", "fp64"],
                     help="operator of the refinement cycles' residuals (the one that meets "
-                         "tol is always recomputed in FP64)")
+                         "tol is always recomputed with the FP64 operator)")
+    ap.add_argument("--fp64-op", default="oz", choices=["oz", "fp64"],
+                    help="the FP64 operator: of the residual that decides convergence and of "
+                         "the plain FP64 block CG (oz: digit-sliced tensor-core form held to the "
+                         "FP64 tolerance; fp64: the FP64 pipes)")
     ap.add_argument("--cheb-order", type=int, default=8)
     ap.add_argument("--cheb-ratio", type=float, default=400.0, help="hi / lo")
     ap.add_argument("--inner-tol", type=float, default=1e-3)
@@ -60,10 +64,9 @@ def parse():
                          "(0: plain restart)")
     ap.add_argument("--check-every", type=int, default=2,
                     help="block-CG iterations between convergence checks (one graph chunk)")
-    ap.add_argument("--fp64-iters", type=int, default=3,
-                    help="FP64 block-CG iterations timed for the plain-FP64 comparison")
-    ap.add_argument("--fp64-full", action="store_true",
-                    help="run the plain FP64 solve to convergence (slow)")
+    ap.add_argument("--fp64-native-iters", type=int, default=3,
+                    help="iterations of plain FP64 block CG on the FP64 pipes timed for the "
+                         "per-iteration comparison (0: skip)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the standalone operator, FP64 and e2e measurements")
     ap.add_argument("--cpu-sites", type=int, default=96, help="oracle sample size (sites)")
@@ -173,7 +176,7 @@ def op_bytes(w, R, prec):
     output vectors once (neighbour re-reads not counted)."""
     V = int(np.prod(w["L"]))
     coef = {"fp64": 16, "df32": 16, "fp32": 8, "bf16": 4, "fp16": 4, "fp16x": 4, "tc32": 8,
-            "oz": 28}[prec]
+            "oz": 32}[prec]
     vec = 16 if prec in WIDE else 8
     # site scale + diagonal (float pair; a double pair for the digit image)
     extra = {"fp64": 0, "df32": 0, "fp32": 0, "oz": 16 * V}.get(prec, 8 * V)
@@ -211,7 +214,7 @@ class OracleSample:
         self.idx = np.sort(rng.choice(self.V, size=min(sites, self.V), replace=False))
         self.A_s = coarse_op(w["L"], w["nb"], w["npts"], w["seed"], shift, sites=self.idx)
 
-    def ms_per_rhs(self, B_host, fp64_iters, min_seconds=10.0):
+    def ms_per_rhs(self, B_host, applications, min_seconds=10.0):
         from oracle import native
         w = self.w
         native.coarse_op_apply_sites(self.A_s[:2], B_host, w["L"], self.disp, self.idx[:2])
@@ -227,17 +230,19 @@ class OracleSample:
         dt = elapsed / reps
         full_ms = dt * 1e3 * self.V / len(self.idx)
         R = B_host.shape[-1]
-        return full_ms * (fp64_iters + 2) / R, dict(
+        return full_ms * applications / R, dict(
             sample=f"FP64 oracle operator on {len(self.idx)} of {self.V} sites, {reps} repetitions "
                    f"({elapsed:.1f} s, {dt:.3f} s each), scaled x{self.V / len(self.idx):.0f} to one "
-                   f"application, x{fp64_iters + 2} applications (FP64 block-CG iterations + 2)",
+                   f"application, x{applications} applications (those of the FP64 block CG)",
             full_apply_ms=full_ms,
             cores=int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
 
 
 def fp64_iteration_count(name):
     """Iterations the plain FP64 block CG needs on this workload, as measured
-    on the GPU and recorded in profiles/fp64_block_cg_iterations.txt."""
+    on the GPU and recorded in profiles/fp64_block_cg_iterations.txt (used by
+    the reference arm only, which runs no GPU code; our own arm measures the
+    count in the same run)."""
     p = os.path.join(ROOT, "profiles", "fp64_block_cg_iterations.txt")
     try:
         with open(p) as f:
@@ -277,7 +282,9 @@ def run_reference(a, w, shift):
     sample = OracleSample(w, shift, a.cpu_sites)
     vals = []
     for i in range(a.warmup + a.steps):
-        v, meta = sample.ms_per_rhs(B, iters)
+        # FP64 block CG from a zero guess: one application per iteration and
+        # one for the final true residual
+        v, meta = sample.ms_per_rhs(B, iters + 1)
         if i >= a.warmup:
             vals.append(v)
     val = statistics.median(vals)
@@ -289,7 +296,9 @@ def run_reference(a, w, shift):
                             "kind": "oracle", "sample": meta["sample"]},
            "e2e": {"value": val, "unit": "ms/RHS", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0},
-           "fp64_iterations": iters}
+           "fp64_iterations": iters,
+           "fp64_iterations_source": "recorded from the GPU FP64 block CG of this workload "
+                                     "(profiles/fp64_block_cg_iterations.txt)"}
     print(json.dumps(out), flush=True)
 
 
@@ -357,12 +366,12 @@ def run_op(a, w, shift):
                 "launches": nk, "peak_kind": f"{kind} copy bandwidth"}
         if prec == "oz":
             # digit-sliced form: bound by the fp16 tensor pipe.  Algorithmic work =
-            # the 28 digit-pair products (s + t <= 8) of the complex operator;
-            # issued = 19 MMAs of M = 128 per point and K step (two digit levels
-            # per accumulator, 10 of the 38 half-MMAs have a zero or dropped half)
-            pairs = sum(range(1, 8))
+            # the 36 digit-pair products (s + t <= 9) of the complex operator;
+            # issued = 20 MMAs of M = 128 per point and K step (two digit levels
+            # per accumulator, 4 of the 40 half-MMAs have a zero half)
+            pairs = sum(range(1, 9))
             alg = pairs * flops
-            issued = 19 * 2 * 128 * (2 * ((nb + 7) // 8 * 8)) * ((nb + 15) // 16 * 16) \
+            issued = 20 * 2 * 128 * (2 * ((nb + 7) // 8 * 8)) * ((nb + 15) // 16 * 16) \
                 * w["npts"] * V
             roof = {"bound": "tensor", "achieved": alg / (per * 1e-3) / 1e12, "peak": bf16_peak,
                     "unit": "TFLOP/s", "frac": alg / (per * 1e-3) / 1e12 / bf16_peak,
@@ -563,7 +572,7 @@ def run_batch(a):
     for w, c in probs:
         disp, _ = stencil(w["npts"])
         A = sdev.coarse_op(w["L"], w["nb"], w["npts"], w["seed"], load_shift(w["name"]))
-        ops.append(mrhs.CoarseOp(A, w["L"], disp, ("fp64", "fp16x", "tc32", "oz")))
+        ops.append(mrhs.CoarseOp(A, w["L"], disp, ("fp16x", "tc32", "oz")))
         del A
         Bs.append(sdev.vectors(w["L"], w["nb"], w["nrhs"], w["seed"] + 101 * c))
     for o in ops:
@@ -730,10 +739,13 @@ def main():
     t0 = time.time()
     A = sdev.coarse_op(w["L"], nb, w["npts"], w["seed"], shift, device=dev)
     # the solve's operator holds the precisions the solve uses (at 12^4, nb 48:
-    # FP64 62 GB, digit image 108 GB, TC32 31 GB, FP16 16 GB); the others are
-    # timed afterwards on a second operator
-    precs = tuple(dict.fromkeys(("fp64", "df32", a.residual, a.precond, a.krylov)))
-    other_precs = tuple(p for p in ("fp32", "bf16", "fp16") if p not in precs)
+    # digit image 124 GB, TC32 31 GB, FP16 16 GB; the FP64 copy, 62 GB, only
+    # when the FP64 pipes are asked for); the others are timed afterwards on a
+    # second operator
+    need64 = a.fp64_op == "fp64" or a.residual in ("fp64", "df32")
+    precs = tuple(dict.fromkeys((a.fp64_op, a.residual, a.precond, a.krylov)
+                                + (("fp64", "df32") if need64 else ())))
+    other_precs = tuple(p for p in ("fp64", "fp32", "bf16", "fp16") if p not in precs)
     op = mrhs.CoarseOp(A, w["L"], disp, precs)
     del A
     torch.cuda.empty_cache()
@@ -745,7 +757,8 @@ def main():
                   krylov_prec=a.krylov,
                   cheb_order=a.cheb_order, cheb_hi=hi, cheb_lo=hi / a.cheb_ratio,
                   inner_tol=a.inner_tol, maxiter=20000, max_cycles=20,
-                  check_every=a.check_every, residual_prec=a.residual, recycle=a.recycle)
+                  check_every=a.check_every, residual_prec=a.residual, recycle=a.recycle,
+                  fp64_prec=a.fp64_op)
 
     stream = torch.cuda.current_stream()
     # launch shapes of the two tensor-core forms, tuned once for this shape
@@ -822,23 +835,31 @@ def main():
                           "gbs": op_bytes(w, R, p) / (t * 1e-3) / 1e9}
         time_ops(op, precs)
         extras["coarse_op"] = cop
-        # plain FP64 block CG: time per iteration, extrapolated when not run to the end
-        if a.fp64_full:
-            Xf, fi = op.solve(B, tol=1e-8, maxiter=20000, raise_on_fail=False)
-            fp64 = {"iters": fi["iters"], "ms": fi["ms_total"], "resid": max(fi["resid"]),
-                    "ms_per_rhs": fi["ms_total"] / R, "extrapolated": False}
-        else:
-            # per-iteration cost as the difference of two short runs, so the
-            # fixed start-up and final residual costs cancel
-            _, f1 = op.solve(B, tol=1e-30, maxiter=2, raise_on_fail=False)
-            _, f2 = op.solve(B, tol=1e-30, maxiter=2 + a.fp64_iters, raise_on_fail=False)
-            per_it = (f2["ms_total"] - f1["ms_total"]) / max(f2["iters"] - f1["iters"], 1)
-            n_it = fp64_iteration_count(w["name"])
-            fp64 = {"ms_per_iter": per_it, "iters_to_tol": n_it, "extrapolated": True,
-                    "ms_per_rhs": (per_it * n_it + f1["ms_total"] - 2 * per_it) / R if n_it else None}
+        if "oz" in cop:
+            # the FP64 operator's roofline on FP64 algorithmic bytes (complex128
+            # coefficients and vectors), and on the tensor pipe it runs on
+            t = cop["oz"]["ms"]
+            b64 = op_bytes(w, R, "fp64")
+            pairs = sum(range(1, 9))
+            hbm, bf16_peak, kind = peaks()
+            cop["oz"]["fp64_roofline"] = {
+                "bound": "tensor", "fp64_algorithmic_bytes": b64,
+                "fp64_bytes_gbs": b64 / (t * 1e-3) / 1e9,
+                "fp64_bytes_hbm_frac": b64 / (t * 1e-3) / 1e9 / hbm,
+                "digit_pair_tflops": pairs * op_flops(w, R) / (t * 1e-3) / 1e12,
+                "tensor_frac": pairs * op_flops(w, R) / (t * 1e-3) / 1e12 / bf16_peak,
+                "peak_kind": f"{kind} copy bandwidth / dense bf16"}
+        # plain FP64 block CG (Fig. 2 left) to the same tolerance on the same
+        # sources, run to the end once, with the FP64 operator of the solve
+        Xf, fi = op.solve(B, tol=1e-8, maxiter=20000, raise_on_fail=False, fp64_prec=a.fp64_op)
+        n_fp64_apply = fi["applies"][a.fp64_op]
+        fp64 = {"iters": fi["iters"], "ms": fi["ms_total"], "resid": max(fi["resid"]),
+                "ms_per_rhs": fi["ms_total"] / R, "operator": a.fp64_op,
+                "operator_applications": n_fp64_apply, "extrapolated": False,
+                "status": fi["status"]}
+        del Xf
         extras["fp64_solve"] = fp64
-        if fp64.get("ms_per_rhs"):
-            extras["mixed_speedup_vs_fp64"] = fp64["ms_per_rhs"] / value
+        extras["mixed_speedup_vs_fp64"] = fp64["ms_per_rhs"] / value
         # end to end through the public API with host buffers
         Bh = B.cpu().pin_memory()
         Xh = torch.empty_like(Bh).pin_memory()
@@ -854,13 +875,13 @@ def main():
         e2e_ms = e0.elapsed_time(e1) / a.steps
         extras["e2e"] = {"value": e2e_ms / R, "unit": "ms/RHS",
                          "h2d_bytes_per_step": Bh.numel() * 16, "d2h_bytes_per_step": Xh.numel() * 16}
-        # CPU oracle on a bounded sample of the same workload
-        n_it = fp64_iteration_count(w["name"])
-        cpu_v, meta = OracleSample(w, shift, a.cpu_sites).ms_per_rhs(Bh.numpy(), n_it or 0)
-        extras["cpu_baseline"] = {"value": cpu_v if n_it else None, "unit": "ms/RHS",
+        # CPU oracle on a bounded sample of the same workload, times the FP64
+        # block CG's operator applications measured above
+        cpu_v, meta = OracleSample(w, shift, a.cpu_sites).ms_per_rhs(Bh.numpy(), n_fp64_apply)
+        extras["cpu_baseline"] = {"value": cpu_v, "unit": "ms/RHS",
                                   "cores": meta["cores"], "kind": "oracle",
-                                  "sample": meta["sample"] + ("" if n_it else
-                                                              "; FP64 iteration count unknown"),
+                                  "sample": meta["sample"] + " (application count of the FP64 "
+                                            "block CG measured in this run)",
                                   "full_apply_ms": meta["full_apply_ms"]}
         # the remaining precisions' operator throughput, on an operator of their own
         if other_precs:
@@ -871,6 +892,19 @@ def main():
             del A2
             torch.cuda.empty_cache()
             time_ops(op2, other_precs)
+            if "fp64" in other_precs and a.fp64_native_iters > 0:
+                # FP64 block CG on the FP64 pipes: its cost per iteration (two
+                # short runs, so start-up and final residual cancel) times the
+                # iteration count measured above -- context, not the baseline
+                _, f1 = op2.solve(B, tol=1e-30, maxiter=2, raise_on_fail=False, fp64_prec="fp64")
+                _, f2 = op2.solve(B, tol=1e-30, maxiter=2 + a.fp64_native_iters,
+                                  raise_on_fail=False, fp64_prec="fp64")
+                per_it = (f2["ms_total"] - f1["ms_total"]) / max(f2["iters"] - f1["iters"], 1)
+                extras["fp64_native_solve_estimate"] = {
+                    "ms_per_iter": per_it, "iters": fp64["iters"], "extrapolated": True,
+                    "ms_per_rhs": (per_it * fp64["iters"] + f1["ms_total"] - 2 * per_it) / R,
+                    "note": "FP64-pipe operator: per-iteration time measured in this run x the "
+                            "iteration count of the FP64 block CG above"}
             del op2
 
     if rank == 0:
@@ -878,14 +912,16 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": "ms/RHS", "n_gpus": world,
                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step,
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-               "dtype": f"f64+{a.residual}+{a.krylov}+{a.precond}", "data": "synthetic",
+               "dtype": f"f64+{a.fp64_op}+{a.residual}+{a.krylov}+{a.precond}", "data": "synthetic",
                "config": {"workload": w["name"], "L": list(w["L"]), "nb": nb, "npts": w["npts"],
                           "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
                           "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
                                      f"[{hi / a.cheb_ratio:.4g}, {hi:.4g}]",
                           "inner_tol": a.inner_tol, "recycle": a.recycle,
                           "parallelism": f"replicas x{world}",
-                          "residuals": f"{a.residual} per cycle, fp64 for the one that meets tol",
+                          "residuals": f"{a.residual} per cycle, the FP64 operator "
+                                       f"({a.fp64_op}) for the one that meets tol",
+                          "fp64_operator": a.fp64_op,
                           "launch_shapes": tuned,
                           "l2": "inputs larger than L2 (coefficients "
                                 f"{op_bytes(w, R, a.precond) / 1e9:.1f} GB per application)"},

@@ -62,15 +62,18 @@ enum {
                           double-float arithmetic (FP32 pairs, error-free
                           products and sums) on the FP32 pipes: about 2^-44
                           relative; built whenever FP64 is */
-  MRHS_PREC_OZ = 7    /* FP64-class operator on the tensor cores by digit
+  MRHS_PREC_OZ = 7    /* FP64 operator on the tensor cores by digit
                           slicing (Ozaki scheme): coefficients (per site) and
-                          input (per column) as seven signed 6-bit fixed-point
-                          digits held exactly in fp16, digit products with
-                          s + t <= 8 summed exactly in FP32 tensor memory,
-                          recombined in int64 and FP64; vectors complex128;
-                          about 2^-42 of the site and column scales per term;
-                          nrhs <= 32; 28 bytes per complex coefficient;
-                          implies FP64 (and DF32) */
+                          input (per column) as eight signed 6-bit fixed-point
+                          digits held exactly in fp16 (2^-48 of the scale),
+                          digit products with s + t <= 9 summed in FP32
+                          tensor memory, recombined in int64 and FP64;
+                          vectors complex128; a few 2^-48 of the site and
+                          column scales per term (relative error ~1e-13, held
+                          to the FP64 tolerance 1e-12 in the tests);
+                          nrhs <= 32; 32 bytes per complex coefficient.
+                          Needs no FP64 copy: block_cg_solve runs its FP64
+                          operator applications with it (see fp64_prec) */
 };
 #define MRHS_NUM_PREC 8
 #define MRHS_PREC_IS_TC(p) ((p) >= MRHS_PREC_BF16 && (p) <= MRHS_PREC_TC32)
@@ -103,9 +106,13 @@ typedef struct mrhs_op_s* mrhs_op;
  *   prec_mask  OR of MRHS_PREC_BIT(p): the precisions to build.  The operator
  *          owns a packed copy of A for each (complex128, complex64, or
  *          16-bit codes with a float scale and diagonal per site; FP16 and
- *          FP16X share one image; OZ keeps seven fp16 digit tiles per
- *          coefficient tile, 28 bytes per complex coefficient, with double
+ *          FP16X share one image; OZ keeps eight fp16 digit tiles per
+ *          coefficient tile, 32 bytes per complex coefficient, with double
  *          scales and diagonals); A may be freed after the call returns.
+ *          DF32 runs on the FP64 copy, so FP64 and DF32 come together.  OZ
+ *          does not need the FP64 copy; its adjoint image is built from the
+ *          FP64 copy on first use, so coarse_op_apply_dag with OZ needs FP64
+ *          built as well (MRHS_ERR_UNSUPPORTED otherwise).
  * On success *out holds the handle.  Synchronises `stream`. */
 int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts,
                    const int8_t* disp, const void* A, uint32_t prec_mask, void* stream);
@@ -290,10 +297,11 @@ typedef struct {
   int32_t residual_prec; /* MIXED: operator of each cycle's residual B - H X:
                            MRHS_PREC_FP64, MRHS_PREC_DF32 or MRHS_PREC_OZ;
                            -1 (default): OZ if built and nrhs <= 32, else
-                           DF32.  A non-FP64 residual that meets tol is
-                           recomputed with FP64 before the solve returns, and
-                           a cycle that needs less than a tenfold reduction
-                           computes its residual in FP64 directly, so the
+                           DF32.  A residual in another precision than
+                           fp64_prec that meets tol is recomputed with
+                           fp64_prec before the solve returns, and a cycle
+                           that needs less than a tenfold reduction computes
+                           its residual with fp64_prec directly, so the
                            residuals reported are FP64 ones */
   int32_t recycle;      /* MIXED (block_cg_solve only): every inner iteration
                            keeps a copy of its search block D and of
@@ -316,10 +324,20 @@ typedef struct {
                            0 (default): 128.  Fewer are kept when device
                            memory runs short (a reserve of max(4 GiB, 1/16
                            of the device) stays free) */
+  int32_t fp64_prec;    /* the FP64 operator of the solve: every operator
+                           application of MRHS_SOLVE_FP64 (Krylov loop,
+                           residuals, FP64 preconditioner), and in MIXED and
+                           CG5D the residual that decides convergence.
+                           MRHS_PREC_FP64 (FP64 FMA pipes) or MRHS_PREC_OZ
+                           (digit-sliced tensor-core form, held to the FP64
+                           tolerance); -1 (default): OZ if built and
+                           nrhs <= 32, else FP64 (MRHS_ERR_UNSUPPORTED if
+                           neither is available) */
 } mrhs_solve_params;
 
 enum {
-  MRHS_SOLVE_FP64 = 0,  /* everything FP64 (plain FP64 block CG) */
+  MRHS_SOLVE_FP64 = 0,  /* everything FP64 (plain FP64 block CG, with the
+                           operator fp64_prec) */
   MRHS_SOLVE_MIXED = 1, /* FP64 outer defect correction (true residual, Gram
                            accumulation, Cholesky, solution update); inner block
                            CG on complex64 vectors with the TC32 (or FP32)

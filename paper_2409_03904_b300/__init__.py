@@ -42,8 +42,9 @@ class CoarseOp:
     A: CUDA complex128 tensor [V][npts][nb][nb]; L: 4 lattice extents; disp:
     int8 [npts][4] displacements (disp[0] = 0); precisions: any of "fp64",
     "fp32", "bf16", "fp16", "fp16x", "tc32", "df32", "oz" ("df32" comes with
-    "fp64" and implies it; "oz", the digit-sliced tensor-core form, implies
-    both).  The operator keeps its own packed copies.
+    "fp64" and implies it; "oz" is the digit-sliced tensor-core form of the
+    FP64 operator and needs neither, except for its adjoint, which is built
+    from the FP64 copy).  The operator keeps its own packed copies.
     """
 
     def __init__(self, A, L, disp, precisions=("fp64", "fp32")):
@@ -57,8 +58,6 @@ class CoarseOp:
         self.nb = int(A.shape[2])
         self.N = self.V * self.nb
         precisions = tuple(precisions)
-        if "oz" in precisions and "fp64" not in precisions:
-            precisions = ("fp64",) + precisions
         if "fp64" in precisions and "df32" not in precisions:
             precisions += ("df32",)
         if "df32" in precisions and "fp64" not in precisions:
@@ -220,7 +219,7 @@ class CoarseOp:
             raise ValueError(f"mode must be one of {sorted(modes)}")
         l.mrhs_solve_params_default(ctypes.byref(p), modes[mode])
         for k, v in kw.items():
-            if k in ("precond_prec", "krylov_prec", "residual_prec") and isinstance(v, str):
+            if k in ("precond_prec", "krylov_prec", "residual_prec", "fp64_prec") and isinstance(v, str):
                 v = PREC[v]
             if not hasattr(p, k):
                 raise KeyError(k)
@@ -293,7 +292,7 @@ def batch_solve(ops, Bs, mode="mixed", raise_on_fail=True, **kw):
     p = SolveParams()
     l.mrhs_solve_params_default(ctypes.byref(p), SOLVE_MIXED if mode == "mixed" else SOLVE_FP64)
     for k, v in kw.items():
-        if k in ("precond_prec", "krylov_prec", "residual_prec") and isinstance(v, str):
+        if k in ("precond_prec", "krylov_prec", "residual_prec", "fp64_prec") and isinstance(v, str):
             v = PREC[v]
         if not hasattr(p, k):
             raise KeyError(k)

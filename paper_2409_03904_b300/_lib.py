@@ -39,7 +39,8 @@ class SolveParams(ctypes.Structure):
                 ("max_cycles", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("breakdown_tau", ctypes.c_double), ("krylov_prec", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("residual_prec", ctypes.c_int32),
-                ("recycle", ctypes.c_int32), ("recycle_max_blocks", ctypes.c_int32)]
+                ("recycle", ctypes.c_int32), ("recycle_max_blocks", ctypes.c_int32),
+                ("fp64_prec", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

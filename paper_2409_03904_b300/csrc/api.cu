@@ -123,14 +123,28 @@ int check_prec(const mrhs_op_s* op, int prec) {
   return MRHS_OK;
 }
 
-// Operator of the refinement cycles' residuals: FP64, DF32 or (when built and
-// the shape fits) the digit-sliced tensor-core form.
-int check_residual_prec(int rp, bool oz_ok) {
-  if (rp == MRHS_PREC_FP64 || rp == MRHS_PREC_DF32) return MRHS_OK;
+// Operator of the refinement cycles' residuals: FP64, DF32 (both on the FP64
+// copy) or, when built and the shape fits, the digit-sliced tensor-core form.
+int check_residual_prec(int rp, bool fp64_ok, bool oz_ok) {
+  if (rp == MRHS_PREC_FP64 || rp == MRHS_PREC_DF32)
+    return fp64_ok ? MRHS_OK : fail(MRHS_ERR_UNSUPPORTED, "residual_prec: FP64 not built");
   if (rp == MRHS_PREC_OZ)
     return oz_ok ? MRHS_OK
                  : fail(MRHS_ERR_UNSUPPORTED, "residual_prec OZ: not built or nrhs > 32");
   return fail(MRHS_ERR_INVALID_ARG, "residual_prec must be FP64, DF32 or OZ");
+}
+
+// The FP64 operator of a solve (fp64_prec): native FP64 or the digit-sliced
+// form; -1 picks OZ when it is built and fits, else FP64.
+int resolve_fp64_prec(int* fp, bool fp64_ok, bool oz_ok) {
+  if (*fp < 0) *fp = oz_ok ? MRHS_PREC_OZ : MRHS_PREC_FP64;
+  if (*fp == MRHS_PREC_FP64)
+    return fp64_ok ? MRHS_OK
+                   : fail(MRHS_ERR_UNSUPPORTED, "the solve needs the FP64 or the OZ operator "
+                                                "(OZ: nrhs <= 32)");
+  if (*fp == MRHS_PREC_OZ)
+    return oz_ok ? MRHS_OK : fail(MRHS_ERR_UNSUPPORTED, "fp64_prec OZ: not built or nrhs > 32");
+  return fail(MRHS_ERR_INVALID_ARG, "fp64_prec must be FP64 or OZ");
 }
 
 }  // namespace
@@ -166,9 +180,8 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   if (prec_mask == 0 || (prec_mask >> MRHS_NUM_PREC))
     return fail(MRHS_ERR_INVALID_ARG, "prec_mask must select precisions 0..7");
   // DF32 runs on the FP64 coefficients; with them it comes for free.  The
-  // digit-sliced form keeps FP64 beside it (its adjoint image and the FP64
-  // confirmation of residuals are built from those coefficients)
-  if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_OZ)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_FP64);
+  // digit-sliced form stands alone (only its adjoint image is built from the
+  // FP64 copy, on first use)
   if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_DF32)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_FP64);
   if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)) prec_mask |= MRHS_PREC_BIT(MRHS_PREC_DF32);
   if (!aligned16(A)) return fail(MRHS_ERR_INVALID_ARG, "A not 16-byte aligned");
@@ -605,26 +618,31 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
     return fail(MRHS_ERR_INVALID_ARG, "mode");
   if (p.recycle < 0 || p.recycle_max_blocks < 0)
     return fail(MRHS_ERR_INVALID_ARG, "recycle / recycle_max_blocks must be >= 0");
-  if (!(op->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)))
-    return fail(MRHS_ERR_UNSUPPORTED, "block_cg_solve needs the FP64 operator");
+  auto built = [&](int pr) { return (op->prec_mask & MRHS_PREC_BIT(pr)) != 0; };
+  const bool fp64_ok = built(MRHS_PREC_FP64);
+  const bool oz_ok = built(MRHS_PREC_OZ) && oz_supported(op, nrhs);
   if (p.mode == MRHS_SOLVE_CG5D) {
     mrhs_solve_params q = p;
-    if (q.krylov_prec < 0) q.krylov_prec = MRHS_PREC_FP64;
-    if (q.krylov_prec != MRHS_PREC_FP64 && q.krylov_prec != MRHS_PREC_DF32)
-      return fail(MRHS_ERR_INVALID_ARG, "CG5D runs the FP64 or DF32 operator");
+    MRHS_TRY(resolve_fp64_prec(&q.fp64_prec, fp64_ok, oz_ok));
+    if (q.krylov_prec < 0) q.krylov_prec = q.fp64_prec;
+    if (q.krylov_prec != MRHS_PREC_FP64 && q.krylov_prec != MRHS_PREC_DF32 &&
+        q.krylov_prec != MRHS_PREC_OZ)
+      return fail(MRHS_ERR_INVALID_ARG, "CG5D runs the FP64, DF32 or OZ operator");
+    if ((q.krylov_prec == MRHS_PREC_OZ && !oz_ok) || (q.krylov_prec != MRHS_PREC_OZ && !fp64_ok))
+      return fail(MRHS_ERR_UNSUPPORTED, "CG5D: operator precision not built");
     if (q.precond) return fail(MRHS_ERR_INVALID_ARG, "CG5D takes no preconditioner");
     if (X == B) return fail(MRHS_ERR_INVALID_ARG, "X and B must differ");
     return cg5d(op, (const double2*)B, (double2*)X, nrhs, q, info, (cudaStream_t)stream);
   }
   mrhs_solve_params q = p;   // resolve the automatic precision choices
-  auto built = [&](int pr) { return (op->prec_mask & MRHS_PREC_BIT(pr)) != 0; };
   auto fits = [&](int pr) {
+    if (pr == MRHS_PREC_OZ) return oz_ok;
     return !MRHS_PREC_IS_TC(pr) || tc_supported(op, pr, nrhs) != 0;
   };
+  MRHS_TRY(resolve_fp64_prec(&q.fp64_prec, fp64_ok, oz_ok));
   if (q.mode == MRHS_SOLVE_MIXED) {
-    const bool oz = built(MRHS_PREC_OZ) && oz_supported(op, nrhs);
-    if (q.residual_prec < 0) q.residual_prec = oz ? MRHS_PREC_OZ : MRHS_PREC_DF32;
-    MRHS_TRY(check_residual_prec(q.residual_prec, oz));
+    if (q.residual_prec < 0) q.residual_prec = oz_ok ? MRHS_PREC_OZ : MRHS_PREC_DF32;
+    MRHS_TRY(check_residual_prec(q.residual_prec, fp64_ok, oz_ok));
     if (q.krylov_prec < 0)
       q.krylov_prec = (built(MRHS_PREC_TC32) && fits(MRHS_PREC_TC32)) ? MRHS_PREC_TC32 : MRHS_PREC_FP32;
     if (q.krylov_prec != MRHS_PREC_FP32 && q.krylov_prec != MRHS_PREC_TC32)
@@ -635,7 +653,7 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
   if (q.precond && q.precond_prec < 0) {
     const int order[] = {MRHS_PREC_FP16X, MRHS_PREC_FP16, MRHS_PREC_BF16, MRHS_PREC_TC32,
                          MRHS_PREC_FP32};
-    q.precond_prec = q.mode == MRHS_SOLVE_FP64 ? MRHS_PREC_FP64 : -1;
+    q.precond_prec = q.mode == MRHS_SOLVE_FP64 ? q.fp64_prec : -1;
     if (q.mode == MRHS_SOLVE_MIXED)
       for (int pr : order)
         if (built(pr) && fits(pr)) { q.precond_prec = pr; break; }
@@ -648,8 +666,9 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
       return fail(MRHS_ERR_UNSUPPORTED, "preconditioner precision does not fit this shape");
     if (!built(pp.precond_prec))
       return fail(MRHS_ERR_UNSUPPORTED, "preconditioner precision not built");
-    if (pp.mode == MRHS_SOLVE_FP64 && pp.precond_prec != MRHS_PREC_FP64)
-      return fail(MRHS_ERR_INVALID_ARG, "FP64 mode takes an FP64 preconditioner");
+    if (pp.mode == MRHS_SOLVE_FP64 && pp.precond_prec != MRHS_PREC_FP64 &&
+        pp.precond_prec != MRHS_PREC_OZ)
+      return fail(MRHS_ERR_INVALID_ARG, "FP64 mode takes an FP64 (or OZ) preconditioner");
     if (pp.mode == MRHS_SOLVE_MIXED && MRHS_PREC_IS_WIDE(pp.precond_prec))
       return fail(MRHS_ERR_INVALID_ARG, "mixed mode takes a low-precision preconditioner");
     if (pp.cheb_order < 0) return fail(MRHS_ERR_INVALID_ARG, "cheb_order");
@@ -732,17 +751,22 @@ int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* 
     for (int j = 0; j < i; ++j)
       if (ops[j] == ops[i]) return fail(MRHS_ERR_INVALID_ARG, "an operator appears twice");
     const uint32_t m = ops[i]->prec_mask;
-    if (!(m & MRHS_PREC_BIT(MRHS_PREC_FP64))) return fail(MRHS_ERR_UNSUPPORTED, "FP64 operator needed");
+    const bool oz_i = (m & MRHS_PREC_BIT(MRHS_PREC_OZ)) && oz_supported(ops[i], nrhs[i]);
+    if (!(m & MRHS_PREC_BIT(MRHS_PREC_FP64)) && !oz_i)
+      return fail(MRHS_ERR_UNSUPPORTED, "the FP64 or the OZ operator is needed");
     if (nrhs[i] > 32 || !(m & MRHS_PREC_BIT(MRHS_PREC_TC32))) batched = false;
   }
   // the batched path: TC32 in the Krylov loop and a tensor-core preconditioner
   // shared by all problems; otherwise each problem is solved in turn
   if (batched) {
-    bool oz = true;
-    for (int i = 0; i < n; ++i)
+    bool oz = true, f64 = true;
+    for (int i = 0; i < n; ++i) {
       oz = oz && (ops[i]->prec_mask & MRHS_PREC_BIT(MRHS_PREC_OZ)) && oz_supported(ops[i], nrhs[i]);
+      f64 = f64 && (ops[i]->prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64));
+    }
+    MRHS_TRY(resolve_fp64_prec(&q.fp64_prec, f64, oz));
     if (q.residual_prec < 0) q.residual_prec = oz ? MRHS_PREC_OZ : MRHS_PREC_DF32;
-    MRHS_TRY(check_residual_prec(q.residual_prec, oz));
+    MRHS_TRY(check_residual_prec(q.residual_prec, f64, oz));
     if (q.krylov_prec < 0) q.krylov_prec = MRHS_PREC_TC32;
     if (q.precond_prec < 0) {
       const int order[] = {MRHS_PREC_FP16X, MRHS_PREC_FP16, MRHS_PREC_BF16, MRHS_PREC_TC32};
@@ -794,6 +818,7 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->breakdown_tau = 1e-12;
   p->recycle = 0;
   p->recycle_max_blocks = 0;
+  p->fp64_prec = -1;
 }
 
 }  // extern "C"

@@ -61,7 +61,7 @@ struct TcImage {             // tensor-core packed coefficients (BF16/FP16)
 };
 
 struct OzImage {             // digit-sliced coefficients (op_oz.cu)
-  void* digits = nullptr;    // [V][npts][nb16/16] slabs of 7 fp16 digit tiles
+  void* digits = nullptr;    // [V][npts][nb16/16] slabs of 8 fp16 digit tiles
   double* scale = nullptr;   // [V] power-of-two site scales s_x
   double* diag = nullptr;    // [V] mean real self diagonal d_x (FP64)
   size_t bytes = 0;

@@ -1,4 +1,4 @@
-// Coarse operator Y(x) = sum_p A_p(x) X(x + delta_p) (Sec. 2.6) to FP64-class
+// Coarse operator Y(x) = sum_p A_p(x) X(x + delta_p) (Sec. 2.6) to FP64
 // accuracy on the tcgen05 tensor cores, by digit slicing: the error-free
 // splitting of Ozaki, Ogita, Oishi and Rump (2012) in the fixed-point form
 // that Mukunoki, Ozaki, Ogita and Imamura ("DGEMM using Tensor Cores, and Its
@@ -7,17 +7,20 @@
 // Both operands become fixed-point numbers with few bits per digit:
 //   coefficients, per site x:  A_p(x) - d_x I = s_x 2^-5 sum_s a_s 2^(-6(s-1))
 //   input, per column r:       X[:, r]         = sigma_r 2^-5 sum_t e_t 2^(-6(t-1))
-// with s, t = 1..7, s_x and sigma_r powers of two above the largest entry
+// with s, t = 1..8, s_x and sigma_r powers of two above the largest entry
 // (d_x = mean real self diagonal, applied exactly in FP64), and integer digits
-// |a_s|, |e_t| <= 32, each held exactly by an fp16 code.  A digit product is
-// at most 2^10 and exact in FP32; level c = s + t gathers c - 1 products per
-// term, so a level sum over npts * nb terms stays below 2^24 -- exact in the
-// FP32 tensor-memory accumulator -- for c <= 5 at 81 x 48 terms; deeper levels
+// |a_s|, |e_t| <= 32, each held exactly by an fp16 code; the representation
+// error is 2^-48 of the scale.  A digit product is at most 2^10 and exact in
+// FP32; level c = s + t gathers c - 1 products per term, so a level sum over
+// npts * nb terms stays below 2^24 -- exact in the FP32 tensor-memory
+// accumulator -- for c <= 5 at 81 x 48 terms in the worst case; deeper levels
 // sit 2^-24 below the first and their rounding is far below the target.
-// Levels c <= 8 are kept (the dropped ones are below 2^-42 of the scales):
-//   Y = s_x sigma_r 2^-46 sum_c D_c 2^(6 (8 - c)) + d_x X,
-// and with |D_c| < 2^25 the sum fits an int64 exactly; one rounding to FP64
-// follows.
+// Levels c <= 9 are kept (the first dropped one, c = 10, is 2^-48 of the
+// scales per term):
+//   Y = s_x sigma_r 2^-46 (sum_{c<=8} D_c 2^(6 (8 - c)) + rint(D_9 2^-6)) + d_x X;
+// with |D_c| < 2^25 the sum fits an int64 exactly; level 9 enters rounded to
+// the unit of level 8 (half a unit per contribution), and one rounding to
+// FP64 follows.
 //
 // Tensor-core mapping (M = input rows, N = coefficient rows, as in op_tc.cu):
 // digit t of the input is a block of 2 rb rows [Re X_t ; Im X_t] (rb =
@@ -26,7 +29,7 @@
 // (j = 0..3, 128 TMEM columns apart) holds levels (2j + 2, 2j + 3) on its two
 // row halves: for coefficient digit s it receives the MMA of window
 // [X_(c-s) ; X_(c+1-s)], c = 2j + 2, against the [Re A_s ; Im A_s] tile.
-// 2 + 4 + 6 + 7 = 19 MMAs (M = 128, N = 2 nb8, K = 16) per stencil point and
+// 2 + 4 + 6 + 8 = 20 MMAs (M = 128, N = 2 nb8, K = 16) per stencil point and
 // 16-column K step.  The epilogue converts each level sum to an integer,
 // weights it by its power of two in int64, combines the Xi rows' and the
 // upper level's contributions with the Xr rows' through shared memory (as
@@ -57,10 +60,10 @@ __device__ unsigned int g_oz_error = 0;
 
 namespace {
 
-constexpr int kDigits = 7;        // digits per operand
+constexpr int kDigits = 8;        // digits per operand
 constexpr int kBeta = 6;          // bits per digit
 constexpr int kTopShift = 5;      // first digit: |a_1| <= 2^5
-constexpr int kLevels = 8;        // levels 2..8 kept
+constexpr int kLevels = 8;        // levels 2..8 combined exactly, level 9 rounded into them
 constexpr int kNormShift = 2 * kTopShift + (kLevels - 2) * kBeta;   // 46
 constexpr int kThreads = 192;
 constexpr int kAccCols = 128;
@@ -75,14 +78,15 @@ constexpr size_t kSmemOneCta = 120 * 1024;
 // One MMA of a stage: input window w (digit blocks w, w + 1), coefficient
 // digit sd, accumulator acc (levels 2 acc + 2 and 2 acc + 3 = w + sd and
 // w + sd + 1); first: the accumulator's first MMA of a site; coll: 0 alone,
-// 1 fill, 2 use, 3 lastuse of the A collector.  Ordered by window.
+// 1 fill, 2 use, 3 lastuse of the A collector.  Ordered by window, so the
+// MMAs of one window share its A operand.
 struct OzMma {
   int8_t w, sd, acc, first, coll;
 };
-constexpr int kOzMmas = 19;
+constexpr int kOzMmas = 20;
 __device__ __constant__ const OzMma kOzOrder[kOzMmas] = {
-    {0, 2, 0, 1, 1}, {0, 4, 1, 1, 2}, {0, 6, 2, 1, 3},
-    {1, 1, 0, 0, 1}, {1, 3, 1, 0, 2}, {1, 5, 2, 0, 2}, {1, 7, 3, 1, 3},
+    {0, 2, 0, 1, 1}, {0, 4, 1, 1, 2}, {0, 6, 2, 1, 2}, {0, 8, 3, 1, 3},
+    {1, 1, 0, 0, 1}, {1, 3, 1, 0, 2}, {1, 5, 2, 0, 2}, {1, 7, 3, 0, 3},
     {2, 2, 1, 0, 1}, {2, 4, 2, 0, 2}, {2, 6, 3, 0, 3},
     {3, 1, 1, 0, 1}, {3, 3, 2, 0, 2}, {3, 5, 3, 0, 3},
     {4, 2, 2, 0, 1}, {4, 4, 3, 0, 3},
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---------------- MMA issuer: 19 MMAs per stage
+      // ---------------- MMA issuer: 20 MMAs per stage
       const uint32_t idesc = od.idesc, zb = g.zbytes, aslice = (uint32_t)g.N * 32u;
       const uint32_t aslab = g.aslab;
       int s = 0;
@@ -463,9 +467,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sa = ptx::smem_u32(stages + (size_t)s * stage_bytes);
             const uint32_t sz = sa + aslab;           // X_0, then X_1..X_7
             const bool first = p == 0 && j == 0;
-            // the 19 MMAs grouped by input window [X_w ; X_(w+1)]: those of one
+            // the 20 MMAs grouped by input window [X_w ; X_(w+1)]: those of one
             // window share the A operand through the tensor core's collector,
-            // so shared memory serves 8 window reads instead of 19
+            // so shared memory serves 8 window reads instead of 20
 #pragma unroll
             for (int m = 0; m < kOzMmas; ++m) {
               const OzMma& q = kOzOrder[m];
@@ -532,21 +536,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           float u[kChunk], w[kChunk];
           ptx::tmem_ld8_sync(taddr + (uint32_t)(a * kAccCols + c0), u);
           ptx::tmem_ld8_sync(taddr + (uint32_t)(a * kAccCols + nbp8 + c0), w);
-          // level 2a + 2 + up, weight 2^(6 (8 - level)); level 9 is dropped
+          // level 2a + 2 + up, weight 2^(6 (8 - level)); level 9 (a = 3,
+          // upper half) enters rounded to the unit of level 8 (the product
+          // by 2^-6 is exact in FP32)
           const int sh = kBeta * (kLevels - 2 - 2 * a - up);
-          if (sh >= 0) {
-            const long long f = 1ll << sh;
 #pragma unroll
-            for (int e = 0; e < kChunk; ++e) {
-              const long long iu = (long long)__float2int_rn(u[e]) * f;
-              const long long iw = (long long)__float2int_rn(w[e]) * f;
-              if (!imag) {        // Re X row: (Re A x, Im A x)
-                vre[e] += iu;
-                vim[e] += iw;
-              } else {            // Im X row: (-Im A x, Re A x)
-                vre[e] -= iw;
-                vim[e] += iu;
-              }
+          for (int e = 0; e < kChunk; ++e) {
+            long long iu, iw;
+            if (sh >= 0) {
+              iu = (long long)__float2int_rn(u[e]) << sh;
+              iw = (long long)__float2int_rn(w[e]) << sh;
+            } else {
+              iu = __float2ll_rn(u[e] * 0.015625f);
+              iw = __float2ll_rn(w[e] * 0.015625f);
+            }
+            if (!imag) {          // Re X row: (Re A x, Im A x)
+              vre[e] += iu;
+              vim[e] += iw;
+            } else {              // Im X row: (-Im A x, Re A x)
+              vre[e] -= iw;
+              vim[e] += iu;
             }
           }
         }
@@ -604,7 +613,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Shared memory of a launch: barriers (1 KB), the ring, the two exchange
 // buffers, and the rows an M = 128 operand read runs past the last stage's
-// input area (a window starts at most 14 rb rows in, the area holds 16 rb).
+// input area (a window starts at most 2 (kDigits - 1) rb rows in, the area
+// holds 2 (kDigits + 1) rb; rows of D beyond 4 rb are never read).
 struct OzRing {
   int nstages = 0;
   size_t smem = 0;
@@ -613,7 +623,7 @@ struct OzRing {
 OzRing plan_oz_ring(const OzGeom& g) {
   OzRing out;
   const size_t ex = 2 * (size_t)3 * g.rb * 2 * kChunk * sizeof(long long);
-  const int over = kM - 2 * g.rb;
+  const int over = kM - 4 * g.rb;
   const size_t tail = (size_t)(over > 0 ? over : 0) * 32u;
   const size_t fixed = 1024 + ex + tail;
   if (kSmemBudget < fixed + 2 * (size_t)g.stage) return out;

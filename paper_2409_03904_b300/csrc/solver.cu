@@ -1133,12 +1133,14 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       if (bnorm[j] > 0 && !(rnorm[j] <= p.tol * bnorm[j])) return false;
     return true;
   };
-  // the cycle residual in residual_prec; one that meets tol is confirmed in
-  // FP64, so convergence is always decided on an FP64 residual
-  const int res_prec = (mixed && p.residual_prec >= 0) ? p.residual_prec : MRHS_PREC_FP64;
+  // the cycle residual in residual_prec; one that meets tol is confirmed with
+  // the FP64 operator (fp64_prec: native FP64 or the digit-sliced OZ form), so
+  // convergence is always decided on an FP64 residual
+  const int f64 = p.fp64_prec;
+  const int res_prec = (mixed && p.residual_prec >= 0) ? p.residual_prec : f64;
   auto true_residual = [&]() -> int {
     MRHS_TRY(residual_in(res_prec));
-    if (res_prec != MRHS_PREC_FP64 && all_done()) MRHS_TRY(residual_in(MRHS_PREC_FP64));
+    if (res_prec != f64 && all_done()) MRHS_TRY(residual_in(f64));
     return MRHS_OK;
   };
   // a zero initial guess needs no operator application: r = B
@@ -1180,7 +1182,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     cycles = 0;
     if (!all_done()) {
       int it = 0;
-      MRHS_TRY(run_bcg<double2>(cx, sb.b64, MRHS_PREC_FP64, B, X, target.data(), p.precond != 0,
+      MRHS_TRY(run_bcg<double2>(cx, sb.b64, f64, B, X, target.data(), p.precond != 0,
                                 p.precond_prec, lo, hi, p.cheb_order, p.maxiter, every, &it,
                                 &flag, nullptr, false, x0_zero));
       total_iters = it;
@@ -1233,7 +1235,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       total_iters += it;
       { k_update_x<<<g, kThreads, 0, s>>>(X, sb.e32, sb.rho_d, cx.N, R); ::mrhs::count_launch(); }
       MRHS_CUDA_TRY(cudaGetLastError());
-      if (final_cycle) MRHS_TRY(residual_in(MRHS_PREC_FP64));
+      if (final_cycle) MRHS_TRY(residual_in(f64));
       else MRHS_TRY(true_residual());
       // a cycle that started from kept blocks and made no progress on some
       // column ends the recycling for this solve (plain restarts follow)
@@ -1264,7 +1266,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       info->resid[j] = j < R ? (bnorm[j] > 0 ? rnorm[j] / bnorm[j] : 0.0) : 0.0;
     info->cheb_lo = lo;
     info->cheb_hi = hi;
-    info->krylov_prec = mixed ? p.krylov_prec : MRHS_PREC_FP64;
+    info->krylov_prec = mixed ? p.krylov_prec : f64;
     info->precond_prec = p.precond ? p.precond_prec : -1;
   }
   MRHS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1424,13 +1426,15 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
       if (b.bnorm[j] > 0 && !(b.rnorm[j] <= p.tol * b.bnorm[j])) return false;
     return true;
   };
-  // the cycle residual in residual_prec, confirmed in FP64 once it meets tol
-  const int res_prec = p.residual_prec >= 0 ? p.residual_prec : MRHS_PREC_FP64;
+  // the cycle residual in residual_prec, confirmed with the FP64 operator
+  // (fp64_prec) once it meets tol
+  const int f64 = p.fp64_prec;
+  const int res_prec = p.residual_prec >= 0 ? p.residual_prec : f64;
   auto true_residual = [&](BatchProb& b, int i) -> int {
     MRHS_TRY(residual_in(b, i, res_prec));
-    if (res_prec != MRHS_PREC_FP64) {
+    if (res_prec != f64) {
       MRHS_CUDA_TRY(cudaStreamSynchronize(s));
-      if (problem_done(b)) MRHS_TRY(residual_in(b, i, MRHS_PREC_FP64));
+      if (problem_done(b)) MRHS_TRY(residual_in(b, i, f64));
     }
     return MRHS_OK;
   };
@@ -1752,7 +1756,7 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
       BatchProb& b = P[i];
       Ctx& cx = b.cx;
       { k_update_x<<<grid_for(cx.N * cx.R), kThreads, 0, s>>>(X[i], b.sb.e32, b.sb.rho_d, cx.N, cx.R); ::mrhs::count_launch(); }
-      if (b.final_cycle) MRHS_TRY(residual_in(b, i, MRHS_PREC_FP64));
+      if (b.final_cycle) MRHS_TRY(residual_in(b, i, f64));
       else MRHS_TRY(true_residual(b, i));
     }
     MRHS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1965,8 +1969,8 @@ int cg5d(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_pa
     if (!finite) break;
     done = all_done();
   }
-  // true residual with the FP64 operator
-  MRHS_TRY(cx.apply(MRHS_PREC_FP64, X, w));
+  // true residual with the FP64 operator (fp64_prec)
+  MRHS_TRY(cx.apply(p.fp64_prec, X, w));
   { k_sub<double2><<<g, kThreads, 0, s>>>(w, B, w, n); ::mrhs::count_launch(); }
   MRHS_TRY(cx.colnorms<double2>(w, rnorm_d));
   MRHS_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), rnorm_d, sizeof(double) * R, cudaMemcpyDeviceToHost, s));

@@ -18,8 +18,8 @@ def test_operator_bytes_by_hand():
     assert bench.op_bytes(W, R, "fp64") == 81 * V * 48 * 48 * 16 + 2 * V * 48 * R * 16
     # TC32: hi and lo fp16 codes, 8 bytes per complex coefficient
     assert bench.op_bytes(W, R, "tc32") - bench.op_bytes(W, R, "fp16") == coef_fp16
-    # the digit image: 7 fp16 digits of Re and Im, a double scale and diagonal
-    assert bench.op_bytes(W, R, "oz") == 81 * V * 48 * 48 * 28 + 16 * V + 2 * V * 48 * R * 16
+    # the digit image: 8 fp16 digits of Re and Im, a double scale and diagonal
+    assert bench.op_bytes(W, R, "oz") == 81 * V * 48 * 48 * 32 + 16 * V + 2 * V * 48 * R * 16
 
 
 def test_operator_flops():
