@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--defl-prec", default="fp16",
                     choices=["fp64", "df32", "fp32", "bf16", "fp16", "fp16x", "tc32"])
     ap.add_argument("--blocking", action="store_true",
-                    help="time block project / promote (Sec. 3.4) at the Table 6 shape")
+                    help="time block project / promote (Sec. 2.5.1) at the Table 6 shape")
     ap.add_argument("--blocks", default="4096,256,64",
                     help="n_blocks,v_block,n_basis for --blocking (nrhs from --nrhs, default 12)")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
@@ -96,7 +96,7 @@ def parse():
                     help="batched solve of independent problems against one-at-a-time solves: "
                          "twelve problems of uneven L, nb and nrhs, or twelve 4^4 problems")
     ap.add_argument("--cg5d", action="store_true",
-                    help="one CG on the enlarged 5D system (Sec. 2.2) against FP64 block CG")
+                    help="one CG on the enlarged 5D system (Sec. 2.1) against FP64 block CG")
     ap.add_argument("--coarsen", default=None, metavar="LF,BLOCK,NBF,NBASIS",
                     help="time coarsening an 81-point fine operator, e.g. 8,2,12,24: fine "
                          "lattice 8^4, 2^4 blocks, 12 fine components, 24 basis vectors")

@@ -170,10 +170,16 @@ int block_inner(const void* X, const void* Y, void* G, int64_t N, int32_t rx, in
  *   fit, so the summation order (not the result beyond rounding) may differ
  *   from block_inner's.
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share the array: calls that overlap
- * on the GPU race and give wrong results.  Each call writes every partial it
- * reads, so nothing carries over between calls. */
+ * device current (cudaGetSymbolAddress); under CUDA's lazy module loading
+ * (the default) that lookup is also what loads the library's device code on
+ * the device and creates the array, so the first call may take device memory
+ * (and fails with MRHS_ERR_CUDA if none is left); later calls take none.
+ * Make that first call at set-up (N = 0 is enough), before any stream
+ * capture.  The address is cached per device for the life of the process:
+ * do not use the library across a cudaDeviceReset.  All calls on a device
+ * share the array: calls that overlap on the GPU race and give wrong
+ * results.  Each call writes every partial it reads, so nothing carries over
+ * between calls. */
 int block_inner_noalloc(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
                         int32_t dtype, void* stream);
 
@@ -208,7 +214,7 @@ int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, c
                 void* P, int32_t nrhs, void* stream);
 
 /* Block project and promote between fine and coarse degrees of freedom
- * (Sec. 3.4): one GEMM per coarse site x,
+ * (Sec. 2.5.1, "Transfer between grids"): one GEMM per coarse site x,
  *   block_project:  C(x) = B(x)^dagger F(x)   (n_basis x nrhs)
  *   block_promote:  F(x) = B(x) C(x)          (v_block x nrhs)
  * basis: device [n_blocks][v_block][n_basis]; F: device
@@ -223,7 +229,7 @@ int block_project(const void* basis, const void* F, void* C, int64_t n_blocks, i
 int block_promote(const void* basis, const void* C, void* F, int64_t n_blocks, int32_t v_block,
                   int32_t n_basis, int32_t nrhs, int32_t dtype, void* stream);
 
-/* Coarse operator of a fine one on a blocked basis (Sec. 3.4, "Coarse
+/* Coarse operator of a fine one on a blocked basis (Sec. 2.6, "Coarse
  * operator"): A_p(b)[j][k] = <phi_j^b | M | phi_k^(b + delta_p)> for the npts
  * coarse displacements disp (host int8 [npts][4] in {-1,0,1}, distinct; they
  * must cover every coarse coupling of M, which holds for the full 81-point
@@ -343,7 +349,7 @@ enum {
                            CG on complex64 vectors with the TC32 (or FP32)
                            operator and the low-precision Chebyshev
                            preconditioner */
-  MRHS_SOLVE_CG5D = 2   /* Sec. 2.2's single five-dimensional system: plain
+  MRHS_SOLVE_CG5D = 2   /* Sec. 2.1's single five-dimensional system: plain
                            CG on the whole block, alpha and beta from inner
                            products summed over all right-hand sides, no
                            preconditioner; operator krylov_prec = FP64 (default,

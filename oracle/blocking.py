@@ -1,5 +1,5 @@
 """Block project and promote between fine and coarse degrees of freedom
-(Sec. 3.4, "Block project / promote"), complex128.
+(Sec. 2.5.1, "Transfer between grids"), complex128.
 
 Test infrastructure only (see the package docstring).
 

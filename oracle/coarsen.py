@@ -1,4 +1,4 @@
-"""Coarsening a fine stencil operator onto a blocked basis (Sec. 3.4,
+"""Coarsening a fine stencil operator onto a blocked basis (Sec. 2.6,
 "Coarse operator"), complex128.
 
 Test infrastructure only (see the package docstring).

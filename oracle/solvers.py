@@ -258,7 +258,7 @@ def lanczos_extremes(apply_H, v0, steps):
 
 
 def cg5d(apply_H, B, X0=None, tol=1e-10, maxiter=1000, history=None):
-    """Conjugate gradients on the enlarged system (Sec. 2.2: the coarse solve
+    """Conjugate gradients on the enlarged system (Sec. 2.1: the coarse solve
     treated as one five-dimensional system with a single Krylov space, block
     diagonal in the right-hand-side index).  The vector is the whole block
     [V][nb][R]; alpha and beta come from inner products summed over all

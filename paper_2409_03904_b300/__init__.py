@@ -319,7 +319,7 @@ def _dtype_code(t):
 
 
 def block_project(basis, F):
-    """C[x] = basis[x]^dagger F[x] per coarse site x (Sec. 3.4): basis
+    """C[x] = basis[x]^dagger F[x] per coarse site x (Sec. 2.5.1): basis
     [n_blocks][v_block][n_basis], F [n_blocks][v_block][nrhs] -> C
     [n_blocks][n_basis][nrhs]; complex128 (FP64) or complex64 (FP32)."""
     nblk, vb, nbasis = (int(v) for v in basis.shape)
@@ -334,7 +334,7 @@ def block_project(basis, F):
 
 
 def block_promote(basis, C):
-    """F[x] = basis[x] C[x] per coarse site x (Sec. 3.4): basis
+    """F[x] = basis[x] C[x] per coarse site x (Sec. 2.5.1): basis
     [n_blocks][v_block][n_basis], C [n_blocks][n_basis][nrhs] -> F
     [n_blocks][v_block][nrhs]; complex128 (FP64) or complex64 (FP32)."""
     nblk, vb, nbasis = (int(v) for v in basis.shape)

@@ -1,5 +1,5 @@
 // Block project / promote between fine and coarse degrees of freedom
-// (Sec. 3.4): one small complex GEMM per coarse site x,
+// (Sec. 2.5.1, "Transfer between grids"): one small complex GEMM per coarse site x,
 //   project:  C(x) = B(x)^dagger F(x)   (n_basis x nrhs)
 //   promote:  F(x) = B(x) C(x)          (v_block x nrhs)
 // with the basis B [n_blocks][v_block][n_basis], fine vectors

@@ -1,4 +1,4 @@
-// Coarsening a fine stencil operator onto a blocked basis (Sec. 3.4, "Coarse
+// Coarsening a fine stencil operator onto a blocked basis (Sec. 2.6, "Coarse
 // operator"), FP64.
 //
 // The fine operator is one of this library's operators (a stencil inside

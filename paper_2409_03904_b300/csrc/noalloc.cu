@@ -12,11 +12,20 @@
 // so the call itself allocates nothing.
 //
 // The array is kStaticSlots complex128 values (2 MiB); every GPU that loads
-// the library holds it until the process exits.  All calls on a device share
-// it: calls whose kernels overlap on the GPU (for example issued on two
-// streams without ordering) race on it and give wrong results.  Each call
-// writes every partial it later reads, so no state carries over from the
-// previous call and nothing needs clearing.
+// the library holds it until the process exits.  With CUDA's lazy module
+// loading (the default) the array is created when the library's device code
+// is first loaded on a device, which the first call here triggers through
+// cudaGetSymbolAddress: that first call on each device may therefore take
+// device memory (and can fail if none is left), later calls take none.  A
+// caller that must not allocate inside its loop makes one call at set-up
+// (N = 0 is enough), with the device current and before any stream capture.
+// All calls on a device share the array: calls whose kernels overlap on the
+// GPU (for example issued on two streams without ordering) race on it and
+// give wrong results.  Each call writes every partial it later reads, so no
+// state carries over from the previous call and nothing needs clearing.
+// The device address is cached per device for the life of the process; the
+// library (this entry point, and every operator) must not be used across a
+// cudaDeviceReset, after which the cached address is no longer valid.
 #include <mutex>
 
 #include "internal.cuh"

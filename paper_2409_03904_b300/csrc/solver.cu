@@ -1809,7 +1809,7 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
 }  // namespace mrhs
 
 // ---------------------------------------------------------------- 5D CG
-// The coarse solve as one enlarged five-dimensional system (Sec. 2.2): plain
+// The coarse solve as one enlarged five-dimensional system (Sec. 2.1): plain
 // CG on the whole [V][nb][R] block, alpha and beta from inner products summed
 // over every right-hand side, so the block algebra is two scalar reductions
 // and three vector updates per iteration instead of Grams and a Hermitian

@@ -57,3 +57,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     G = torch.zeros((65, 65), dtype=torch.complex128, device="cuda")
     assert _noalloc(lib, X, X, G, 16, 65, 65, mrhs.C128) == -1
     assert b"64" in lib.mrhs_last_error()
+
+
+def test_noalloc_takes_no_device_memory_after_set_up():
+    """After one set-up call (which loads the library's device code and so
+    its static array), calls with shapes that would make block_inner grow its
+    workspace leave the device's free memory unchanged."""
+    import paper_2409_03904_b300 as mrhs
+    lib = mrhs._lib.lib()
+    shapes = ((4096, 8, 8), (1000003, 64, 64), (300001, 48, 17))
+    rng = np.random.default_rng(77)
+    bufs = []
+    for N, rx, ry in shapes:
+        X = torch.from_numpy(rng.standard_normal((N, rx)) + 1j * rng.standard_normal((N, rx))).cuda()
+        Y = torch.from_numpy(rng.standard_normal((N, ry)) + 1j * rng.standard_normal((N, ry))).cuda()
+        G = torch.empty((rx, ry), dtype=torch.complex128, device="cuda")
+        bufs.append((X, Y, G, N, rx, ry))
+    Z = torch.zeros((1, 1), dtype=torch.complex128, device="cuda")
+    assert _noalloc(lib, Z, Z, Z, 0, 1, 1, mrhs.C128) == 0      # set-up call
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for X, Y, G, N, rx, ry in bufs:
+        assert _noalloc(lib, X, Y, G, N, rx, ry, mrhs.C128) == 0, lib.mrhs_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    X, Y, G, N, rx, ry = bufs[1]
+    ref = X.conj().T @ Y
+    assert float(torch.linalg.norm(G - ref)) <= 1e-13 * float(torch.linalg.norm(X) * torch.linalg.norm(Y))
