@@ -6,6 +6,9 @@ and autograd bookkeeping only here):
                  grad A = grad Y X^dagger on the stencil (coarse_op_outer);
 * coarse_solve:  grad B = H^-1 grad X (block CG again: H is Hermitian, so
                  H^-dagger = H^-1), grad A = -grad B X^dagger on the stencil.
+                 B may be complex128 or complex64; a complex64 B gives a
+                 complex64 X and grad B (the solve itself runs on complex128
+                 vectors, in the mode the options choose, e.g. "mixed").
 Coefficients A are complex128 [V][npts][nb][nb]; each entry is an independent
 parameter (a perturbation that breaks Hermiticity is outside what the solve
 accepts, so finite-difference checks of the solve use Hermitian directions).
@@ -41,18 +44,18 @@ class _Solve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, A, B, L, disp, opts):
         op = CoarseOp(A.detach().contiguous(), L, disp, opts.pop("precisions", ("fp64", "fp32")))
-        X, info = op.solve(B.detach().contiguous(), **opts)
-        ctx.op, ctx.opts = op, opts
+        X, info = op.solve(B.detach().to(torch.complex128).contiguous(), **opts)
+        ctx.op, ctx.opts, ctx.dtype = op, opts, B.dtype
         ctx.save_for_backward(X)
         ctx.info = info
-        return X
+        return X.to(B.dtype)
 
     @staticmethod
     def backward(ctx, gX):
         (X,) = ctx.saved_tensors
-        gB, _ = ctx.op.solve(gX.contiguous(), **ctx.opts)
+        gB, _ = ctx.op.solve(gX.to(torch.complex128).contiguous(), **ctx.opts)
         gA = ctx.op.outer(gB, X, -1.0) if ctx.needs_input_grad[0] else None
-        return gA, (gB if ctx.needs_input_grad[1] else None), None, None, None
+        return gA, (gB.to(ctx.dtype) if ctx.needs_input_grad[1] else None), None, None, None
 
 
 def coarse_apply(A, X, L, disp, prec="fp64"):

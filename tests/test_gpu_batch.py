@@ -89,7 +89,8 @@ def test_batch_solve_against_oracle(mrhs):
 def test_full_batch_of_twelve(mrhs):
     """All twelve problems (lattices 4^4..8^4, nb 24..48, 9/81 points, 4..24
     RHS) in one batched solve; the residual of each is checked by the C
-    oracle on a sample of sites."""
+    oracle on a sample of sites, against the solve tolerance times the
+    column's global |b_j| (|(b - Hx)_S| <= |b - Hx| <= tol |b|)."""
     import synth.device as sdev
     ops, Bs = [], []
     for w in BATCH:
@@ -109,8 +110,8 @@ def test_full_batch_of_twelve(mrhs):
         Xh, Bh = X.cpu().numpy(), B.cpu().numpy()
         Y = native.coarse_op_apply_sites(A_s, Xh, w["L"], disp, sites)
         r = np.linalg.norm((Bh[sites] - Y).reshape(-1, w["nrhs"]), axis=0)
-        bs = np.linalg.norm(Bh[sites].reshape(-1, w["nrhs"]), axis=0)
-        assert np.max(r / bs) <= 1e-6
+        bn = np.linalg.norm(Bh.reshape(-1, w["nrhs"]), axis=0)
+        assert np.max(r / bn) <= 1.5e-8, w["name"]
 
 
 def test_autotune_single_and_batch(mrhs):

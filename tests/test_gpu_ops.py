@@ -106,16 +106,22 @@ def test_fp16x_is_linear_and_tc32_is_fp32_class(mrhs):
     assert e32 <= 1e-5 and ef <= 1e-5
 
 
-@pytest.mark.parametrize("kind", ["bf16", "fp16"])
-def test_tensor_core_dag(mrhs, kind):
-    L, nb, npts, R = (3, 2, 3, 2), 16, 81, 8
+@pytest.mark.parametrize("kind", ["bf16", "fp16", "fp16x", "tc32"])
+@pytest.mark.parametrize("L,nb,npts,R", [((3, 2, 3, 2), 16, 81, 8), ((3, 2, 2, 2), 48, 81, 32),
+                                         ((2, 2, 3, 3), 24, 9, 5)])
+def test_tensor_core_dag(mrhs, kind, L, nb, npts, R):
+    """The adjoint applications of all four tensor-core forms (a daggered
+    packed image built on first use) against the quantised oracle of the
+    daggered coefficient field and against the exact FP64 adjoint at the
+    forms' analytic bounds."""
     disp, _ = stencil(npts)
-    rng = np.random.default_rng(7)
+    rng = np.random.default_rng(7 + nb)
     V = int(np.prod(L))
     A = rng.standard_normal((V, npts, nb, nb)) + 1j * rng.standard_normal((V, npts, nb, nb))
     X = vectors(L, nb, R, 7)
     op = mrhs.CoarseOp(dev(A), L, disp, ("fp64", kind))
     Y = op.apply_dag(dev(X.astype(np.complex64)), kind).cpu().numpy()
+    assert mrhs.device_error() == 0
     # the daggered operator's own coefficient field, quantised by the same rule
     from oracle.ops import neighbour_table
     back = neighbour_table(L, -disp.astype(np.int64))
@@ -124,6 +130,9 @@ def test_tensor_core_dag(mrhs, kind):
         Ad[:, p] = np.conj(np.swapaxes(A[back[p], p], -1, -2))
     ref = lowprec_apply(Ad, X, L, -disp.astype(np.int64), kind)
     assert rel_per_rhs(Y, ref) <= 1e-5
+    exact = coarse_op_apply_dag(A, X, L, disp)
+    bound = {"bf16": 2.0 ** -6, "fp16": 2.0 ** -9, "fp16x": 2.0 ** -9, "tc32": 2.0 ** -17}[kind]
+    assert rel_per_rhs(Y, exact) <= bound
 
 
 def test_tc_repeat_and_large_nrhs_stream(mrhs):
