@@ -117,6 +117,45 @@ typedef struct mrhs_op_s* mrhs_op;
 int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts,
                    const int8_t* disp, const void* A, uint32_t prec_mask, void* stream);
 
+/* One rank's part of a coarse operator on a 4D-decomposed lattice (Sec. 2.6,
+ * "Applying the coarse operator": the input vector lives on the padded local
+ * volume that includes the ghost zones, the result on the owned local volume
+ * only, the coefficients stay local).
+ *   L      host int32[4]: the local (owned) extents; V = prod(L) output sites
+ *   halo   host int32[4], each 0 or 1: a ghost layer of depth 1 on both sides
+ *          of dimension mu.  Input vectors are [Vin][nb][nrhs] on the padded
+ *          lattice Lin = L + 2 halo (site index over Lin, first dimension
+ *          fastest); owned site x with coordinates c reads its neighbour
+ *          c + halo + delta_p of the input without wrapping in a padded
+ *          dimension and with periodic wrap (on L) in the others.  Every
+ *          input site an application reads must be filled by the caller
+ *          (mrhs_gather_rows / mrhs_scatter_rows and a message exchange).
+ *   A      device complex128 [V][npts][nb][nb]: the owned sites' coefficients
+ *   prec_mask  FP64, FP32, DF32 and OZ only (MRHS_ERR_UNSUPPORTED otherwise)
+ * Only coarse_op_apply takes such an operator; the adjoint, the solvers and
+ * the other operator calls return MRHS_ERR_UNSUPPORTED (they need the whole
+ * periodic lattice; the decomposed solve is driven from the host, see
+ * domain.py).  halo = {0,0,0,0} gives the same operator as mrhs_op_create.
+ * Synchronises `stream`. */
+int mrhs_op_create_halo(mrhs_op* out, const int32_t L[4], const int32_t halo[4], int32_t nb,
+                        int32_t npts, const int8_t* disp, const void* A, uint32_t prec_mask,
+                        void* stream);
+
+/* Row copies between a site-indexed array and a contiguous buffer, for the
+ * ghost-zone exchange of Sec. 2.6 (faces are gathered into message buffers,
+ * received messages scattered into the ghost layers, one dimension after the
+ * other so that corner sites travel through the earlier dimensions' layers):
+ *   mrhs_gather_rows:  dst[i] = src[idx[i]],   i < n  (src has src_rows rows)
+ *   mrhs_scatter_rows: dst[idx[i]] = src[i],   i < n  (dst has dst_rows rows)
+ * A row is row_bytes bytes (a positive multiple of 16; for a vector block,
+ * nb * nrhs * element size).  src, dst: device, 16-byte aligned; idx: device
+ * int64[n].  An index outside [0, rows) is skipped.  Indices of a scatter
+ * must be distinct.  Asynchronous on `stream`. */
+int mrhs_gather_rows(const void* src, int64_t src_rows, const int64_t* idx, int64_t n, void* dst,
+                     int64_t row_bytes, void* stream);
+int mrhs_scatter_rows(const void* src, int64_t n, const int64_t* idx, void* dst,
+                      int64_t dst_rows, int64_t row_bytes, void* stream);
+
 /* Release the operator and its device copies (after its last use is done). */
 int mrhs_op_destroy(mrhs_op op);
 

@@ -47,10 +47,16 @@ class CoarseOp:
     from the FP64 copy).  The operator keeps its own packed copies.
     """
 
-    def __init__(self, A, L, disp, precisions=("fp64", "fp32")):
+    def __init__(self, A, L, disp, precisions=("fp64", "fp32"), halo=None):
+        """halo: None, or 4 ints in {0, 1}: one rank's part of a decomposed
+        lattice (mrhs_op_create_halo) -- L are the owned extents, inputs live
+        on the padded lattice L + 2 halo, outputs on L; only apply() works."""
         l = _lib.lib()
         self.L = tuple(int(v) for v in L)
         self.V = int(np.prod(self.L))
+        self.halo = tuple(int(v) for v in halo) if halo is not None else (0, 0, 0, 0)
+        self.Lin = tuple(a + 2 * h for a, h in zip(self.L, self.halo))
+        self.Vin = int(np.prod(self.Lin))
         disp = np.ascontiguousarray(np.asarray(disp, dtype=np.int8).reshape(-1, 4))
         self.npts = disp.shape[0]
         if A.dim() != 4 or A.shape[0] != self.V or A.shape[1] != self.npts or A.shape[2] != A.shape[3]:
@@ -69,10 +75,17 @@ class CoarseOp:
         Lc = (ctypes.c_int32 * 4)(*self.L)
         h = ctypes.c_void_p()
         with torch.cuda.device(A.device):
-            _lib.check(l.mrhs_op_create(ctypes.byref(h), Lc, self.nb, self.npts,
-                                        disp.ctypes.data_as(ctypes.c_void_p),
-                                        _lib.dev_ptr(A, torch.complex128, "A"), mask,
-                                        _lib.stream_ptr()))
+            if halo is None:
+                _lib.check(l.mrhs_op_create(ctypes.byref(h), Lc, self.nb, self.npts,
+                                            disp.ctypes.data_as(ctypes.c_void_p),
+                                            _lib.dev_ptr(A, torch.complex128, "A"), mask,
+                                            _lib.stream_ptr()))
+            else:
+                Hc = (ctypes.c_int32 * 4)(*self.halo)
+                _lib.check(l.mrhs_op_create_halo(ctypes.byref(h), Lc, Hc, self.nb, self.npts,
+                                                 disp.ctypes.data_as(ctypes.c_void_p),
+                                                 _lib.dev_ptr(A, torch.complex128, "A"), mask,
+                                                 _lib.stream_ptr()))
         self._h = h
         self.device = A.device
         self.disp = disp
@@ -90,9 +103,14 @@ class CoarseOp:
 
     def _apply(self, fn, X, prec, out):
         dt = _lib.vec_dtype(prec)
-        if X.shape[:2] != (self.V, self.nb):
-            raise ValueError(f"X must be [V][nb][nrhs], got {tuple(X.shape)}")
-        Y = torch.empty_like(X) if out is None else out
+        if X.shape[:2] != (self.Vin, self.nb):
+            raise ValueError(f"X must be [{self.Vin}][nb][nrhs], got {tuple(X.shape)}")
+        if out is None:
+            Y = torch.empty((self.V,) + tuple(X.shape[1:]), dtype=X.dtype, device=X.device)
+        else:
+            Y = out
+            if Y.shape != (self.V,) + tuple(X.shape[1:]):
+                raise ValueError("out must be [V][nb][nrhs]")
         fn(self._h, PREC[prec], _lib.dev_ptr(X, dt, "X"), _lib.dev_ptr(Y, dt, "Y"),
            int(X.shape[2]), _lib.stream_ptr())
         return Y

@@ -80,6 +80,9 @@ P, I32, I64, D, U32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c
                        ctypes.c_uint32)
 SIGNATURES = {
     "mrhs_op_create": [ctypes.POINTER(P), P, I32, I32, P, P, U32, P],
+    "mrhs_op_create_halo": [ctypes.POINTER(P), P, P, I32, I32, P, P, U32, P],
+    "mrhs_gather_rows": [P, I64, P, I64, P, I64, P],
+    "mrhs_scatter_rows": [P, I64, P, P, I64, I64, P],
     "mrhs_op_destroy": [P],
     "coarse_op_apply": [P, I32, P, P, I32, P],
     "coarse_op_apply_dag": [P, I32, P, P, I32, P],

@@ -55,23 +55,30 @@ int num_sms() {
 
 namespace {
 
-__global__ void k_neighbours(int32_t* fwd, int32_t* bwd, int64_t V, int npts, int L0, int L1,
-                             int L2, int L3, const int8_t* __restrict__ disp) {
+struct Geom4 {
+  int32_t L[4], Lin[4], h[4];
+};
+
+// Input-site index of x + delta_p (fwd) and x - delta_p (bwd) for every
+// output site x: coordinates c of x on L, then c + h +- delta on the input
+// lattice Lin, wrapped periodically (a padded dimension never wraps, since
+// |delta| <= 1 = h there).
+__global__ void k_neighbours(int32_t* fwd, int32_t* bwd, int64_t V, int npts, Geom4 g,
+                             const int8_t* __restrict__ disp) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (x >= V) return;
   int c[4];
   int64_t r = x;
-  const int L[4] = {L0, L1, L2, L3};
   for (int mu = 0; mu < 4; ++mu) {
-    c[mu] = (int)(r % L[mu]);
-    r /= L[mu];
+    c[mu] = (int)(r % g.L[mu]);
+    r /= g.L[mu];
   }
   int64_t yf = 0, yb = 0;
   for (int mu = 3; mu >= 0; --mu) {
-    const int d = disp[4 * p + mu];
-    yf = yf * L[mu] + (c[mu] + d + L[mu]) % L[mu];
-    yb = yb * L[mu] + (c[mu] - d + L[mu]) % L[mu];
+    const int d = disp[4 * p + mu], n = g.Lin[mu], ci = c[mu] + g.h[mu];
+    yf = yf * n + (ci + d + n) % n;
+    yb = yb * n + (ci - d + n) % n;
   }
   fwd[(int64_t)p * V + x] = (int32_t)yf;
   bwd[(int64_t)p * V + x] = (int32_t)yb;
@@ -107,6 +114,15 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int check_op(const mrhs_op_s* op) {
   if (!op) return fail(MRHS_ERR_INVALID_ARG, "null operator");
+  return MRHS_OK;
+}
+
+// Entry points that need the whole periodic lattice on one operator: an
+// operator with an input halo (one rank's part of a decomposed lattice)
+// supports coarse_op_apply only.
+int check_plain(const mrhs_op_s* op) {
+  if (op->Vin != op->V)
+    return fail(MRHS_ERR_UNSUPPORTED, "this entry point needs an operator without an input halo");
   return MRHS_OK;
 }
 
@@ -171,10 +187,20 @@ int32_t mrhs_device_error(void) {
   return (int32_t)(tc_read_and_clear_error() | oz_read_and_clear_error());
 }
 
-int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, const int8_t* disp,
-                   const void* A, uint32_t prec_mask, void* stream) {
+static int op_create(mrhs_op* out, const int32_t L[4], const int32_t halo[4], int32_t nb,
+                     int32_t npts, const int8_t* disp, const void* A, uint32_t prec_mask,
+                     void* stream) {
   if (!out || !L || !disp || !A) return fail(MRHS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  bool any_halo = false;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (halo[mu] != 0 && halo[mu] != 1) return fail(MRHS_ERR_INVALID_ARG, "halo must be 0 or 1");
+    any_halo = any_halo || halo[mu] != 0;
+  }
+  if (any_halo && (prec_mask & ~(MRHS_PREC_BIT(MRHS_PREC_FP64) | MRHS_PREC_BIT(MRHS_PREC_FP32) |
+                                 MRHS_PREC_BIT(MRHS_PREC_DF32) | MRHS_PREC_BIT(MRHS_PREC_OZ))))
+    return fail(MRHS_ERR_UNSUPPORTED,
+                "an operator with an input halo builds FP64, DF32, FP32 and OZ only");
   if (nb < 1 || nb > 64) return fail(MRHS_ERR_INVALID_ARG, "nb must be in 1..64");
   if (npts < 1 || npts > MRHS_MAX_PTS) return fail(MRHS_ERR_INVALID_ARG, "npts must be in 1..81");
   if (prec_mask == 0 || (prec_mask >> MRHS_NUM_PREC))
@@ -199,7 +225,17 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
     if (disp[mu] != 0) return fail(MRHS_ERR_INVALID_ARG, "disp[0] must be the self term");
   cudaStream_t s = (cudaStream_t)stream;
   mrhs_op_s* op = new mrhs_op_s();
-  for (int mu = 0; mu < 4; ++mu) op->L[mu] = L[mu];
+  op->Vin = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    op->L[mu] = L[mu];
+    op->halo[mu] = halo[mu];
+    op->Lin[mu] = L[mu] + 2 * halo[mu];
+    op->Vin *= op->Lin[mu];
+  }
+  if (op->Vin * npts > INT32_MAX) {
+    delete op;
+    return fail(MRHS_ERR_INVALID_ARG, "lattice too large");
+  }
   op->nb = nb;
   op->npts = npts;
   op->V = V;
@@ -225,8 +261,14 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   }
   {
     dim3 grid((unsigned)((V + 255) / 256), (unsigned)npts);
-    { k_neighbours<<<grid, 256, 0, s>>>(op->nbr_fwd, op->nbr_bwd, V, npts, L[0], L[1], L[2], L[3],
-                                      d_disp); ::mrhs::count_launch(); }
+    Geom4 g4;
+    for (int mu = 0; mu < 4; ++mu) {
+      g4.L[mu] = op->L[mu];
+      g4.Lin[mu] = op->Lin[mu];
+      g4.h[mu] = op->halo[mu];
+    }
+    { k_neighbours<<<grid, 256, 0, s>>>(op->nbr_fwd, op->nbr_bwd, V, npts, g4, d_disp);
+      ::mrhs::count_launch(); }
   }
   if (prec_mask & MRHS_PREC_BIT(MRHS_PREC_FP64)) {
     if (cudaMalloc(&op->a64, sizeof(double2) * nA) != cudaSuccess) {
@@ -245,8 +287,9 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
     { k_to_c64<<<num_sms() * 8, 256, 0, s>>>((const double2*)A, op->a32, (int64_t)nA); ::mrhs::count_launch(); }
   }
   // Hermitian stencil operators let the tensor-core kernel read one tile per
-  // pair of points (p, -p): detect exact Hermiticity once
-  {
+  // pair of points (p, -p): detect exact Hermiticity once (an operator with
+  // an input halo holds no partner tiles across its boundary: not checked)
+  if (!any_halo) {
     int8_t partner[MRHS_MAX_PTS];
     bool paired = true;
     for (int p = 0; p < npts && paired; ++p) {
@@ -311,8 +354,22 @@ int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, c
   return MRHS_OK;
 }
 
+int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, const int8_t* disp,
+                   const void* A, uint32_t prec_mask, void* stream) {
+  const int32_t none[4] = {0, 0, 0, 0};
+  return op_create(out, L, none, nb, npts, disp, A, prec_mask, stream);
+}
+
+int mrhs_op_create_halo(mrhs_op* out, const int32_t L[4], const int32_t halo[4], int32_t nb,
+                        int32_t npts, const int8_t* disp, const void* A, uint32_t prec_mask,
+                        void* stream) {
+  if (!halo) return fail(MRHS_ERR_INVALID_ARG, "null argument");
+  return op_create(out, L, halo, nb, npts, disp, A, prec_mask, stream);
+}
+
 int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, void* stream) {
   MRHS_TRY(check_op(op));
+  MRHS_TRY(check_plain(op));
   MRHS_TRY(check_prec(op, prec));
   if (!lam || iters < 1) return fail(MRHS_ERR_INVALID_ARG, "mrhs_op_lambda_max: arguments");
   MRHS_TRY(lambda_max(op, prec, iters, (cudaStream_t)stream, lam));
@@ -413,11 +470,15 @@ static int apply_common(mrhs_op op, int32_t prec, const void* X, void* Y, int32_
   MRHS_TRY(check_vec(X, "X"));
   MRHS_TRY(check_vec(Y, "Y"));
   if (nrhs < 1 || nrhs > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs must be in 1..64");
+  if (dag && op->Vin != op->V)
+    return fail(MRHS_ERR_UNSUPPORTED, "the adjoint of an operator with an input halo needs "
+                                      "coefficients of neighbouring sites it does not hold");
   const size_t es = MRHS_PREC_IS_WIDE(prec) ? 16 : 8;
-  const size_t bytes = es * (size_t)op->V * op->nb * nrhs;
+  const size_t xbytes = es * (size_t)op->Vin * op->nb * nrhs;
+  const size_t ybytes = es * (size_t)op->V * op->nb * nrhs;
   const char* x = (const char*)X;
   const char* y = (const char*)Y;
-  if (x < y + bytes && y < x + bytes) return fail(MRHS_ERR_INVALID_ARG, "X and Y overlap");
+  if (x < y + ybytes && y < x + xbytes) return fail(MRHS_ERR_INVALID_ARG, "X and Y overlap");
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != op->device) return fail(MRHS_ERR_INVALID_ARG, "operator lives on another device");
@@ -437,6 +498,7 @@ int coarse_op_apply_dag(mrhs_op op, int32_t prec, const void* X, void* Y, int32_
 int coarse_op_outer(mrhs_op op, const void* G, const void* X, void* GA, double alpha,
                     int32_t nrhs, int32_t dtype, void* stream) {
   MRHS_TRY(check_op(op));
+  MRHS_TRY(check_plain(op));
   MRHS_TRY(check_vec(G, "G"));
   MRHS_TRY(check_vec(X, "X"));
   MRHS_TRY(check_vec(GA, "GA"));
@@ -495,6 +557,7 @@ int herm_factor(const void* G, void* S, void* W, int32_t* rank, int32_t r, doubl
 int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, const void* X,
                 void* P, int32_t nrhs, void* stream) {
   MRHS_TRY(check_op(op));
+  MRHS_TRY(check_plain(op));
   MRHS_TRY(check_prec(op, prec));
   MRHS_TRY(check_vec(X, "X"));
   MRHS_TRY(check_vec(P, "P"));
@@ -542,6 +605,7 @@ int block_promote(const void* basis, const void* C, void* F, int64_t n_blocks, i
 int coarsen_op(mrhs_op fine, const int32_t block[4], const void* basis, int32_t nbasis,
                const int8_t* disp, int32_t npts, void* A, void* stream) {
   MRHS_TRY(check_op(fine));
+  MRHS_TRY(check_plain(fine));
   MRHS_TRY(check_prec(fine, MRHS_PREC_FP64));
   if (!block || !disp) return fail(MRHS_ERR_INVALID_ARG, "coarsen_op: null argument");
   MRHS_TRY(check_vec(basis, "basis"));
@@ -578,6 +642,7 @@ int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const doubl
                             int32_t n_ev, double lo, double hi, int32_t order, const void* B,
                             void* X, int32_t nrhs, void* stream) {
   MRHS_TRY(check_op(op));
+  MRHS_TRY(check_plain(op));
   MRHS_TRY(check_prec(op, prec));
   MRHS_TRY(check_vec(B, "B"));
   MRHS_TRY(check_vec(X, "X"));
@@ -608,6 +673,7 @@ int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const doubl
 int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
                    const mrhs_solve_params* params, mrhs_solve_info* info, void* stream) {
   MRHS_TRY(check_op(op));
+  MRHS_TRY(check_plain(op));
   if (!params) return fail(MRHS_ERR_INVALID_ARG, "params is null");
   MRHS_TRY(check_vec(B, "B"));
   MRHS_TRY(check_vec(X, "X"));
@@ -687,6 +753,7 @@ int mrhs_autotune(const mrhs_op* ops, int32_t n, int32_t prec, const int32_t* nr
   cudaGetDevice(&dev);
   for (int i = 0; i < n; ++i) {
     MRHS_TRY(check_op(ops[i]));
+    MRHS_TRY(check_plain(ops[i]));
     MRHS_TRY(check_prec(ops[i], prec));
     if (ops[i]->device != dev) return fail(MRHS_ERR_INVALID_ARG, "operator on another device");
     if (nrhs[i] < 1 || nrhs[i] > MRHS_MAX_RHS) return fail(MRHS_ERR_INVALID_ARG, "nrhs[i]");
@@ -721,6 +788,7 @@ int mrhs_batch_apply(const mrhs_op* ops, int32_t n, int32_t prec, const void* co
   cudaGetDevice(&dev);
   for (int i = 0; i < n; ++i) {
     MRHS_TRY(check_op(ops[i]));
+    MRHS_TRY(check_plain(ops[i]));
     MRHS_TRY(check_prec(ops[i], prec));
     MRHS_TRY(check_vec(X[i], "X[i]"));
     MRHS_TRY(check_vec(Y[i], "Y[i]"));
@@ -744,6 +812,7 @@ int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* 
   cudaGetDevice(&dev);
   for (int i = 0; i < n; ++i) {
     MRHS_TRY(check_op(ops[i]));
+    MRHS_TRY(check_plain(ops[i]));
     MRHS_TRY(check_vec(B[i], "B[i]"));
     MRHS_TRY(check_vec(X[i], "X[i]"));
     if (ops[i]->device != dev) return fail(MRHS_ERR_INVALID_ARG, "operator on another device");

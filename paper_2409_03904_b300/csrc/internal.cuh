@@ -110,6 +110,13 @@ struct mrhs_op_s {
   int32_t L[4];
   int32_t nb, npts;
   int64_t V;
+  // input halo (mrhs_op_create_halo): the input vectors live on the padded
+  // lattice Lin = L + 2 halo (halo[mu] in {0, 1}; no wrap in a padded
+  // dimension, periodic wrap in the others), Vin sites; the output on L.
+  // Without a halo Lin = L and Vin = V.
+  int32_t halo[4] = {0, 0, 0, 0};
+  int32_t Lin[4] = {0, 0, 0, 0};
+  int64_t Vin = 0;
   int8_t disp[MRHS_MAX_PTS][4];
   int device;
   uint32_t prec_mask;

@@ -322,7 +322,9 @@ __global__ void k_oz_pack_x(const double2* __restrict__ X, const double* __restr
 }
 
 struct OzStencil {
-  int32_t L[4];
+  int32_t L[4];            // output lattice
+  int32_t Lin[4];          // input lattice: L + 2 h (an input halo h in {0, 1} per dimension)
+  int32_t h[4];
   int32_t sign;            // +1: x + delta_p (forward); -1: x - delta_p (adjoint)
   int8_t d[MRHS_MAX_PTS][4];
 };
@@ -395,9 +397,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t aslab = g.aslab, xslab = g.xslab, xoff = g.aslab + g.zbytes;
       const int sign = od.st.sign;
       const uint32_t* dwords = reinterpret_cast<const uint32_t*>(&od.st.d[0][0]);
-      int Lm[4];
+      int Lm[4], Ln[4], hm[4];
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) Lm[mu] = od.st.L[mu];
+      for (int mu = 0; mu < 4; ++mu) {
+        Lm[mu] = od.st.L[mu];
+        Ln[mu] = od.st.Lin[mu];
+        hm[mu] = od.st.h[mu];
+      }
       int s = 0;
       uint32_t ph = 0;
       int64_t issued = 0;
@@ -418,9 +424,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int mu = 3; mu >= 0; --mu) {
             int v = c[mu] + sign * (int)(int8_t)(dw >> (8 * mu));
-            v += (v < 0) ? Lm[mu] : 0;
-            v -= (v >= Lm[mu]) ? Lm[mu] : 0;
-            y = y * Lm[mu] + v;
+            v += hm[mu];                      // input coordinates: shifted by the halo
+            v += (v < 0) ? Ln[mu] : 0;
+            v -= (v >= Ln[mu]) ? Ln[mu] : 0;
+            y = y * Ln[mu] + v;
           }
           for (int j = 0; j < nk; ++j) {
             if (!ptx::mbar_wait(&empty[s], ph ^ 1u, &s_abort)) { ok = false; break; }
@@ -513,9 +520,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t aph = 0;
     for (int64_t x = blockIdx.x; x < V; x += gridDim.x) {
       double sc = 0.0, dx = 0.0;
+      int64_t xin = x;             // x on the input lattice (differs with an input halo)
       if (writer) {
         sc = __ldg(&od.scale[x]) * sig;
         dx = __ldg(&od.diag[x]);
+        int64_t rr = x, acc_in = 0, stride = 1;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          const int c = (int)(rr % od.st.L[mu]);
+          rr /= od.st.L[mu];
+          acc_in += (int64_t)(c + od.st.h[mu]) * stride;
+          stride *= od.st.Lin[mu];
+        }
+        xin = acc_in;
       }
       const bool got = ptx::mbar_wait(acc_full, aph, &s_abort);
       if (!ptx::epilogue_all(got)) {
@@ -591,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ar = c0 + e;
             if (ar < nb) {
               const int64_t idx = ((int64_t)x * nb + ar) * R + r;
-              const double2 xv = __ldg(&Xp[idx]);
+              const double2 xv = __ldg(&Xp[((int64_t)xin * nb + ar) * R + r]);
               Yp[idx] = make_double2(fma(sc, (double)vre[e], dx * xv.x),
                                      fma(sc, (double)vim[e], dx * xv.y));
             }
@@ -682,17 +699,17 @@ int oz_apply(mrhs_op_s* op, bool dag, const void* X, void* Y, int nrhs, cudaStre
   // applications), the input digits after it
   constexpr size_t kHead = 1024;
   const size_t before = op->ws_ozpack.bytes;
-  MRHS_TRY(op->ws_ozpack.ensure(kHead + (size_t)op->V * g.nk * g.xslab));
+  MRHS_TRY(op->ws_ozpack.ensure(kHead + (size_t)op->Vin * g.nk * g.xslab));
   unsigned long long* colmax = (unsigned long long*)op->ws_ozpack.ptr;
   double* sigma = (double*)(colmax + MRHS_MAX_RHS);
   uint8_t* xb = (uint8_t*)op->ws_ozpack.ptr + kHead;
   if (op->ws_ozpack.bytes != before)
     MRHS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * MRHS_MAX_RHS, s));
   const int sms = num_sms();
-  { k_oz_colmax<<<sms * 4, 256, 0, s>>>((const double2*)X, colmax, op->V * op->nb, nrhs);
+  { k_oz_colmax<<<sms * 4, 256, 0, s>>>((const double2*)X, colmax, op->Vin * op->nb, nrhs);
     count_launch(); }
   { k_oz_colscale<<<1, 64, 0, s>>>(colmax, sigma, nrhs); count_launch(); }
-  { k_oz_pack_x<<<sms * 8, 256, 0, s>>>((const double2*)X, sigma, xb, op->V, g); count_launch(); }
+  { k_oz_pack_x<<<sms * 8, 256, 0, s>>>((const double2*)X, sigma, xb, op->Vin, g); count_launch(); }
   MRHS_CUDA_TRY(cudaGetLastError());
   OzDesc od;
   od.coef = (const uint8_t*)img.digits;
@@ -706,7 +723,11 @@ int oz_apply(mrhs_op_s* op, bool dag, const void* X, void* Y, int nrhs, cudaStre
   od.npts = op->npts;
   od.idesc = ptx::idesc_f16(kM, g.N, false);
   od.g = g;
-  for (int mu = 0; mu < 4; ++mu) od.st.L[mu] = op->L[mu];
+  for (int mu = 0; mu < 4; ++mu) {
+    od.st.L[mu] = op->L[mu];
+    od.st.Lin[mu] = op->Lin[mu];
+    od.st.h[mu] = op->halo[mu];
+  }
   od.st.sign = dag ? -1 : 1;
   for (int p = 0; p < op->npts; ++p)
     for (int mu = 0; mu < 4; ++mu) od.st.d[p][mu] = op->disp[p][mu];
