@@ -222,6 +222,25 @@ int block_inner(const void* X, const void* Y, void* G, int64_t N, int32_t rx, in
 int block_inner_noalloc(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
                         int32_t dtype, void* stream);
 
+/* Column-wise algebra for one Krylov process per right-hand side, run in
+ * lockstep over the columns of an N x r block (the flexible ADEF2 CG of
+ * Fig. 1 and its fixed-iteration CG smoother, which Sec. 2 runs as distinct
+ * processes per right-hand side).  Scalars live on the device as complex128
+ * [r] arrays.
+ *   mrhs_col_dot:    out[j] = sum_n conj(X[n][j]) Y[n][j], FP64 sums in a
+ *                    fixed order (bitwise reproducible); X, Y of dtype;
+ *                    uses a library-owned workspace per (device, stream)
+ *   mrhs_col_ratio:  out[j] = scale * num[j] / den[j]; 0 where den[j] = 0 or
+ *                    active[j] = 0 (active: device int32[r], or NULL = all)
+ *   mrhs_col_update: Y[n][j] = beta Y[n][j] + coef[j] X[n][j] (Y may be X)
+ * 1 <= r <= MRHS_MAX_RHS; N >= 0.  Asynchronous on `stream`. */
+int mrhs_col_dot(const void* X, const void* Y, void* out, int64_t N, int32_t r, int32_t dtype,
+                 void* stream);
+int mrhs_col_ratio(const void* num, const void* den, void* out, const int32_t* active, int32_t r,
+                   double scale, void* stream);
+int mrhs_col_update(void* Y, const void* X, const void* coef, double beta, int64_t N, int32_t r,
+                    int32_t dtype, void* stream);
+
 /* Y = beta*Y + X M  (Fig. 2 block updates X + D M, Q - Z M, D S^dagger, ...)
  *   X [N][rin], Y [N][rout] of element type dtype; Y may alias X when
  *   rin == rout (the update is done row tile by row tile)

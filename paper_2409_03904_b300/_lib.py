@@ -82,6 +82,9 @@ SIGNATURES = {
     "mrhs_op_create": [ctypes.POINTER(P), P, I32, I32, P, P, U32, P],
     "mrhs_op_create_halo": [ctypes.POINTER(P), P, P, I32, I32, P, P, U32, P],
     "mrhs_gather_rows": [P, I64, P, I64, P, I64, P],
+    "mrhs_col_dot": [P, P, P, I64, I32, I32, P],
+    "mrhs_col_ratio": [P, P, P, P, I32, D, P],
+    "mrhs_col_update": [P, P, P, D, I64, I32, I32, P],
     "mrhs_scatter_rows": [P, I64, P, P, I64, I64, P],
     "mrhs_op_destroy": [P],
     "coarse_op_apply": [P, I32, P, P, I32, P],

@@ -72,3 +72,26 @@ def test_site_subset_consistent():
     B = vectors(L, 4, 6, 31)
     Bs = vectors(L, 4, 3, 31, sites=sites)
     assert np.array_equal(B[sites][:, :, :3], Bs)
+
+
+def test_covariant_laplacian():
+    """Links unitary; the operator Hermitian with its spectrum in [m, 16 + m];
+    at eps = 0 it is the free Laplacian, whose eigenvalues are
+    8 + m - 2 sum_mu cos(2 pi k_mu / L_mu), each nb times."""
+    import numpy as np
+    from synth.laplace import covariant_laplacian, links
+    from tests.test_oracle_ops import dense_matrix
+    from synth import stencil
+    L, nb, m = (3, 2, 2, 3), 3, 0.25
+    U = links(L, nb, 0.4, 11)
+    assert np.allclose(np.conj(np.swapaxes(U, -1, -2)) @ U, np.eye(nb), atol=1e-13)
+    disp, _ = stencil(9)
+    H = dense_matrix(covariant_laplacian(L, nb, 0.4, m, 11), L, disp)
+    assert np.allclose(H, np.conj(H.T), atol=1e-13)
+    ev = np.linalg.eigvalsh(H)
+    assert ev[0] >= m - 1e-12 and ev[-1] <= 16 + m + 1e-12
+    H0 = dense_matrix(covariant_laplacian(L, nb, 0.0, m, 11), L, disp)
+    k = np.meshgrid(*[np.arange(l) for l in L], indexing="ij")
+    lam = 8 + m - 2 * sum(np.cos(2 * np.pi * k[mu] / L[mu]) for mu in range(4))
+    ref = np.sort(np.repeat(lam.reshape(-1), nb))
+    assert np.allclose(np.linalg.eigvalsh(H0), ref, atol=1e-12)
