@@ -484,6 +484,17 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode);
  * its output undefined.  Synchronises the current device. */
 int32_t mrhs_device_error(void);
 
+/* Debugging: the limit, in ns, of the bounded wait with which the epilogue
+ * of the tensor-core kernels (BF16 ... TC32 and OZ) waits for its
+ * accumulator; 0 restores the default of 1 s.  A short limit (a microsecond)
+ * makes that wait run out on purpose: the kernel records bit 4 (BF16 ...
+ * TC32) or 32 (OZ) in mrhs_device_error (the producer and the MMA issuer,
+ * told to stop, may add theirs), waits for its own copies and MMAs, frees
+ * its tensor memory and returns; its output is then undefined.  Lets a test
+ * exercise the failure path without faulting the GPU.  Applies to the
+ * current device; synchronous. */
+int mrhs_debug_wait_limit(uint64_t ns);
+
 /* Measurement hooks.  mrhs_op_kernel_timing(op, 1) makes every following
  * application of `op` record a CUDA event pair on its stream around the
  * operator's main kernel (the tcgen05 kernel for BF16/FP16, the FMA kernel

@@ -354,6 +354,13 @@ static int op_create(mrhs_op* out, const int32_t L[4], const int32_t halo[4], in
   return MRHS_OK;
 }
 
+int mrhs_debug_wait_limit(uint64_t ns) {
+  if (ns > 10000000000ull) return fail(MRHS_ERR_INVALID_ARG, "wait limit above 10 s");
+  MRHS_TRY(tc_set_wait_limit(ns));
+  MRHS_TRY(oz_set_wait_limit(ns));
+  return MRHS_OK;
+}
+
 int mrhs_op_create(mrhs_op* out, const int32_t L[4], int32_t nb, int32_t npts, const int8_t* disp,
                    const void* A, uint32_t prec_mask, void* stream) {
   const int32_t none[4] = {0, 0, 0, 0};

@@ -169,6 +169,7 @@ int simt_apply(mrhs_op_s* op, int prec, bool dag, const void* X, void* Y, int nr
 // op_tc.cu
 int tc_build(mrhs_op_s* op, int prec, bool dag, const double2* A, cudaStream_t s);
 unsigned tc_read_and_clear_error();
+int tc_set_wait_limit(unsigned long long ns);
 int tc_apply_batch(mrhs_op_s* const* ops, int n, int prec, const void* const* X,
                    void* const* Y, const int32_t* nrhs, const int32_t* active, cudaStream_t s,
                    const TcTune* force = nullptr, const ChebFuse* fuse = nullptr);
@@ -188,6 +189,7 @@ int oz_build(mrhs_op_s* op, bool dag, const double2* A, cudaStream_t s);
 int oz_apply(mrhs_op_s* op, bool dag, const void* X, void* Y, int nrhs, cudaStream_t s);
 int oz_supported(const mrhs_op_s* op, int nrhs);
 unsigned oz_read_and_clear_error();
+int oz_set_wait_limit(unsigned long long ns);
 // blas.cu
 int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, int dtype,
          cudaStream_t s);

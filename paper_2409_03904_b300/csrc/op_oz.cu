@@ -57,6 +57,9 @@ namespace mrhs {
 // translation unit without relocatable device code): 8 producer, 16 MMA
 // issuer, 32 epilogue wait expired
 __device__ unsigned int g_oz_error = 0;
+// limit of the epilogue's accumulator wait in ns (0: the default 1 s); set
+// only by the debugging entry point mrhs_debug_wait_limit
+__device__ unsigned long long g_oz_wait_ns = 0;
 
 namespace {
 
@@ -351,7 +354,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + nstages;
   uint64_t* acc_full = empty + nstages;
   uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint64_t* mma_done = acc_empty + 1;     // every MMA of this CTA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   uint8_t* stages = smem + 1024;
   const OzGeom g = od.g;
   const uint32_t stage_bytes = g.stage;
@@ -367,6 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::mbar_init(acc_full, 1);
     ptx::mbar_init(acc_empty, 4);
+    ptx::mbar_init(mma_done, 1);
     ptx::fence_mbar_init();
     s_abort = 0;
   }
@@ -501,6 +506,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_abort = 1;
         atomicOr(&g_oz_error, 16u);
       }
+      // every MMA issued has completed before tensor memory is freed (also
+      // after an abort left accumulators unread)
+      ptx::mma_commit(mma_done);
+      volatile int never = 0;
+      ptx::mbar_wait(mma_done, 0, &never);
     }
   } else {
     // ---------------- epilogue, warps 2..5 -> TMEM lane quarters 2,3,0,1
@@ -516,6 +526,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const double2* Xp = od.X;
     double2* Yp = od.Y;
     const double sig = writer ? ldexp(__ldg(&od.sigma[r]), -kNormShift) : 0.0;
+    const unsigned long long lim_dbg = g_oz_wait_ns;
+    const uint64_t wait_ns = lim_dbg ? lim_dbg : 1000000000ull;
     int xbuf = 0;
     uint32_t aph = 0;
     for (int64_t x = blockIdx.x; x < V; x += gridDim.x) {
@@ -534,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         xin = acc_in;
       }
-      const bool got = ptx::mbar_wait(acc_full, aph, &s_abort);
+      const bool got = ptx::mbar_wait(acc_full, aph, &s_abort, wait_ns);
       if (!ptx::epilogue_all(got)) {
         s_abort = 1;
         atomicOr(&g_oz_error, 32u);
@@ -738,6 +750,11 @@ int oz_apply(mrhs_op_s* op, bool dag, const void* X, void* Y, int nrhs, cudaStre
   { k_op_oz<<<(unsigned)grid, kThreads, ring.smem, s>>>(od, ring.nstages); count_launch(); }
   timer_mark(op, MRHS_PREC_OZ, s);
   MRHS_CUDA_TRY(cudaGetLastError());
+  return MRHS_OK;
+}
+
+int oz_set_wait_limit(unsigned long long ns) {
+  MRHS_CUDA_TRY(cudaMemcpyToSymbol(g_oz_wait_ns, &ns, sizeof(ns)));
   return MRHS_OK;
 }
 

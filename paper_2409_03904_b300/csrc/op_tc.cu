@@ -70,6 +70,9 @@
 namespace mrhs {
 
 __device__ unsigned int g_tc_error = 0;
+// limit of the epilogue's accumulator wait in ns (0: the default 1 s); set
+// only by the debugging entry point mrhs_debug_wait_limit
+__device__ unsigned long long g_tc_wait_ns = 0;
 
 namespace {
 
@@ -480,7 +483,8 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
   uint64_t* empty = full + nstages;
   uint64_t* acc_full = empty + nstages;
   uint64_t* acc_empty = acc_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* mma_done = acc_empty + 2;     // every MMA of this CTA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   uint8_t* stages = smem + 1024;
   // a stage holds up to `pps` consecutive stencil points of one site: their
   // coefficient tiles (contiguous in HBM, one bulk copy) at the start, their
@@ -500,6 +504,7 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
       ptx::mbar_init(&acc_full[i], 1);
       ptx::mbar_init(&acc_empty[i], 4);
     }
+    ptx::mbar_init(mma_done, 1);
     ptx::fence_mbar_init();
     s_abort = 0;
   }
@@ -727,6 +732,12 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
         s_abort = 1;
         atomicOr(&g_tc_error, 2u);
       }
+      // wait until every MMA this thread issued has completed, so that tensor
+      // memory is freed only after its last write, also when an abort left
+      // accumulators that nobody reads
+      ptx::mma_commit(mma_done);
+      volatile int never = 0;
+      ptx::mbar_wait(mma_done, 0, &never);
     }
   } else {
     // ---------------- epilogue, warps 2..5 -> TMEM lane quarters 2,3,0,1
@@ -734,6 +745,8 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
     const int mrow = 32 * q + lane;              // D row = TMEM lane
     int acc = 0, xbuf = 0;
     uint32_t aph = 0;
+    const unsigned long long lim_dbg = g_tc_wait_ns;
+    const uint64_t wait_ns = lim_dbg ? lim_dbg : 1000000000ull;
     // running column maximum of the Chebyshev output (writer lanes)
     float cm = 0.f;
     int cm_prob = -1, cm_r = -1;
@@ -766,7 +779,7 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
         dx = __ldg(&pd.diag[x]);
         cm_r = r;
       }
-      const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort);
+      const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort, wait_ns);
       // give up together: tcgen05.ld below is .aligned per warp and the four
       // epilogue warps meet at named barriers
       if (!ptx::epilogue_all(got)) {
@@ -1226,6 +1239,11 @@ int tc_apply_batch(mrhs_op_s* const* ops, int n, int prec, const void* const* X,
   MRHS_TRY(pack_batch(pb, prec, s, colmax_ready));
   // a single problem keeps its operator's kernel timer
   return run_batch(bt, g, prec, tune, set, prec, n == 1 ? ops[0] : nullptr, s);
+}
+
+int tc_set_wait_limit(unsigned long long ns) {
+  MRHS_CUDA_TRY(cudaMemcpyToSymbol(g_tc_wait_ns, &ns, sizeof(ns)));
+  return MRHS_OK;
 }
 
 unsigned tc_read_and_clear_error() {
