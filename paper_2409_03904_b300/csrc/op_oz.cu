@@ -4,7 +4,8 @@
 // that Mukunoki, Ozaki, Ogita and Imamura ("DGEMM using Tensor Cores, and Its
 // Accurate and Reproducible Versions", ISC 2020) run on FP16 tensor cores.
 //
-// Both operands become fixed-point numbers with few bits per digit:
+// Both operands become fixed-point numbers with few bits per digit (balanced
+// base-64 digits of rint(2^47 v / scale), see digits_of):
 //   coefficients, per site x:  A_p(x) - d_x I = s_x 2^-5 sum_s a_s 2^(-6(s-1))
 //   input, per column r:       X[:, r]         = sigma_r 2^-5 sum_t e_t 2^(-6(t-1))
 // with s, t = 1..8, s_x and sigma_r powers of two above the largest entry
@@ -139,20 +140,28 @@ __device__ inline double pow2_at_least(double m) {
   return ldexp(1.0, e);
 }
 
-// The kDigits digits of w (|w| <= 2^5): d_1 = rint(w), then the remainder
-// times 2^6, rounded, and so on.  Every step is exact in FP64; every digit is
-// an integer in [-32, 32], exact in fp16.
+// The kDigits digits of w (|w| <= 2^5): the fixed-point integer
+// n = rint(w 2^42) (one rounding, so |w - n 2^-42| <= 2^-43, i.e. 2^-48 of
+// the scale), then its balanced base-64 digits from the bottom,
+// d = ((n + 32) mod 64) - 32 in [-32, 31] and n <- (n - d) / 64 exactly; the
+// remaining top digit lies in [-32, 32].  Every digit is exact in fp16.  One
+// FP64 product and one conversion per value (the FP64 pipe is thin on this
+// part); the rest is integer arithmetic.  A NaN gives NaN digits, so a
+// non-finite operand yields a non-finite result.
 __device__ inline void digits_of(double w, uint16_t* out) {
-  double d = rint(w);
-  out[0] = __half_as_ushort(__float2half_rn((float)d));
-  double r = w - d;
+  if (w != w) {
 #pragma unroll
-  for (int s = 1; s < kDigits; ++s) {
-    r *= (double)(1 << kBeta);
-    d = rint(r);
-    out[s] = __half_as_ushort(__float2half_rn((float)d));
-    r -= d;
+    for (int s = 0; s < kDigits; ++s) out[s] = 0x7E00u;   // fp16 NaN
+    return;
   }
+  long long n = __double2ll_rn(w * 4398046511104.0);    // w 2^42, an exact scaling
+#pragma unroll
+  for (int s = kDigits - 1; s >= 1; --s) {
+    const long long d = ((n + 32) & 63) - 32;
+    out[s] = __half_as_ushort(__int2half_rn((int)d));
+    n = (n - d) >> kBeta;
+  }
+  out[0] = __half_as_ushort(__int2half_rn((int)n));
 }
 
 __device__ inline uint4 pack8(const uint16_t* h) {

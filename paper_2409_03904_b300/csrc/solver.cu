@@ -320,8 +320,15 @@ __global__ void k_small_start(Small* st, int R, double tau) {
   }
 }
 
-// M = (G_kk)^-1, MC = M C, negM = -M.
-__global__ void k_small_M(Small* st, int R, double tau) {
+// The nrhs x nrhs steps of an iteration, split so that only the
+// factorisation (inherently sequential) runs on one CTA; the products run
+// one CTA per row or column (on B300 one SM's FP64 rate made them the bulk
+// of a single-CTA kernel).  Sums run in the same order as a plain loop, so
+// the results do not depend on the split.
+//
+// M step: factor the Gram D^dagger Z (rank checked against the block's), then
+// M = W W^dagger, negM = -M (k_small_WWh) and MC = M C (k_small_mul).
+__global__ void k_small_Mf(Small* st, int R, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* sA = reinterpret_cast<double2*>(smem_raw);
   double2* sS = sA + R * R;
@@ -329,106 +336,85 @@ __global__ void k_small_M(Small* st, int R, double tau) {
   __shared__ int perm[64];
   const int k_in = st->rank;
   const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, nullptr, st->W);
-  // st->W now holds the inverse factor in caller order: M = W W^dagger.  The
-  // products below run from shared memory (W stored transposed, so that a
-  // warp's lanes read consecutive words); on B300 one SM's FP64 rate makes
-  // them the bulk of this kernel.
-  __syncthreads();
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    const int j = e / R, l = e % R;
-    sA[l * R + j] = st->W[e];                       // sA[l][j] = W[j][l]
-    sW[e] = st->C[e];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    const int i = e / R, j = e % R;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int l = 0; l < R; ++l) {
-      const double2 a = sA[l * R + i], b = sA[l * R + j];
-      acc = cfma(a, make_double2(b.x, -b.y), acc);
-    }
-    sS[e] = acc;
-    st->M[e] = acc;
-    st->negM[e] = make_double2(-acc.x, -acc.y);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    const int i = e / R, j = e % R;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int l = 0; l < R; ++l) acc = cfma(sS[i * R + l], sW[l * R + j], acc);
-    st->MC[e] = acc;
-  }
   if (threadIdx.x == 0 && k < k_in) st->flag |= 2;   // D^dagger H D lost rank
 }
 
-// After the second Gram: factor -> S, W, new rank; estimate; C <- S C; test.
-// precond: est_j^2 = (C^dagger G2 C)_jj with G2 = t^dagger t (old C);
-// otherwise est_j = |(S C) e_j| (Q orthonormal).
-__global__ void k_small_S(Small* st, int R, double tau, int precond) {
+// M = W W^dagger and negM = -M: block i (row), thread j (column)
+__global__ void k_small_WWh(Small* st, int R) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j >= R) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int l = 0; l < R; ++l) {
+    const double2 a = st->W[i * R + l], b = st->W[j * R + l];
+    acc = cfma(a, make_double2(b.x, -b.y), acc);
+  }
+  st->M[i * R + j] = acc;
+  st->negM[i * R + j] = make_double2(-acc.x, -acc.y);
+}
+
+// S step.  Preconditioned form first: est_j^2 = (C^dagger G2 C)_jj with
+// G2 = t^dagger t and the old C; block j (column), thread a.
+__global__ void k_small_est_pre(Small* st, int R) {
+  __shared__ double part[64];
+  const int j = blockIdx.x, a = threadIdx.x;
+  if (a < R) {
+    double2 v = make_double2(0.0, 0.0);
+    for (int b = 0; b < R; ++b) v = cfma(st->G2[a * R + b], st->C[b * R + j], v);
+    const double2 c = st->C[a * R + j];
+    part[a] = c.x * v.x + c.y * v.y;                 // Re(conj(C_aj) v_aj)
+  }
+  __syncthreads();
+  if (a == 0) {
+    double s = 0.0;
+    for (int i = 0; i < R; ++i) s += part[i];
+    st->est[j] = sqrt(fmax(s, 0.0));
+  }
+}
+
+// factor T^dagger t -> S, W and the new rank (one CTA)
+__global__ void k_small_Sf(Small* st, int R, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* sA = reinterpret_cast<double2*>(smem_raw);
   double2* sS = sA + R * R;
   double2* sW = sS + R * R;
   __shared__ int perm[64];
   const int k_in = st->rank;
-  if (precond) {
-    // est_j = |C[:, j]|_{G2}: V = G2 C from shared memory, then the columns
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      sA[e] = st->G2[e];
-      sW[e] = st->C[e];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      const int a = e / R, j = e % R;
-      double2 v = make_double2(0.0, 0.0);
-      for (int b = 0; b < R; ++b) v = cfma(sA[a * R + b], sW[b * R + j], v);
-      sS[e] = v;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < R; j += blockDim.x) {
-      double s = 0.0;
-      for (int a = 0; a < R; ++a) {
-        const double2 c = sW[a * R + j], v = sS[a * R + j];
-        s += c.x * v.x + c.y * v.y;                 // Re(conj(C_aj) v_aj)
-      }
-      st->est[j] = sqrt(fmax(s, 0.0));
-    }
-  }
-  __syncthreads();
   const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, st->S, st->W);
+  if (threadIdx.x == 0) st->rank = k;
+}
+
+// C <- S C in place, block j owning column j; unpreconditioned form: est_j =
+// |(S C) e_j| (Q orthonormal)
+__global__ void k_small_SC(Small* st, int R, int precond) {
+  __shared__ double2 col[64];
+  __shared__ double part[64];
+  const int j = blockIdx.x, i = threadIdx.x;
+  if (i < R) col[i] = st->C[i * R + j];
   __syncthreads();
-  // C <- S C from shared memory
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    sA[e] = st->S[e];
-    sW[e] = st->C[e];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    const int i = e / R, j = e % R;
+  if (i < R) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int l = 0; l < R; ++l) acc = cfma(sA[i * R + l], sW[l * R + j], acc);
-    sS[e] = acc;
+    for (int l = 0; l < R; ++l) acc = cfma(st->S[i * R + l], col[l], acc);
+    st->C[i * R + j] = acc;
+    part[i] = acc.x * acc.x + acc.y * acc.y;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) st->C[e] = sS[e];
-  __syncthreads();
-  if (!precond)
-    for (int j = threadIdx.x; j < R; j += blockDim.x) {
-      double s = 0.0;
-      for (int a = 0; a < R; ++a) s += sS[a * R + j].x * sS[a * R + j].x + sS[a * R + j].y * sS[a * R + j].y;
-      st->est[j] = sqrt(s);
-    }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->rank = k;
-    int conv = 1;
-    for (int j = 0; j < R; ++j) {
-      if (!isfinite(st->est[j])) st->flag |= 4;
-      if (!(st->est[j] <= st->target[j])) conv = 0;
-    }
-    if (k == 0) conv = 1;
-    if (conv) st->flag |= 1;
+  if (!precond && i == 0) {
+    double s = 0.0;
+    for (int a = 0; a < R; ++a) s += part[a];
+    st->est[j] = sqrt(s);
   }
+}
+
+// convergence, breakdown and non-finite flags of the S step
+__global__ void k_small_flags(Small* st, int R) {
+  if (threadIdx.x != 0) return;
+  int conv = 1;
+  for (int j = 0; j < R; ++j) {
+    if (!isfinite(st->est[j])) st->flag |= 4;
+    if (!(st->est[j] <= st->target[j])) conv = 0;
+  }
+  if (st->rank == 0) conv = 1;
+  if (conv) st->flag |= 1;
 }
 
 // deterministic start vector in [-1, 1] (an integer hash of the index)
@@ -586,11 +572,16 @@ struct Ctx {
       MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       { k_small_start<<<1, 256, smem, s>>>(st, R, tau); ::mrhs::count_launch(); }
     } else if (which == 1) {
-      MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      { k_small_M<<<1, 256, smem, s>>>(st, R, tau); ::mrhs::count_launch(); }
+      MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_Mf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      { k_small_Mf<<<1, 256, smem, s>>>(st, R, tau); ::mrhs::count_launch(); }
+      { k_small_WWh<<<R, 64, 0, s>>>(st, R); ::mrhs::count_launch(); }
+      { k_small_mul<<<R, 64, 0, s>>>(st->MC, st->M, st->C, R); ::mrhs::count_launch(); }
     } else {
-      MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      { k_small_S<<<1, 256, smem, s>>>(st, R, tau, precond); ::mrhs::count_launch(); }
+      if (precond) { k_small_est_pre<<<R, 64, 0, s>>>(st, R); ::mrhs::count_launch(); }
+      MRHS_CUDA_TRY(cudaFuncSetAttribute(k_small_Sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      { k_small_Sf<<<1, 256, smem, s>>>(st, R, tau); ::mrhs::count_launch(); }
+      { k_small_SC<<<R, 64, 0, s>>>(st, R, precond); ::mrhs::count_launch(); }
+      { k_small_flags<<<1, 32, 0, s>>>(st, R); ::mrhs::count_launch(); }
     }
     MRHS_CUDA_TRY(cudaGetLastError());
     return MRHS_OK;

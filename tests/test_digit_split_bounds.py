@@ -2,9 +2,11 @@
 on the CPU in exact arithmetic (Python integers and fractions), independent
 of the CUDA code:
 
-* eight signed 6-bit digits (first digit from rint(2^5 v), then remainder
-  times 2^6) represent |v| <= 1 to within 2^-48, and every digit is an
-  integer in [-32, 32] (exact in fp16);
+* eight signed 6-bit digits represent |v| <= 1 to within 2^-48, and every
+  digit is an integer in [-32, 32] (exact in fp16): the kernel's form,
+  balanced base-64 digits of the fixed-point integer rint(2^47 v), and the
+  remainder form (first digit rint(2^5 v), then the remainder times 2^6,
+  rounded) meet the same bound;
 * a level sum D_c = sum over digit pairs s + t = c of the products over
   npts * nb terms stays below 2^24 in magnitude for c <= 5 at 81 x 48 terms
   (so FP32 holds it exactly), and the weighted recombination
@@ -35,6 +37,20 @@ def digits(v, n=8):
     return out
 
 
+def digits_int(v, n=8):
+    """The kernel's digits: N = rint(v 2^(5 + 6 (n - 1))), then balanced
+    base-64 digits from the bottom, d = ((N + 32) mod 64) - 32 and
+    N <- (N - d) / 64, the remainder the top digit."""
+    N = round(Fraction(v) * 2 ** (TOP + BETA * (n - 1)))    # ties to even, like rint
+    out = []
+    for _ in range(n - 1):
+        d = (N + 32) % 64 - 32
+        out.append(d)
+        N = (N - d) // 64
+    out.append(N)
+    return out[::-1]
+
+
 def value(ds):
     return sum(Fraction(d, 2 ** (TOP + BETA * s)) for s, d in enumerate(ds))
 
@@ -46,11 +62,15 @@ def rint_frac(q):
 
 def test_representation_error_and_digit_range():
     rng = np.random.default_rng(5)
-    vals = list(rng.uniform(-1, 1, 2000)) + [1.0, -1.0, 0.0, 2.0 ** -40, -0.5, 0.5 - 2 ** -53]
+    vals = list(rng.uniform(-1, 1, 2000)) + [1.0, -1.0, 0.0, 2.0 ** -40, -0.5, 0.5 - 2 ** -53,
+                                              1 - 2 ** -53, -(1 - 2 ** -53), 2 ** -48, 2 ** -49]
     for v in vals:
-        ds = digits(v)
-        assert all(-32 <= d <= 32 for d in ds), (v, ds)
-        assert abs(value(ds) - Fraction(v)) <= Fraction(1, 2 ** 48), v
+        for ds in (digits(v), digits_int(v)):
+            assert len(ds) == 8
+            assert all(-32 <= d <= 32 for d in ds), (v, ds)
+            assert abs(value(ds) - Fraction(v)) <= Fraction(1, 2 ** 48), v
+        # the kernel's low digits stay in [-32, 31]
+        assert all(-32 <= d <= 31 for d in digits_int(v)[1:]), v
 
 
 def test_level_sums_fit_fp32_and_int64():
@@ -69,9 +89,10 @@ def test_level_sums_fit_fp32_and_int64():
         assert total < 2 ** 63
 
 
-def dot_by_levels(a, x, ndig, maxlev, round9):
-    da = [digits(v, ndig) for v in a]
-    dx = [digits(v, ndig) for v in x]
+def dot_by_levels(a, x, ndig, maxlev, round9, split=None):
+    split = split or (digits_int if ndig == 8 else digits)
+    da = [split(v, ndig) for v in a]
+    dx = [split(v, ndig) for v in x]
     D = {c: 0 for c in range(2, maxlev + 1)}
     for k in range(len(a)):
         for s in range(1, ndig + 1):
@@ -98,6 +119,9 @@ def test_truncated_level_product_error(K):
     exact = sum(Fraction(u) * Fraction(v) for u, v in zip(a, x))
     approx = dot_by_levels(a, x, 8, 9, True)
     assert abs(approx - exact) <= Fraction(4 * K, 2 ** 48) + Fraction(1, 2 ** 46)
+    # the remainder form of the digits meets the same bound
+    alt = dot_by_levels(a, x, 8, 9, True, split=digits)
+    assert abs(alt - exact) <= Fraction(4 * K, 2 ** 48) + Fraction(1, 2 ** 46)
     # the seven-digit scheme with levels <= 8 is bounded only at 2^-42
     old = dot_by_levels(a, x, 7, 8, False)
     assert abs(old - exact) <= Fraction(2 * K, 2 ** 42)
