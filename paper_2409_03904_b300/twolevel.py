@@ -96,8 +96,8 @@ def cg_columns(apply_H, B, X0=None, iters=None, tol=None, maxiter=1000, stats=No
     exhausted column, zero residual, stays put); ``tol``: each column stops
     once its recurrence residual |r_j| <= tol |b_j| (checked before each
     iteration), at most ``maxiter``
-    iterations.  Returns X; ``stats`` (a dict, optional) receives the
-    number of iterations run."""
+    iterations (a zero column stays zero).  Returns X; ``stats`` (a dict,
+    optional) receives the number of iterations run."""
     R, dev = int(B.shape[-1]), B.device
     ones, mones = _const(R, 1.0, dev), _const(R, -1.0, dev)
     if X0 is None:
@@ -252,6 +252,8 @@ def flex_adef2(apply_H, apply_Minv, coarse, B, tol=1e-8, maxiter=1000, mmax=1):
     ones = _const(R, 1.0, dev)
     mones = _const(R, -1.0, dev)
     bn = _norms(B)
+    if not np.all(bn > 0):
+        raise ValueError("flex_adef2: every right-hand side must be nonzero")
     X = coarse(B)                                                      # x_0 = Q b
     r = B.clone()
     col_update(r, apply_H(X), mones, 1.0)
@@ -324,6 +326,8 @@ def prec_block_cg(apply_H, apply_Minv, B, tol=1e-8, maxiter=1000, tau=1e-14):
         return S, W
 
     bn = _norms(B)
+    if not np.all(bn > 0):
+        raise ValueError("prec_block_cg: every right-hand side must be nonzero")
     X = torch.zeros_like(B)
     r0 = B.clone()                                                      # z_0 = B - H X_0
     Z0 = apply_Minv(r0)

@@ -184,3 +184,20 @@ def test_prec_block_cg_with_the_stationary_preconditioner(prob):
     bn = np.linalg.norm(p["B"].reshape(-1, R), axis=0)
     assert np.max(np.linalg.norm(r.reshape(-1, R), axis=0) / bn) <= 1.5e-8
     assert p["m"].device_error() == 0
+
+
+def test_zero_right_hand_side_is_rejected(prob):
+    p, tl = prob, prob["tl"]
+    B = p["B"].copy()
+    B[..., 1] = 0
+    Bd = p["dev"](B)
+    two = p["two"]
+    stat = two.stationary((2.0, p["hi_f"], 8),
+                          (p["dev"](p["U"]), p["lam"], p["lam"][-1] / 10, p["hi_c"], 40))
+    with pytest.raises(ValueError):
+        tl.prec_block_cg(two.H, stat, Bd)
+    with pytest.raises(ValueError):
+        tl.flex_adef2(two.H, stat, lambda v: v, Bd)
+    # the per-column CG leaves a zero column at zero
+    X = tl.cg_columns(two.H, Bd, tol=1e-8, maxiter=500).cpu().numpy()
+    assert np.all(X[..., 1] == 0)
