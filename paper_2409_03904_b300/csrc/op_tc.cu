@@ -55,8 +55,10 @@
 //   warp 1      allocates TMEM, issues tcgen05.mma (one elected thread) into
 //               two alternating sets of accumulators, commits stage releases
 //   warps 2-5   epilogue: tcgen05.ld of their 32-lane quarter in 8-column
-//               chunks, exchanges the Xi and lo rows' contributions through
-//               shared memory, scales, adds d_x X(x), stores complex64 Y
+//               chunks, every row group's contribution posted to shared
+//               memory; then all 128 threads split the chunk's outputs, sum
+//               the groups, scale, add d_x X(x) (and the Chebyshev step) and
+//               store complex64 Y, the chunk's global reads issued ahead
 // Every mbarrier wait is bounded (1 s); on expiry the kernel records an
 // error, drains its own copies, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -79,7 +81,7 @@ namespace {
 constexpr int kThreadsTc = 192;
 constexpr int kAccCols = 128;    // TMEM columns per accumulator (n_mma <= 128)
 constexpr int kChunk = 8;        // epilogue columns per tcgen05.ld
-constexpr int kExFloats = 3 * 2 * kChunk * 32;   // one exchange buffer (3 x 16 x 32 or 1 x 16 x 64)
+constexpr int kExFloats = 4 * 2 * kChunk * 32;   // one exchange buffer ([4][2][8][32] or [2][2][8][64])
 constexpr int kM = 128;
 constexpr size_t kSmemBudget = 220 * 1024;   // dynamic shared memory per SM
 constexpr size_t kSmemOneCta = 120 * 1024;   // at least this much keeps a CTA alone on its SM
@@ -493,6 +495,7 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
   // two exchange buffers (Xi and lo rows -> Xr rows), after the ring
   float* ex = reinterpret_cast<float*>(stages + (size_t)nstages * stage_bytes);
   __shared__ volatile int s_abort;
+  __shared__ unsigned s_cm[MRHS_MAX_RHS];   // epilogue: column maxima of the Chebyshev output
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -741,16 +744,34 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
     }
   } else {
     // ---------------- epilogue, warps 2..5 -> TMEM lane quarters 2,3,0,1
+    // Per 8-column chunk every live row posts its row group's contribution
+    // to (Re Y, Im Y) through shared memory; then the 128 threads split the
+    // chunk's 8 R outputs (item i = e R + r, consecutive in Y) and each sums
+    // the groups, applies the scales and the Chebyshev step and does the
+    // global reads and writes.  The reads of a chunk are issued before its
+    // tensor-memory loads (the first chunk's before the accumulator wait), so
+    // their latency overlaps the exchange.
     const int q = warp & 3;
     const int mrow = 32 * q + lane;              // D row = TMEM lane
+    const int et = (int)threadIdx.x - 64;        // epilogue thread 0..127
     int acc = 0, xbuf = 0;
     uint32_t aph = 0;
     const unsigned long long lim_dbg = g_tc_wait_ns;
     const uint64_t wait_ns = lim_dbg ? lim_dbg : 1000000000ull;
-    // running column maximum of the Chebyshev output (writer lanes)
-    float cm = 0.f;
-    int cm_prob = -1, cm_r = -1;
+    // column maxima of the Chebyshev output of the current problem
+    for (int i = et; i < MRHS_MAX_RHS; i += 128) s_cm[i] = 0u;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    int cm_prob = -1;
     unsigned* cm_dst = nullptr;
+    auto post_maxima = [&]() {
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (cm_dst)
+        for (int i = et; i < MRHS_MAX_RHS; i += 128)
+          if (s_cm[i]) atomicMax(&cm_dst[i], s_cm[i]);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      for (int i = et; i < MRHS_MAX_RHS; i += 128) s_cm[i] = 0u;
+    };
+    constexpr int kMaxItems = kChunk * MRHS_MAX_RHS / 128;   // outputs per thread and chunk
     for (int64_t t = blockIdx.x; t < bt.total; t += gridDim.x) {
       const int k = find_prob(bt, t);
       if (!item_live(bt, k)) continue;
@@ -761,24 +782,37 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
       float2* Yp = reinterpret_cast<float2*>(pd.Y);
       const int cheb = pd.cheb;
       if (k != cm_prob) {      // a new problem: post the previous one's column maxima
-        if (cm_dst && cm_r >= 0) atomicMax(&cm_dst[cm_r], __float_as_uint(cm));
-        cm = 0.f;
+        post_maxima();
         cm_prob = k;
         cm_dst = pd.colmax_next;
-        cm_r = -1;
       }
-      // row group of this lane: 0 Xr (writes Y), 1 Xi, 2 Xr_lo, 3 Xi_lo
-      const int grp = mrow / rb, r = mrow % rb;
-      const bool live = r < R && grp < (XSPLIT ? 4 : 2);
-      const bool writer = live && grp == 0;
+      // row group of this lane: 0 Xr, 1 Xi, 2 Xr_lo, 3 Xi_lo
+      constexpr int kGroups = XSPLIT ? 4 : 2;
+      const int grp = mrow / rb, r_row = mrow % rb;
+      const bool live = r_row < R && grp < kGroups;
       const bool imag = (grp & 1) != 0;
       const float gs = grp >= 2 ? kLoScale : 1.0f;
-      float sc = 0.f, dx = 0.f;
-      if (writer) {
-        sc = __ldg(&pd.scale[x]) * __ldg(&pd.sigma[r]);
-        dx = __ldg(&pd.diag[x]);
-        cm_r = r;
-      }
+      const float sx = __ldg(&pd.scale[x]), dx = __ldg(&pd.diag[x]);
+      const int nitem = kChunk * R;
+      const int64_t site0 = (int64_t)x * nb * R;
+      // this thread's outputs of a chunk: items et + 128 j
+      float2 xv[kMaxItems], tp[kMaxItems], pv[kMaxItems];
+      auto load_items = [&](int c0) {
+#pragma unroll
+        for (int j = 0; j < kMaxItems; ++j) {
+          const int i = et + 128 * j;
+          const int e = i / R;
+          const bool in = i < nitem && c0 + e < nb;
+          const int64_t idx = site0 + (int64_t)c0 * R + i;
+          xv[j] = in ? __ldg(&Xp[idx]) : make_float2(0.f, 0.f);
+          tp[j] = pv[j] = make_float2(0.f, 0.f);
+          if (cheb == 2 && in) {
+            tp[j] = reinterpret_cast<const float2*>(pd.Tp)[idx];   // may be Tout: no .nc load
+            pv[j] = reinterpret_cast<const float2*>(pd.P)[idx];
+          }
+        }
+      };
+      load_items(0);
       const bool got = ptx::mbar_wait(&acc_full[acc], aph, &s_abort, wait_ns);
       // give up together: tcgen05.ld below is .aligned per warp and the four
       // epilogue warps meet at named barriers
@@ -814,13 +848,12 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
           if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
         }
         // contribution of this row to (Re Y, Im Y)[a][r]: an Xr row gives
-        // (u, w), an Xi row (-w, u); lo rows scaled by 2^-11
-        // exchange layout [group - 1][value][row r] (3 x 16 x 32 floats split,
-        // 1 x 16 x 64 otherwise): consecutive lanes touch consecutive words,
-        // so the accesses are free of bank conflicts
+        // (u, w), an Xi row (-w, u); lo rows scaled by 2^-11.  Exchange
+        // layout [group][value][column e][row r]: consecutive lanes touch
+        // consecutive words, free of bank conflicts both ways
         float* xe = ex + xbuf * kExFloats;
-        if (live && !writer) {
-          float* slot = xe + (grp - 1) * 2 * kChunk * rb + r;
+        if (live) {
+          float* slot = xe + grp * 2 * kChunk * rb + r_row;
 #pragma unroll
           for (int e = 0; e < kChunk; ++e) {
             slot[e * rb] = gs * (imag ? -w[e] : u[e]);
@@ -828,61 +861,45 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (writer) {
 #pragma unroll
-          for (int gg = 1; gg < (XSPLIT ? 4 : 2); ++gg) {
-            const float* slot = xe + (gg - 1) * 2 * kChunk * rb + r;
+        for (int j = 0; j < kMaxItems; ++j) {
+          const int i = et + 128 * j;
+          const int e = i / R, r = i - e * R;
+          if (i >= nitem || c0 + e >= nb) continue;
+          // the groups summed in order 0, 1, 2, 3
+          const float* col = xe + e * rb + r;
+          float re = col[0], im = col[kChunk * rb];
 #pragma unroll
-            for (int e = 0; e < kChunk; ++e) {
-              u[e] += slot[e * rb];
-              w[e] += slot[(kChunk + e) * rb];
-            }
+          for (int gg = 1; gg < kGroups; ++gg) {
+            re += col[gg * 2 * kChunk * rb];
+            im += col[(gg * 2 + 1) * kChunk * rb];
           }
-#pragma unroll
-          // every load of the chunk first, then the stores: a store may alias a
-          // later element's load as far as the compiler knows, and would
-          // otherwise serialise the loads
-          const int64_t base = (int64_t)x * nb * R + r;
-          float2 xv[kChunk], tp[kChunk], pv[kChunk];
-#pragma unroll
-          for (int e = 0; e < kChunk; ++e) {
-            const int64_t idx = base + (int64_t)(c0 + e) * R;
-            const bool in = c0 + e < nb;
-            xv[e] = in ? __ldg(&Xp[idx]) : make_float2(0.f, 0.f);
-            tp[e] = pv[e] = make_float2(0.f, 0.f);
-            if (cheb == 2 && in) {
-              tp[e] = reinterpret_cast<const float2*>(pd.Tp)[idx];   // may be Tout: no .nc load
-              pv[e] = reinterpret_cast<const float2*>(pd.P)[idx];
-            }
+          const float sc = sx * __ldg(&pd.sigma[r]);
+          const int64_t idx = site0 + (int64_t)c0 * R + i;
+          const float2 y = make_float2(fmaf(sc, re, dx * xv[j].x), fmaf(sc, im, dx * xv[j].y));
+          if (cheb == 0) {
+            Yp[idx] = y;
+            continue;
           }
-#pragma unroll
-          for (int e = 0; e < kChunk; ++e) {
-            if (c0 + e >= nb) continue;
-            const int64_t idx = base + (int64_t)(c0 + e) * R;
-            const float2 y = make_float2(fmaf(sc, u[e], dx * xv[e].x), fmaf(sc, w[e], dx * xv[e].y));
-            if (cheb == 0) {
-              Yp[idx] = y;
-              continue;
-            }
-            const float ca = pd.ca, cb = pd.cb, cc = pd.cc;
-            float2 t = make_float2(ca * y.x + cb * xv[e].x, ca * y.y + cb * xv[e].y);
-            float2 p;
-            if (cheb == 1) {
-              p = make_float2(pd.c0 * xv[e].x + cc * t.x, pd.c0 * xv[e].y + cc * t.y);
-            } else {
-              t = make_float2(2.f * t.x - tp[e].x, 2.f * t.y - tp[e].y);
-              p = make_float2(pv[e].x + cc * t.x, pv[e].y + cc * t.y);
-            }
-            reinterpret_cast<float2*>(pd.Tout)[idx] = t;
-            reinterpret_cast<float2*>(pd.P)[idx] = p;
-            cm = fmaxf(cm, fmaxf(fabsf(t.x), fabsf(t.y)));
+          const float ca = pd.ca, cb = pd.cb, cc = pd.cc;
+          float2 tv = make_float2(ca * y.x + cb * xv[j].x, ca * y.y + cb * xv[j].y);
+          float2 p;
+          if (cheb == 1) {
+            p = make_float2(pd.c0 * xv[j].x + cc * tv.x, pd.c0 * xv[j].y + cc * tv.y);
+          } else {
+            tv = make_float2(2.f * tv.x - tp[j].x, 2.f * tv.y - tp[j].y);
+            p = make_float2(pv[j].x + cc * tv.x, pv[j].y + cc * tv.y);
           }
+          reinterpret_cast<float2*>(pd.Tout)[idx] = tv;
+          reinterpret_cast<float2*>(pd.P)[idx] = p;
+          if (cm_dst) atomicMax(&s_cm[r], __float_as_uint(fmaxf(fabsf(tv.x), fabsf(tv.y))));
         }
         xbuf ^= 1;      // the next chunk writes the other buffer
+        if (c0 + kChunk < nbp8) load_items(c0 + kChunk);
       }
       if (++acc == 2) { acc = 0; aph ^= 1u; }
     }
-    if (cm_dst && cm_r >= 0) atomicMax(&cm_dst[cm_r], __float_as_uint(cm));
+    post_maxima();
   }
   ptx::tc_fence_before();
   __syncthreads();
