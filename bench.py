@@ -1065,8 +1065,9 @@ def main():
                                        f"({a.fp64_op}) for the one that meets tol",
                           "fp64_operator": a.fp64_op,
                           "block_algebra": "inner block CG on complex64 vectors: Gram products "
-                                           "in FP32 summed per thread over at most 64 rows in "
-                                           "FP32, then in FP64 in a fixed order; Cholesky, "
+                                           "in FP32 summed per thread over at most 256 rows "
+                                           "(blocks of <= 32 columns; 64 rows for wider "
+                                           "blocks), then in FP64 in a fixed order; Cholesky, "
                                            "inverses and the outer update in FP64",
                           "launch_shapes": tuned,
                           "l2": "inputs larger than L2 (coefficients "
