@@ -31,8 +31,10 @@
 // Split forms (up to 32 right-hand sides): a value u is held as hi = fp16(u),
 // lo = fp16((u - hi) 2^11).  XSPLIT adds the input's lo rows (Xr_lo, Xi_lo)
 // as two more row groups of the same operand, so one MMA also gives Ahi Xlo;
-// ASPLIT adds a second MMA per step against the coefficients' lo tile into a
-// second accumulator (Alo Xhi on the hi rows).  The epilogue adds 2^-11 times
+// ASPLIT stacks the coefficients' lo tile under the hi tile along N (the two
+// tiles are contiguous with the same layout), so one MMA of N = 4 nb8 also
+// gives Alo X in the accumulator columns 2 nb8 .. 4 nb8 (used on the hi rows).
+// An MMA of twice the width costs the tensor core far less than two.  The epilogue adds 2^-11 times
 // the lo contributions.  FP16X = FP16 coefficients with a two-term input
 // (linear in X to ~2^-22, for a stationary preconditioner); TC32 = both
 // operands in two terms (FP32-class operator, same bytes per coefficient as
@@ -478,7 +480,8 @@ template <bool BF16, bool XSPLIT, bool ASPLIT>
 __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
     k_op_tc(const __grid_constant__ Batch bt, int nstages, uint32_t stage_bytes) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  // accumulators per buffer: D (+ the lo-coefficient D2), kAccCols each
+  // accumulators per buffer: D, and for ASPLIT the lo-coefficient D2 in the
+  // n_mma columns right after it (one MMA of N = 2 n_mma writes both)
   constexpr int kAccStride = (ASPLIT ? 2 : 1) * kAccCols;   // TMEM cols per buffer
   constexpr uint32_t kTmemCols = 2u * kAccStride;           // two buffers
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -647,6 +650,8 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
         const int nk = pd.K / 16, npts = pd.npts, pps = pd.pps;
         const uint32_t cbytes = pd.coef_bytes, xbytes = pd.xb_bytes, sbo = pd.sbo,
                        idesc = pd.idesc, coef1 = pd.coef1, xb_off = pd.xb_off;
+        const uint32_t lo_off = (uint32_t)pd.n_mma;     // D2: columns n_mma .. 2 n_mma
+        const uint32_t idesc2 = ptx::idesc_f16(kM, 2 * pd.n_mma, false);
         if (!ptx::mbar_wait(&acc_empty[acc], aph ^ 1u, &s_abort)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t tmem_d = tmem_base + (uint32_t)(acc * kAccStride);
@@ -668,11 +673,8 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
               const uint32_t accum = (j > 0 || kk > 0) ? 1u : 0u;
               const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)kk * 256u, 128u, sbo);
               const uint64_t bhi = ptx::smem_desc(sb + (uint32_t)kk * 256u, 128u, sbo);
-              ptx::mma_f16(tmem_d, adesc, bhi, idesc, accum);
-              if (ASPLIT)
-                ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc,
-                             ptx::smem_desc(sb + coef1 + (uint32_t)kk * 256u, 128u, sbo), idesc,
-                             accum);
+              // hi and lo tiles stacked: one MMA of N = 2 n_mma (ASPLIT)
+              ptx::mma_f16(tmem_d, adesc, bhi, ASPLIT ? idesc2 : idesc, accum);
             }
             if (j > 0) {
               const uint32_t cbk = sb + cbytes, abk = ab + xbytes;
@@ -685,9 +687,9 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
                 ptx::mma_f16(tmem_d + im_col, adesc, ptx::smem_desc(cbk + im_row + rows, sbo, 128u),
                              idesc_tn, 1u);
                 if (ASPLIT) {
-                  ptx::mma_f16(tmem_d + (uint32_t)kAccCols, adesc,
+                  ptx::mma_f16(tmem_d + lo_off, adesc,
                                ptx::smem_desc(cbk + coef1 + rows, sbo, 128u), idesc_t, 1u);
-                  ptx::mma_f16(tmem_d + (uint32_t)kAccCols + im_col, adesc,
+                  ptx::mma_f16(tmem_d + lo_off + im_col, adesc,
                                ptx::smem_desc(cbk + coef1 + im_row + rows, sbo, 128u), idesc_tn,
                                1u);
                 }
@@ -714,14 +716,9 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
               const uint32_t accum = (first || j > 0) ? 1u : 0u;
               const uint64_t adesc = ptx::smem_desc(ab + (uint32_t)j * 256u, 128u, sbo);
               const uint64_t bhi = ptx::smem_desc(cb + (uint32_t)j * 256u, 128u, sbo);
-              if (ASPLIT) {    // hi and lo coefficient tiles share the input operand
-                ptx::mma_f16_coll<ptx::CollA::fill>(tmem_d, adesc, bhi, idesc, accum);
-                ptx::mma_f16_coll<ptx::CollA::lastuse>(
-                    tmem_d + (uint32_t)kAccCols, adesc,
-                    ptx::smem_desc(cb + coef1 + (uint32_t)j * 256u, 128u, sbo), idesc, accum);
-              } else {
-                ptx::mma_f16(tmem_d, adesc, bhi, idesc, accum);
-              }
+              // ASPLIT: the hi and lo coefficient tiles, contiguous, form one
+              // operand of 2 n_mma rows; one MMA gives both accumulators
+              ptx::mma_f16(tmem_d, adesc, bhi, ASPLIT ? idesc2 : idesc, accum);
             }
           }
           ptx::mma_commit(&empty[s]);
@@ -832,8 +829,8 @@ __global__ void __launch_bounds__(kThreadsTc, ASPLIT ? 1 : 2)
         ptx::tmem_ld8_sync(taddr + (uint32_t)(nbp8 + c0), w);
         if (ASPLIT) {      // + 2^-11 Alo X, kept on the hi rows
           float u2[kChunk], w2[kChunk];
-          ptx::tmem_ld8_sync(taddr + (uint32_t)(kAccCols + c0), u2);
-          ptx::tmem_ld8_sync(taddr + (uint32_t)(kAccCols + nbp8 + c0), w2);
+          ptx::tmem_ld8_sync(taddr + (uint32_t)(2 * nbp8 + c0), u2);
+          ptx::tmem_ld8_sync(taddr + (uint32_t)(3 * nbp8 + c0), w2);
           if (grp < 2) {
 #pragma unroll
             for (int e = 0; e < kChunk; ++e) {
