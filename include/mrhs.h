@@ -194,7 +194,11 @@ int coarse_op_outer(mrhs_op op, const void* G, const void* X, void* GA, double a
  *   G device complex128 [rx][ry] row-major (written, not accumulated)
  *   N >= 0 rows, 1 <= rx, ry <= MRHS_MAX_RHS
  * Products are formed in the vectors' precision and summed in FP64 over a
- * fixed reduction tree, so the result is bitwise reproducible.  Uses a
+ * fixed reduction tree, so the result is bitwise reproducible.  Complex64
+ * blocks of 4..32 columns (multiples of 4; X rows contiguous, 16-byte
+ * aligned, N >= 1024) run on the tensor cores (mrhs_block_tc): each FP32
+ * value split exactly into three bf16 terms, the six products down to order
+ * 2^-16 summed in FP32 over at most 512 rows, then in FP64.  Uses a
  * library-owned device workspace. */
 int block_inner(const void* X, const void* Y, void* G, int64_t N, int32_t rx, int32_t ry,
                 int32_t dtype, void* stream);
@@ -245,7 +249,10 @@ int mrhs_col_update(void* Y, const void* X, const void* coef, double beta, int64
  *   X [N][rin], Y [N][rout] of element type dtype; Y may alias X when
  *   rin == rout (the update is done row tile by row tile)
  *   M device complex128 [rin][rout] row-major; beta real
- * For MRHS_C64 the arithmetic is FP32 with M rounded to complex64. */
+ * For MRHS_C64 the arithmetic is FP32 with M rounded to complex64: on the
+ * tensor cores (mrhs_block_tc) for 4..32 columns (multiples of 4), 16-byte
+ * aligned blocks and N >= 1024, from exact three-term bf16 splits of X and M
+ * (six products, FP32 accumulation over the 2 rin reals of a row). */
 int block_axpy(void* Y, const void* X, const void* M, double beta, int64_t N, int32_t rin,
                int32_t rout, int32_t dtype, void* stream);
 
@@ -479,10 +486,21 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode);
 /* Returns and clears the sticky error word of the tensor-core kernels: 0 if
  * none, else a bit set by a bounded wait that expired inside a kernel (1 the
  * TMA producer, 2 the MMA issuer, 4 the epilogue of the BF16 ... TC32 kernel;
- * 8, 16, 32 the same roles in the OZ kernel); such a kernel records the
+ * 8, 16, 32 the same roles in the OZ kernel; 64, 128, 256 the same and 512
+ * the operand converters of the tensor-core Gram and block update
+ * (mrhs_block_tc)); such a kernel records the
  * bit, drains its own copies, frees its tensor memory and returns, leaving
  * its output undefined.  Synchronises the current device. */
 int32_t mrhs_device_error(void);
+
+/* Which kernels run the complex64 block algebra of blocks of 4..32 columns
+ * (block_inner, block_axpy and the updates inside the block-CG solves):
+ * mode 1 (default) the tcgen05 tensor-core kernels (Fig. 2's Grams and
+ * block updates as MMAs on three-term bf16 splits, FP32-class products),
+ * mode 0 the FP32 FMA kernels.  Process-wide; returns the previous mode, or
+ * MRHS_ERR_INVALID_ARG for another value.  Not thread-safe against calls in
+ * flight on other host threads. */
+int32_t mrhs_block_tc(int32_t mode);
 
 /* Debugging: the limit, in ns, of the bounded wait with which the epilogue
  * of the tensor-core kernels (BF16 ... TC32 and OZ) waits for its

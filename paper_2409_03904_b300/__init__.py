@@ -19,7 +19,7 @@ __all__ = ["CoarseOp", "coarse_apply", "coarse_solve", "batch_apply", "batch_sol
            "autotune_save", "autotune_load", "autotune_entries", "autotune_clear", "block_inner",
            "block_project", "block_promote",
            "block_axpy", "herm_factor", "MrhsError", "PREC",
-           "SOLVE_FP64", "SOLVE_MIXED", "device_error", "version"]
+           "SOLVE_FP64", "SOLVE_MIXED", "block_tc", "device_error", "version"]
 
 
 def launch_count():
@@ -29,6 +29,15 @@ def launch_count():
 
 def version():
     return _lib.lib().mrhs_version().decode()
+
+
+def block_tc(mode):
+    """Complex64 block algebra of 4..32 columns on the tensor cores (1, the
+    default) or on the FP32 FMA pipes (0); returns the previous mode."""
+    r = int(_lib.lib().mrhs_block_tc(int(mode)))
+    if r < 0:
+        _lib.check(r)
+    return r
 
 
 def device_error():

@@ -105,6 +105,7 @@ SIGNATURES = {
     "mrhs_version": [],
     "mrhs_device_error": [],
     "mrhs_debug_wait_limit": [ctypes.c_uint64],
+    "mrhs_block_tc": [I32],
     "mrhs_op_kernel_timing": [P, I32],
     "mrhs_op_kernel_time": [P, I32, P, P],
     "mrhs_launch_count": [],

@@ -184,7 +184,15 @@ const char* mrhs_version(void) { return "mrhs 0.1 (sm_103a)"; }
 
 int32_t mrhs_device_error(void) {
   cudaDeviceSynchronize();
-  return (int32_t)(tc_read_and_clear_error() | oz_read_and_clear_error());
+  return (int32_t)(tc_read_and_clear_error() | oz_read_and_clear_error() |
+                   btc_read_and_clear_error());
+}
+
+int32_t mrhs_block_tc(int32_t mode) {
+  if (mode != 0 && mode != 1) return fail(MRHS_ERR_INVALID_ARG, "block algebra mode is 0 or 1");
+  const int32_t prev = g_block_tc_mode;
+  g_block_tc_mode = mode;
+  return prev;
 }
 
 static int op_create(mrhs_op* out, const int32_t L[4], const int32_t halo[4], int32_t nb,
@@ -358,6 +366,7 @@ int mrhs_debug_wait_limit(uint64_t ns) {
   if (ns > 10000000000ull) return fail(MRHS_ERR_INVALID_ARG, "wait limit above 10 s");
   MRHS_TRY(tc_set_wait_limit(ns));
   MRHS_TRY(oz_set_wait_limit(ns));
+  MRHS_TRY(btc_set_wait_limit(ns));
   return MRHS_OK;
 }
 

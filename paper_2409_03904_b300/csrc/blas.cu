@@ -478,6 +478,12 @@ int gram_ws_capped(const void* X, const void* Y, double2* G, int64_t N, int rx, 
     MRHS_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double2) * ne, s));
     return MRHS_OK;
   }
+  if (gram_tc_applies(X, Y, N, rx, ry, dtype, ldx)) {     // tensor cores (blas_tc.cu)
+    MRHS_TRY(gram_tc_partial(X, Y, part, N, rx, ry, max_entries / ne, &nblk, s));
+    { k_gram_final<<<(unsigned)((ne * 32 + 255) / 256), 256, 0, s>>>(part, G, nblk, ne); ::mrhs::count_launch(); }
+    MRHS_CUDA_TRY(cudaGetLastError());
+    return MRHS_OK;
+  }
   if (dtype == MRHS_C128) MRHS_TRY(launch_gram<double2>(X, Y, part, N, rx, ry, nblk, per, ldx, s));
   else if (rx <= 32 && ry <= 32) MRHS_TRY(launch_gram_w(X, Y, part, N, rx, ry, nblk, per, ldx, s));
   else MRHS_TRY(launch_gram<float2>(X, Y, part, N, rx, ry, nblk, per, ldx, s));
@@ -501,6 +507,8 @@ int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int r
          int dtype, cudaStream_t s, int64_t ldx) {
   if (ldx <= 0) ldx = rin;
   if (N == 0) return MRHS_OK;
+  if (update_tc_applies(Y, X, Y, N, rin, rout, dtype, ldx))   // tensor cores (blas_tc.cu)
+    return update_tc(Y, X, Y, M, 0, beta, N, rin, rout, s);
   int64_t grid = (N + kTile - 1) / kTile;
   const int64_t cap = (int64_t)num_sms() * 16;
   if (grid > cap) grid = cap;

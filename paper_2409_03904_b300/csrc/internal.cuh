@@ -195,6 +195,18 @@ int gram(const void* X, const void* Y, double2* G, int64_t N, int rx, int ry, in
          cudaStream_t s);
 int axpy(void* Y, const void* X, const double2* M, double beta, int64_t N, int rin, int rout,
          int dtype, cudaStream_t s, int64_t ldx = 0);   // ldx: X's row stride (0: rin)
+// blas_tc.cu: complex64 Gram and block update on the tensor cores
+extern int g_block_tc_mode;   // 0: SIMT kernels only, 1: tensor cores where they apply
+bool gram_tc_applies(const void* X, const void* Y, int64_t N, int rx, int ry, int dtype,
+                     int64_t ldx);
+int gram_tc_partial(const void* X, const void* Y, double2* part, int64_t N, int rx, int ry,
+                    int64_t max_blocks, int* nblk_out, cudaStream_t s);
+bool update_tc_applies(const void* Out, const void* X, const void* Add, int64_t N, int rin,
+                       int rout, int dtype, int64_t ldx);
+int update_tc(void* Out, const void* X, const void* Add, const double2* M, int mode, double beta,
+              int64_t N, int rin, int rout, cudaStream_t s);
+int btc_set_wait_limit(unsigned long long ns);
+unsigned btc_read_and_clear_error();
 // small.cu
 int factor(const double2* G, double2* S, double2* W, int32_t* rank, int r, double tau,
            cudaStream_t s);

@@ -588,6 +588,14 @@ struct Ctx {
   }
   template <typename C>
   int rotate(C* P1, C* P2, C* D) {
+    if (sizeof(C) == sizeof(float2) &&
+        update_tc_applies(P1, P1, D, N, R, R, MRHS_C64, R) &&
+        (P2 == nullptr || update_tc_applies(P2, P2, D, N, R, R, MRHS_C64, R))) {
+      // tensor cores (blas_tc.cu): P1 <- P1 W, P2 <- P2 W, D <- P + D S^dagger
+      MRHS_TRY(update_tc(P1, P1, nullptr, st->W, 0, 0.0, N, R, R, s));
+      if (P2) MRHS_TRY(update_tc(P2, P2, nullptr, st->W, 0, 0.0, N, R, R, s));
+      return update_tc(D, D, P2 ? P2 : P1, st->S, 1, 1.0, N, R, R, s);
+    }
     if (sizeof(C) == sizeof(float2) && R <= 32) {
       float2 *p1 = (float2*)P1, *p2 = (float2*)P2, *d = (float2*)D;
       int64_t g = (N + kRotWarps * kRotRows - 1) / (kRotWarps * kRotRows);
