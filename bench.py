@@ -91,6 +91,9 @@ def parse():
                     help="time block project / promote (Sec. 2.5.1) at the Table 6 shape")
     ap.add_argument("--blocks", default="4096,256,64",
                     help="n_blocks,v_block,n_basis for --blocking (nrhs from --nrhs, default 12)")
+    ap.add_argument("--block-algebra", action="store_true",
+                    help="time the complex64 Gram and block update (Fig. 2) at the workload's "
+                         "vector shape (V nb rows, nrhs columns), tensor-core and FMA kernels")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--batch", default=None, choices=["uneven12", "small"],
                     help="batched solve of independent problems against one-at-a-time solves: "
@@ -566,6 +569,59 @@ def run_blocking(a):
     print(json.dumps(out), flush=True)
 
 
+def run_block_algebra(a, w):
+    """The inner solve's block algebra at the workload's shape: Gram X^dagger Y
+    (two blocks, and one block against itself) and the block update
+    Y = Y + X M, on complex64 [V nb][R] blocks resident in HBM, each timed over
+    K launches with CUDA events, for the tensor-core kernels (mode 1) and the
+    FP32 FMA kernels (mode 0).  Bytes: blocks read (and written) once."""
+    import torch
+    import paper_2409_03904_b300 as mrhs
+    nb = a.nb or w["nb"]
+    R = a.nrhs or w["nrhs"]
+    L = tuple(int(v) for v in a.lattice.split(",")) if a.lattice else w["L"]
+    N = int(np.prod(L)) * nb
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(2409)
+    X = torch.randn((N, R), dtype=torch.complex64, device=dev, generator=g)
+    Y = torch.randn((N, R), dtype=torch.complex64, device=dev, generator=g)
+    M = torch.randn((R, R), dtype=torch.complex128, device=dev, generator=g)
+    stream = torch.cuda.current_stream()
+    hbm, _, kind = peaks()
+    blk = 8.0 * N * R
+    cases = (("gram", lambda: mrhs.block_inner(X, Y), 2 * blk),
+             ("gram_herm", lambda: mrhs.block_inner(X, X), blk),
+             ("update", lambda: mrhs.block_axpy(Y, X, M, 1.0), 3 * blk))
+    res = {}
+    for mode in (1, 0):
+        prev = mrhs.block_tc(mode)
+        for name, fn, byts in cases:
+            for _ in range(a.warmup):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(a.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / a.steps
+            res[f"{name}_{'tc' if mode else 'fma'}"] = {
+                "ms": ms, "gbs": byts / (ms * 1e-3) / 1e9,
+                "hbm_frac": byts / (ms * 1e-3) / 1e9 / hbm}
+        mrhs.block_tc(prev)
+    ms = res["gram_tc"]["ms"] + res["update_tc"]["ms"]
+    out = {"metric": "block algebra time (Gram + update, tensor cores)", "value": ms,
+           "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64", "data": "synthetic",
+           "config": {"workload": f"complex64 blocks of {N} x {R} (lattice {L}, nb {nb})",
+                      "l2": f"each block {blk / 1e9:.2f} GB (inputs larger than L2 at the "
+                            "workload shape)"},
+           "kernels": res, "peak_kind": f"{kind} copy bandwidth"}
+    print(json.dumps(out), flush=True)
+
+
 def run_batch(a):
     """Lockstep batched mixed solve (mrhs_batch_solve) against the same
     problems solved one after another (block_cg_solve), to tol 1e-8, plus
@@ -846,6 +902,8 @@ def main():
         return run_defl(a, w, shift)
     if a.blocking:
         return run_blocking(a)
+    if a.block_algebra:
+        return run_block_algebra(a, w)
     if a.batch:
         return run_batch(a)
     if a.cg5d:
@@ -1064,11 +1122,12 @@ def main():
                           "residuals": f"{a.residual} per cycle, the FP64 operator "
                                        f"({a.fp64_op}) for the one that meets tol",
                           "fp64_operator": a.fp64_op,
-                          "block_algebra": "inner block CG on complex64 vectors: Gram products "
-                                           "in FP32 summed per thread over at most 256 rows "
-                                           "(blocks of <= 32 columns; 64 rows for wider "
-                                           "blocks), then in FP64 in a fixed order; Cholesky, "
-                                           "inverses and the outer update in FP64",
+                          "block_algebra": "inner block CG on complex64 vectors: Grams and "
+                                           "block updates on the tensor cores (tcgen05) from "
+                                           "exact three-term bf16 splits, six products summed "
+                                           "in FP32, Grams flushed to FP64 every 512 rows and "
+                                           "summed in a fixed order; Cholesky, inverses and the "
+                                           "outer update in FP64",
                           "launch_shapes": tuned,
                           "l2": "inputs larger than L2 (coefficients "
                                 f"{op_bytes(w, R, a.precond) / 1e9:.1f} GB per application)"},

@@ -24,18 +24,18 @@
 //
 // Operand layouts: canonical K-major, no swizzle (8-row x 16-byte core
 // matrices, K groups 128 bytes apart, 8-row groups `sbo` apart), written by
-// converter warps from raw rows that one 1-D bulk copy per tile lands in
-// shared memory.
+// converter warps.
 //
 //   Gram: K = 16 rows of the vectors per MMA step.  The A operand (M = 128)
 //   is a window of two 64-row term blocks of X stored in the order
-//   [m, h, l, 0], B (N = 64 or 128) term blocks of Y in the order [m, h, l]:
-//     [m; h] x [m; h]  (N = 128)  ->  mm, mh | hm, hh
-//     [h; l] x l       (N = 64)   ->  hl | ll
-//     [l; 0] x h       (N = 64)   ->  lh | 0
-//   all into one 128 x 128 accumulator D, so P[i][j] = D[i][j] + D[i][64+j]
-//   + D[64+i][j] + D[64+i][64+j] (ll, below 2^-32, is kept as it comes).
-//   When X and Y are the same block, X's term blocks serve as B as well.
+//   [m, h, l, 0], B (N = 192 or 64) term blocks of Y in the order [m, h, l]:
+//     [m; h] x [m; h; l]  (N = 192)  ->  mm, mh, ml | hm, hh, hl
+//     [l; 0] x h          (N = 64)   ->  lh | 0
+//   into one 128 x 192 accumulator D, so P[i][j] is the sum of D[i][j],
+//   D[i][64+j], D[i][128+j] and the same three of row 64 + i (ml, below
+//   2^-24, is kept as it comes).  Two MMAs per step: the issue of an MMA, not
+//   its size, sets the pace at these widths.  When X and Y are the same
+//   block, X's term blocks serve as B as well.
 //
 //   Update: M = 128 rows of X, K = 2 rin (in steps of 16), the small matrix's
 //   terms stacked along N as [Mh; Mm; Ml] (Nn = round16(2 rout) rows each):
@@ -45,10 +45,12 @@
 //   and row n of the result is D[n][j] + D[n][Nn+j] + D[n][2Nn+j].
 //
 // Kernels are persistent, one CTA per SM, warp-specialised:
-//   warp 0       bulk copies of raw row tiles into a ring
+//   warp 0       bulk copies of raw row tiles into a ring (update)
 //   warp 1       allocates tensor memory, issues the MMAs (one thread)
-//   warps 2-5    epilogue (tensor-memory lane quarters 2, 3, 0, 1)
-//   warps 6-13   converters: raw rows -> bf16 term operands
+//   warps 2-5    epilogue (tensor-memory lane quarters 2, 3, 0, 1); the
+//                update has a second epilogue group in warps 6-9
+//   the rest     converters: rows -> bf16 term operands (the Gram's read
+//                global memory directly, the update's a bulk-copied tile)
 // Every mbarrier wait is bounded (1 s); on expiry the kernel records an error
 // bit (mrhs_device_error), drains its own copies and MMAs, frees its tensor
 // memory and returns.
@@ -117,12 +119,10 @@ __device__ __forceinline__ bool wait_epi(uint64_t* bar, uint32_t parity, volatil
 }
 
 // ============================================================ Gram
-constexpr int kGRows = 64;                       // rows per raw tile (4 MMA steps)
-constexpr int kGRaw = 3;                         // raw ring depth
-constexpr int kGTerm = 4;                        // term ring depth (MMA steps)
+constexpr int kGRaw = 2;                         // raw ring depth
+constexpr int kGTerm = 8;                        // term ring depth (16-row MMA steps)
 constexpr int kGFlush = 32;                      // MMA steps per FP64 flush (512 rows)
-constexpr uint32_t kGRawHalf = kGRows * 64 * 4;  // 16 KB: 64 rows x 32 complex64
-constexpr uint32_t kGRawBytes = 2 * kGRawHalf;   // X then Y
+constexpr uint32_t kGRawBytes = 32 * 1024;       // 64 rows of X and Y, or 128 rows of X (herm)
 constexpr uint32_t kGBlk = 64 * 16 * 2;          // one term block: 64 x 16 bf16 = 2 KB
 constexpr uint32_t kGTermX = 4 * kGBlk;          // X: m, h, l, zero
 constexpr uint32_t kGTermBytes = kGTermX + 3 * kGBlk;   // + Y: m, h, l
@@ -134,8 +134,12 @@ constexpr uint32_t kGSmem = kGOffAcc + 64 * 64 * 8;        // FP64 accumulators 
 
 // Partial Grams of contiguous row ranges: CTA b reduces rows
 // [b per, min(N, (b + 1) per)) into part[b][rx][ry] (complex128).
-// Requires rx, ry multiples of 4 in [4, 32], X and Y 16-byte aligned,
-// per a multiple of 64; herm: Y is X.
+// Requires rx, ry multiples of 4 in [4, 32], X and Y 16-byte aligned, per a
+// multiple of 128; herm: Y is X.  A raw tile is 64 rows of X and Y (128 of X
+// alone with herm), landed by one bulk copy per block.  Converter lanes are
+// real columns, so the reads of a row are conflict-free.  Without herm warps
+// 0-3 convert X and 4-7 Y, every step; with herm warps 0-3 convert the even
+// steps of X and 4-7 the odd ones.
 __global__ void __launch_bounds__(kBtcThreads, 1)
     k_gram_tc(const float2* __restrict__ X, const float2* __restrict__ Y,
               double2* __restrict__ part, int64_t N, int rx, int ry, int64_t per, int herm) {
@@ -158,10 +162,12 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
   const int64_t b0 = (int64_t)blockIdx.x * per;
   int64_t b1 = b0 + per;
   if (b1 > N) b1 = N;
-  const int ntile = b1 > b0 ? (int)((b1 - b0 + kGRows - 1) / kGRows) : 0;
-  const int nstep = 4 * ntile;
+  const int trows = herm ? 128 : 64;             // rows per raw tile
+  const int tsteps = trows / 16;
+  const int ntile = b1 > b0 ? (int)((b1 - b0 + trows - 1) / trows) : 0;
+  const int nstep = tsteps * ntile;
   const int nflush = (nstep + kGFlush - 1) / kGFlush;
-  const int xr = 2 * rx, yr = 2 * ry;      // reals per row
+  const int xr = 2 * rx, yr = 2 * ry;            // reals per row
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kGRaw; ++s) {
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
       ptx::mbar_init(&raw_empty[s], kConvWarps);
     }
     for (int s = 0; s < kGTerm; ++s) {
-      ptx::mbar_init(&term_full[s], kConvWarps);
+      ptx::mbar_init(&term_full[s], herm ? kConvWarps / 2 : kConvWarps);
       ptx::mbar_init(&term_empty[s], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
   for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) acc64[i] = 0.0;
   ptx::fence_proxy_async_smem();
   if (warp == 1) {
-    ptx::tmem_alloc(tmem_slot, 256);
+    ptx::tmem_alloc(tmem_slot, 512);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -207,13 +213,13 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
         const int s = i % kGRaw;
         const uint32_t ph = (uint32_t)(i / kGRaw) & 1u;
         if (!ptx::mbar_wait(&raw_empty[s], ph ^ 1u, &s_abort)) { ok = false; break; }
-        const int64_t n0 = b0 + (int64_t)i * kGRows;
-        const int64_t rows = (b1 - n0) < kGRows ? (b1 - n0) : kGRows;
+        const int64_t n0 = b0 + (int64_t)i * trows;
+        const int64_t rows = (b1 - n0) < trows ? (b1 - n0) : trows;
         const uint32_t xb = (uint32_t)(rows * rx * 8), yb = herm ? 0u : (uint32_t)(rows * ry * 8);
         uint8_t* dst = raw + (size_t)s * kGRawBytes;
         ptx::mbar_arrive_expect_tx(&raw_full[s], xb + yb);
         ptx::bulk_g2s(dst, X + n0 * rx, xb, &raw_full[s], pol);
-        if (yb) ptx::bulk_g2s(dst + kGRawHalf, Y + n0 * ry, yb, &raw_full[s], pol);
+        if (yb) ptx::bulk_g2s(dst + kGRawBytes / 2, Y + n0 * ry, yb, &raw_full[s], pol);
         ++issued;
       }
       if (!ok) {
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      const uint32_t id128 = ptx::idesc_f16(128, 128, true), id64 = ptx::idesc_f16(128, 64, true);
+      const uint32_t id192 = ptx::idesc_f16(128, 192, true), id64 = ptx::idesc_f16(128, 64, true);
       const uint32_t tb = ptx::smem_u32(term);
       int acc = 0, in_acc = 0;
       uint32_t aph = 0;
@@ -248,11 +254,9 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
         ptx::tc_fence_after();
         const uint32_t xa = tb + (uint32_t)ts * kGTermBytes;
         const uint32_t ya = herm ? xa : xa + kGTermX;
-        const uint32_t d = tmem_base + (uint32_t)(acc * 128);
-        ptx::mma_f16(d, ptx::smem_desc(xa, 128u, 256u), ptx::smem_desc(ya, 128u, 256u), id128,
-                     in_acc > 0 ? 1u : 0u);                                  // [m;h] x [m;h]
-        ptx::mma_f16(d, ptx::smem_desc(xa + kGBlk, 128u, 256u),
-                     ptx::smem_desc(ya + 2 * kGBlk, 128u, 256u), id64, 1u);   // [h;l] x l
+        const uint32_t d = tmem_base + (uint32_t)(acc * 256);
+        ptx::mma_f16(d, ptx::smem_desc(xa, 128u, 256u), ptx::smem_desc(ya, 128u, 256u), id192,
+                     in_acc > 0 ? 1u : 0u);                                  // [m;h] x [m;h;l]
         ptx::mma_f16(d, ptx::smem_desc(xa + 2 * kGBlk, 128u, 256u),
                      ptx::smem_desc(ya + kGBlk, 128u, 256u), id64, 1u);       // [l;0] x h
         ptx::mma_commit(&term_empty[ts]);
@@ -285,27 +289,26 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
         break;
       }
       ptx::tc_fence_after();
-      const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 128);
-      float s0[32], s1[32];
-      {
-        float a[32], b[32];
-        ptx::tmem_ld32_sync(ta, a);
-        ptx::tmem_ld32_sync(ta + 64, b);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) s0[j] = a[j] + b[j];
-        ptx::tmem_ld32_sync(ta + 32, a);
-        ptx::tmem_ld32_sync(ta + 96, b);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) s1[j] = a[j] + b[j];
-      }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+      const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 256);
       // rows 64 + i hand their sums to row i through shared memory, one
       // 32-column half at a time; row i adds them into FP64 (layout [j][i])
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
-        const float* sv = half ? s1 : s0;
+        float sv[32];
+#pragma unroll
+        for (int sub = 0; sub < 2; ++sub) {
+          float a[16], b[16], c[16];
+          ptx::tmem_ld16_sync(ta + (uint32_t)(32 * half + 16 * sub), a);
+          ptx::tmem_ld16_sync(ta + (uint32_t)(64 + 32 * half + 16 * sub), b);
+          ptx::tmem_ld16_sync(ta + (uint32_t)(128 + 32 * half + 16 * sub), c);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sv[16 * sub + j] = (a[j] + b[j]) + c[j];
+        }
+        if (half == 1) {        // the last tensor-memory read of this flush
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+        }
         if (L >= 64)
 #pragma unroll
           for (int j = 0; j < 32; ++j) ex[j * 64 + (L - 64)] = sv[j];
@@ -329,46 +332,45 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
         out[e] = make_double2(p00 + p11, p01 - p10);
       }
   } else {
-    // ---------------- converters: warps 0-3 X, 4-7 Y; lane = real column m
-    // (mod 32), one 8-row half of a 16-row step per warp
+    // ---------------- converters: lane = real column m (mod 32), one 8-row
+    // half of a 16-row step per warp
     const int cw = warp - 6;
-    const int op = cw >> 2, sub = cw & 3;
+    const int S = herm ? 2 : 1, o = herm ? (cw >> 2) : 0;    // steps of a tile: o, o + S, ...
+    const int op = herm ? 0 : (cw >> 2);
+    const int sub = cw & 3;
     const int kh = sub >> 1, m = (sub & 1) * 32 + lane;
     const int width = op ? yr : xr;
-    const bool work = !(op == 1 && herm);
     const uint32_t boff = (uint32_t)(m >> 3) * 256u + (uint32_t)kh * 128u + (uint32_t)(m & 7) * 16u;
     bool ok = true;
     for (int i = 0; i < ntile && ok; ++i) {
       const int rs = i % kGRaw;
       if (!ptx::mbar_wait(&raw_full[rs], (uint32_t)(i / kGRaw) & 1u, &s_abort)) { ok = false; break; }
-      const int64_t n0 = b0 + (int64_t)i * kGRows;
-      const int rows = (b1 - n0) < kGRows ? (int)(b1 - n0) : kGRows;
+      const int64_t n0 = b0 + (int64_t)i * trows;
+      const int rows = (b1 - n0) < trows ? (int)(b1 - n0) : trows;
       const float* src = reinterpret_cast<const float*>(raw + (size_t)rs * kGRawBytes +
-                                                        (op ? kGRawHalf : 0u));
-      for (int j = 0; j < 4; ++j) {
-        const int g = 4 * i + j, ts = g % kGTerm;
+                                                        (op ? kGRawBytes / 2 : 0u));
+      for (int j = o; j < tsteps; j += S) {
+        const int g = tsteps * i + j, ts = g % kGTerm;
         if (!ptx::mbar_wait(&term_empty[ts], ((uint32_t)(g / kGTerm) & 1u) ^ 1u, &s_abort)) {
           ok = false;
           break;
         }
-        if (work) {
-          uint32_t hh[8], mm[8], ll[8];
+        uint32_t hh[8], mm[8], ll[8];
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const int r = 16 * j + 8 * kh + kk;
-            const float v = (m < width && r < rows) ? src[r * width + m] : 0.f;
-            split3(v, hh[kk], mm[kk], ll[kk]);
-          }
-          const uint32_t base =
-              ptx::smem_u32(term + (size_t)ts * kGTermBytes + (op ? kGTermX : 0u)) + boff;
-          // blocks m, h, l
-          sts128(base, pack_bf16(mm[0], mm[1]), pack_bf16(mm[2], mm[3]), pack_bf16(mm[4], mm[5]),
-                 pack_bf16(mm[6], mm[7]));
-          sts128(base + kGBlk, pack_bf16(hh[0], hh[1]), pack_bf16(hh[2], hh[3]),
-                 pack_bf16(hh[4], hh[5]), pack_bf16(hh[6], hh[7]));
-          sts128(base + 2 * kGBlk, pack_bf16(ll[0], ll[1]), pack_bf16(ll[2], ll[3]),
-                 pack_bf16(ll[4], ll[5]), pack_bf16(ll[6], ll[7]));
+        for (int kk = 0; kk < 8; ++kk) {
+          const int r = 16 * j + 8 * kh + kk;
+          const float v = (m < width && r < rows) ? src[r * width + m] : 0.f;
+          split3(v, hh[kk], mm[kk], ll[kk]);
         }
+        const uint32_t base =
+            ptx::smem_u32(term + (size_t)ts * kGTermBytes + (op ? kGTermX : 0u)) + boff;
+        // blocks m, h, l
+        sts128(base, pack_bf16(mm[0], mm[1]), pack_bf16(mm[2], mm[3]), pack_bf16(mm[4], mm[5]),
+               pack_bf16(mm[6], mm[7]));
+        sts128(base + kGBlk, pack_bf16(hh[0], hh[1]), pack_bf16(hh[2], hh[3]),
+               pack_bf16(hh[4], hh[5]), pack_bf16(hh[6], hh[7]));
+        sts128(base + 2 * kGBlk, pack_bf16(ll[0], ll[1]), pack_bf16(ll[2], ll[3]),
+               pack_bf16(ll[4], ll[5]), pack_bf16(ll[6], ll[7]));
         conv_publish(&term_full[ts], lane);
       }
       if (!ok) break;
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
   if (warp == 1) {
     __syncwarp();
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem_base, 256);
+    ptx::tmem_dealloc(tmem_base, 512);
   }
 }
 
@@ -393,18 +395,20 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
 constexpr int kURows = 128;                      // rows per tile (M of the MMA)
 constexpr int kURaw = 2;
 constexpr int kUTerm = 2;
+constexpr int kUConv = 4;                        // converter warps (10..13)
 constexpr uint32_t kURawBytes = kURows * 32 * 8;           // 32 KB
 constexpr uint32_t kUTermBlk = kURows * 64 * 2;            // one term, K <= 64: 16 KB
 constexpr uint32_t kUTermBytes = 3 * kUTermBlk;            // 48 KB
 constexpr uint32_t kUBBytes = 3 * 64 * 64 * 2;             // [Mh; Mm; Ml], 24 KB
-constexpr int kUExStride = 68;                             // floats per exchange row
+constexpr int kUExStride = 36;                             // floats per exchange row (32 + 4)
+constexpr uint32_t kUExBytes = kURows * kUExStride * 4;    // one group's exchange: 18 KB
 constexpr uint32_t kUOffRaw = 1024;
 constexpr uint32_t kUOffTerm = kUOffRaw + kURaw * kURawBytes;
 constexpr uint32_t kUOffB = kUOffTerm + kUTerm * kUTermBytes;
 constexpr uint32_t kUOffEx = kUOffB + kUBBytes;
-constexpr uint32_t kUSmem = kUOffEx + kURows * kUExStride * 4;
-static_assert(kUSmem <= 227 * 1024, "block update: shared memory");
-static_assert(kGSmem <= 227 * 1024, "Gram: shared memory");
+constexpr uint32_t kUSmem = kUOffEx + 2 * kUExBytes;
+static_assert(kUSmem + 1024 <= 227 * 1024, "block update: shared memory");
+static_assert(kGSmem + 1024 <= 227 * 1024, "Gram: shared memory");
 
 struct UpdArgs {
   const float2* X;     // [N][rin]
@@ -416,11 +420,43 @@ struct UpdArgs {
   float beta;
 };
 
+// AND of pred over the 128 threads of epilogue group grp (named barrier 1 + grp)
+__device__ __forceinline__ bool group_all(bool pred, int grp) {
+  uint32_t r;
+  if (grp == 0)
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred)
+        : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void bar_group(int grp) {
+  if (grp == 0)
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+  else
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
 // Out = beta Add + X M, 128-row tiles handed out round robin.  Requires rin,
 // rout multiples of 4 in [4, 32] and 16-byte aligned vectors.  A tile's rows
 // of X are in shared memory before any of its rows of Out are written, and
 // its rows of Add are read by the thread that writes them, so Out may alias
-// X and Add.
+// X and Add.  Two epilogue groups (warps 2-5 and 6-9) take alternate tiles,
+// each with its own accumulator and exchange buffer, so the global reads of
+// Add for one tile overlap the other group's work.
 __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_constant__ UpdArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);
@@ -434,7 +470,6 @@ __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_const
   uint8_t* raw = smem + kUOffRaw;
   uint8_t* term = smem + kUOffTerm;
   uint8_t* bmat = smem + kUOffB;
-  float* ex = reinterpret_cast<float*>(smem + kUOffEx);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -449,10 +484,10 @@ __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_const
   if (threadIdx.x == 0) {
     for (int s = 0; s < kURaw; ++s) {
       ptx::mbar_init(&raw_full[s], 1);
-      ptx::mbar_init(&raw_empty[s], kConvWarps);
+      ptx::mbar_init(&raw_empty[s], kUConv);
     }
     for (int s = 0; s < kUTerm; ++s) {
-      ptx::mbar_init(&term_full[s], kConvWarps);
+      ptx::mbar_init(&term_full[s], kUConv);
       ptx::mbar_init(&term_empty[s], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -528,16 +563,18 @@ __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_const
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---------------- MMA issuer
+      // ---------------- MMA issuer: tile i into accumulator i & 1
       const uint32_t id3 = ptx::idesc_f16(128, 3 * Nn, true), id2 = ptx::idesc_f16(128, 2 * Nn, true),
                      id1 = ptx::idesc_f16(128, Nn, true);
       const uint32_t tb = ptx::smem_u32(term), bb = ptx::smem_u32(bmat);
       const int nk = K16 / 16;
-      int acc = 0;
-      uint32_t aph = 0;
       bool ok = true;
       for (int i = 0; i < mytiles && ok; ++i) {
-        if (!ptx::mbar_wait(&acc_empty[acc], aph ^ 1u, &s_abort)) { ok = false; break; }
+        const int acc = i & 1;
+        if (!ptx::mbar_wait(&acc_empty[acc], (((uint32_t)(i >> 1)) & 1u) ^ 1u, &s_abort)) {
+          ok = false;
+          break;
+        }
         ptx::tc_fence_after();
         const int ts = i % kUTerm;
         if (!ptx::mbar_wait(&term_full[ts], (uint32_t)(i / kUTerm) & 1u, &s_abort)) {
@@ -556,7 +593,6 @@ __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_const
         }
         ptx::mma_commit(&term_empty[ts]);
         ptx::mma_commit(&acc_full[acc]);
-        if (++acc == 2) { acc = 0; aph ^= 1u; }
       }
       if (!ok) {
         s_abort = 1;
@@ -566,76 +602,89 @@ __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_const
       volatile int never = 0;
       ptx::mbar_wait(mma_done, 0, &never);
     }
-  } else if (warp < 6) {
-    // ---------------- epilogue: lane r of the accumulator = tile row r
+  } else if (warp < 10) {
+    // ---------------- epilogue group grp (warps 2-5: tiles 0, 2, ...; warps
+    // 6-9: tiles 1, 3, ...): lane r of the accumulator = tile row r
+    const int grp = (warp - 2) >> 2;
     const int q = warp & 3;
     const int r = 32 * q + lane;
-    const int et = (int)threadIdx.x - 64;
+    const int et = 32 * ((warp - 2) & 3) + lane;        // 0..127 within the group
+    float* ex = reinterpret_cast<float*>(smem + kUOffEx + (size_t)grp * kUExBytes);
     const unsigned long long lim = g_btc_wait_ns;
     const uint64_t wait_ns = lim ? lim : 1000000000ull;
     const int v4row = kout / 4;                 // float4 per output row
+    const int hw = kout < 32 ? kout : 32;       // reals per row in one exchange pass
+    const int v4half = hw / 4;
     constexpr int kMaxV4 = kURows * 16 / 128;   // per thread and tile (rout <= 32)
-    int acc = 0;
-    uint32_t aph = 0;
-    for (int i = 0; i < mytiles; ++i) {
+    const float beta = a.beta;
+    for (int i = grp; i < mytiles; i += 2) {
+      const int acc = grp;
       const int64_t n0 = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kURows;
       const int rows = (a.N - n0) < kURows ? (int)(a.N - n0) : kURows;
       const int nv4 = rows * v4row;
+      // this thread's outputs: pass h, item u -> row e / v4half, float4 e % v4half
       float4 add[kMaxV4];
       const float4* addp = reinterpret_cast<const float4*>(a.Add + n0 * rout);
 #pragma unroll
       for (int u = 0; u < kMaxV4; ++u) {
-        const int e = et + 128 * u;
-        add[u] = (a.beta != 0.f && e < nv4) ? addp[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int h = u / (kMaxV4 / 2), e = et + 128 * (u % (kMaxV4 / 2));
+        const int rr = e / v4half, cc = e - rr * v4half + h * v4half;
+        const bool in = rr < rows && cc < v4row;
+        add[u] = (beta != 0.f && in) ? addp[rr * v4row + cc] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      const bool got = wait_epi(&acc_full[acc], aph, &s_abort, wait_ns);
-      if (!ptx::epilogue_all(got)) {
+      const bool got = wait_epi(&acc_full[acc], (uint32_t)(i >> 1) & 1u, &s_abort, wait_ns);
+      if (!group_all(got, grp)) {
         s_abort = 1;
         atomicOr(&g_btc_error, kErrEpi);
         break;
       }
       ptx::tc_fence_after();
       const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * 256);
-      for (int c0 = 0; c0 < kout; c0 += 16) {
-        float u0[16], u1[16], u2[16];
-        ptx::tmem_ld16_sync(ta + (uint32_t)c0, u0);
-        ptx::tmem_ld16_sync(ta + (uint32_t)(Nn + c0), u1);
-        ptx::tmem_ld16_sync(ta + (uint32_t)(2 * Nn + c0), u2);
-        float* row = ex + r * kUExStride + c0;
-#pragma unroll
-        for (int e = 0; e < 16; e += 4)
-          *reinterpret_cast<float4*>(row + e) =
-              make_float4(u0[e] + u1[e] + u2[e], u0[e + 1] + u1[e + 1] + u2[e + 1],
-                          u0[e + 2] + u1[e + 2] + u2[e + 2], u0[e + 3] + u1[e + 3] + u2[e + 3]);
-      }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
-      if (++acc == 2) { acc = 0; aph ^= 1u; }
-      bar_epi();
       float4* outp = reinterpret_cast<float4*>(a.Out + n0 * rout);
-      const float beta = a.beta;
 #pragma unroll
-      for (int u = 0; u < kMaxV4; ++u) {
-        const int e = et + 128 * u;
-        if (e >= nv4) continue;
-        const int rr = e / v4row, cc = (e - rr * v4row) * 4;
-        const float4 y = *reinterpret_cast<const float4*>(ex + rr * kUExStride + cc);
-        outp[e] = make_float4(fmaf(beta, add[u].x, y.x), fmaf(beta, add[u].y, y.y),
-                              fmaf(beta, add[u].z, y.z), fmaf(beta, add[u].w, y.w));
+      for (int h = 0; h < 2; ++h) {
+        if (h * 32 >= kout) break;
+        // reals 32 h .. 32 h + 31 of every row into the exchange, then out
+        for (int c0 = 32 * h; c0 < kout && c0 < 32 * h + 32; c0 += 8) {
+          float u0[8], u1[8], u2[8];
+          ptx::tmem_ld8_sync(ta + (uint32_t)c0, u0);
+          ptx::tmem_ld8_sync(ta + (uint32_t)(Nn + c0), u1);
+          ptx::tmem_ld8_sync(ta + (uint32_t)(2 * Nn + c0), u2);
+          float* row = ex + r * kUExStride + (c0 - 32 * h);
+#pragma unroll
+          for (int e = 0; e < 8; e += 4)
+            *reinterpret_cast<float4*>(row + e) =
+                make_float4(u0[e] + u1[e] + u2[e], u0[e + 1] + u1[e + 1] + u2[e + 1],
+                            u0[e + 2] + u1[e + 2] + u2[e + 2], u0[e + 3] + u1[e + 3] + u2[e + 3]);
+        }
+        if (32 * h + 32 >= kout) {      // the last tensor-memory read of this tile
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
+        }
+        bar_group(grp);
+#pragma unroll
+        for (int uu = 0; uu < kMaxV4 / 2; ++uu) {
+          const int u = h * (kMaxV4 / 2) + uu;
+          const int e = et + 128 * uu;
+          const int rr = e / v4half, cl = e - rr * v4half, cc = cl + h * v4half;
+          if (rr >= rows || cc >= v4row) continue;
+          const float4 y = *reinterpret_cast<const float4*>(ex + rr * kUExStride + 4 * cl);
+          outp[rr * v4row + cc] = make_float4(fmaf(beta, add[u].x, y.x), fmaf(beta, add[u].y, y.y),
+                                              fmaf(beta, add[u].z, y.z), fmaf(beta, add[u].w, y.w));
+        }
+        bar_group(grp);
       }
-      bar_epi();
     }
   } else {
-    // ---------------- converters: row r of a tile, 8-real (32-byte) pieces
-    // of it; the pieces of a row are visited in a lane-rotated order and each
-    // is read in two 16-byte halves, first the half (lane >> 2) & 1, so that
-    // eight consecutive rows (256-byte stride) hit distinct banks
-    const int cw = warp - 6;
-    const int r = 32 * (cw & 3) + lane;
+    // ---------------- converters (warps 10-13): row r of a tile, its
+    // 8-real (32-byte) pieces visited in the lane-rotated order
+    // (q + lane) mod 8 and each read in two 16-byte halves, first the half
+    // (lane >> 2) & 1, so that eight consecutive rows (256-byte stride) hit
+    // distinct banks
+    const int cw = warp - 10;
+    const int r = 32 * cw + lane;
     const int npc = K16 / 8;                      // pieces per row (<= 8)
-    const int half_pc = (npc + 1) / 2;
-    const int pc0 = (cw >> 2) * half_pc;          // this warp's pieces: pc0 .. pc0 + half_pc - 1
     const int h0 = (lane >> 2) & 1;
     bool ok = true;
     for (int i = 0; i < mytiles && ok; ++i) {
@@ -650,9 +699,8 @@ __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_const
       const uint8_t* src = raw + (size_t)rs * kURawBytes + (size_t)r * rin * 8;
       const uint32_t tbase = ptx::smem_u32(term + (size_t)ts * kUTermBytes) +
                              (uint32_t)(r >> 3) * sbo + (uint32_t)(r & 7) * 16u;
-      for (int qq = 0; qq < half_pc; ++qq) {
-        const int pc = pc0 + (qq + (lane & 3)) % half_pc;
-        if (pc >= npc) continue;
+      for (int qq = 0; qq < npc; ++qq) {
+        const int pc = (qq + (lane & 7)) % npc;
         float v[8];
         if (r < rows && 8 * pc < kin) {
           const float4 x0 = *reinterpret_cast<const float4*>(src + pc * 32 + h0 * 16);
@@ -717,7 +765,7 @@ int gram_tc_partial(const void* X, const void* Y, double2* part, int64_t N, int 
   if (nblk > max_blocks) nblk = max_blocks;
   if (nblk < 1) return fail(MRHS_ERR_INVALID_ARG, "partial-Gram buffer too small");
   int64_t per = (N + nblk - 1) / nblk;
-  per = (per + kGRows - 1) / kGRows * kGRows;
+  per = (per + 127) / 128 * 128;
   nblk = (N + per - 1) / per;
   const int herm = (X == Y && rx == ry) ? 1 : 0;
   MRHS_CUDA_TRY(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
