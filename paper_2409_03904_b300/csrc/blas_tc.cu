@@ -12,8 +12,10 @@
 // nine term products the six down to order 2^-16 (hh, hm, mh, mm, hl, lh) are
 // accumulated, each product exact in FP32, into FP32 tensor memory; the
 // dropped ones are below 2^-23 of |x||y|, the size of an FP32 rounding.  The
-// Gram adds its FP32 accumulators into FP64 every 512 rows and sums those in
-// a fixed order, so it is bitwise reproducible.
+// Gram adds its FP32 accumulators every 512 rows into double-float sums
+// (an FP32 pair updated by the error-free TwoSum, ~2^-48 relative; B300's
+// FP64 adds would cost sixty times as much) and sums the CTAs' partials in
+// FP64 in a fixed order, so it is bitwise reproducible.
 //
 // Real forms.  A complex64 row of r columns is 2r interleaved reals
 // (k = 2c + part).  The Gram's real product P = Xre^T Yre gives
@@ -130,7 +132,7 @@ constexpr uint32_t kGOffRaw = 1024;
 constexpr uint32_t kGOffTerm = kGOffRaw + kGRaw * kGRawBytes;
 constexpr uint32_t kGOffEx = kGOffTerm + kGTerm * kGTermBytes;
 constexpr uint32_t kGOffAcc = kGOffEx + 64 * 32 * 4;       // exchange: 32 columns x 64 rows
-constexpr uint32_t kGSmem = kGOffAcc + 64 * 64 * 8;        // FP64 accumulators [j][i]
+constexpr uint32_t kGSmem = kGOffAcc + 64 * 64 * 8;        // double-float sums [j][i]: hi, lo
 
 // Partial Grams of contiguous row ranges: CTA b reduces rows
 // [b per, min(N, (b + 1) per)) into part[b][rx][ry] (complex128).
@@ -155,7 +157,8 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
   uint8_t* raw = smem + kGOffRaw;
   uint8_t* term = smem + kGOffTerm;
   float* ex = reinterpret_cast<float*>(smem + kGOffEx);
-  double* acc64 = reinterpret_cast<double*>(smem + kGOffAcc);
+  float* acc_hi = reinterpret_cast<float*>(smem + kGOffAcc);      // [j][i]
+  float* acc_lo = acc_hi + 64 * 64;
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -186,13 +189,13 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
     ptx::fence_mbar_init();
     s_abort = 0;
   }
-  // the zero block of every X term stage, and the FP64 accumulators
+  // the zero block of every X term stage, and the double-float accumulators
   for (int i = threadIdx.x; i < kGTerm * (int)(kGBlk / 16); i += blockDim.x) {
     const int s = i / (kGBlk / 16), o = i % (kGBlk / 16);
     uint4* z = reinterpret_cast<uint4*>(term + s * kGTermBytes + 3 * kGBlk) + o;
     *z = make_uint4(0u, 0u, 0u, 0u);
   }
-  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) acc64[i] = 0.0;
+  for (int i = threadIdx.x; i < 2 * 64 * 64; i += blockDim.x) acc_hi[i] = 0.f;
   ptx::fence_proxy_async_smem();
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, 512);
@@ -291,7 +294,9 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
       ptx::tc_fence_after();
       const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 256);
       // rows 64 + i hand their sums to row i through shared memory, one
-      // 32-column half at a time; row i adds them into FP64 (layout [j][i])
+      // 32-column half at a time; row i adds them into its double-float
+      // accumulators (hi + lo, the error of each FP32 add kept exactly by
+      // TwoSum: ~2^-48 relative, at FP32 speed; layout [j][i])
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         float sv[32];
@@ -315,8 +320,14 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
         bar_epi();
         if (L < 64)
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            acc64[(32 * half + j) * 64 + L] += (double)(sv[j] + ex[j * 64 + L]);
+          for (int j = 0; j < 32; ++j) {
+            const int idx = (32 * half + j) * 64 + L;
+            const float v = sv[j] + ex[j * 64 + L];
+            const float a = acc_hi[idx];
+            const float sum = a + v, bv = sum - a;
+            acc_hi[idx] = sum;
+            acc_lo[idx] += (a - (sum - bv)) + (v - bv);
+          }
         bar_epi();
       }
     }
@@ -327,8 +338,11 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
     if (!s_abort)
       for (int e = et; e < ne; e += 128) {
         const int c = e / ry, dd = e - c * ry;
-        const double p00 = acc64[(2 * dd) * 64 + 2 * c], p11 = acc64[(2 * dd + 1) * 64 + 2 * c + 1];
-        const double p01 = acc64[(2 * dd + 1) * 64 + 2 * c], p10 = acc64[(2 * dd) * 64 + 2 * c + 1];
+        auto P = [&](int ii, int jj) {
+          return (double)acc_hi[jj * 64 + ii] + (double)acc_lo[jj * 64 + ii];
+        };
+        const double p00 = P(2 * c, 2 * dd), p11 = P(2 * c + 1, 2 * dd + 1);
+        const double p01 = P(2 * c, 2 * dd + 1), p10 = P(2 * c + 1, 2 * dd);
         out[e] = make_double2(p00 + p11, p01 - p10);
       }
   } else {
@@ -349,29 +363,47 @@ __global__ void __launch_bounds__(kBtcThreads, 1)
       const int rows = (b1 - n0) < trows ? (int)(b1 - n0) : trows;
       const float* src = reinterpret_cast<const float*>(raw + (size_t)rs * kGRawBytes +
                                                         (op ? kGRawBytes / 2 : 0u));
-      for (int j = o; j < tsteps; j += S) {
-        const int g = tsteps * i + j, ts = g % kGTerm;
-        if (!ptx::mbar_wait(&term_empty[ts], ((uint32_t)(g / kGTerm) & 1u) ^ 1u, &s_abort)) {
+      // this warp's four steps of the tile, two at a time: both steps'
+      // loads and splits are independent, and one proxy fence serves both
+#pragma unroll
+      for (int pr = 0; pr < 2; ++pr) {
+        const int ja = o + 2 * pr * S, jb = ja + S;
+        const int ga = tsteps * i + ja, gb = tsteps * i + jb;
+        const int tsa = ga % kGTerm, tsb = gb % kGTerm;
+        if (!ptx::mbar_wait(&term_empty[tsa], ((uint32_t)(ga / kGTerm) & 1u) ^ 1u, &s_abort) ||
+            !ptx::mbar_wait(&term_empty[tsb], ((uint32_t)(gb / kGTerm) & 1u) ^ 1u, &s_abort)) {
           ok = false;
           break;
         }
-        uint32_t hh[8], mm[8], ll[8];
+        float va[8], vb[8];
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
-          const int r = 16 * j + 8 * kh + kk;
-          const float v = (m < width && r < rows) ? src[r * width + m] : 0.f;
-          split3(v, hh[kk], mm[kk], ll[kk]);
+          const int ra = 16 * ja + 8 * kh + kk, rb = 16 * jb + 8 * kh + kk;
+          va[kk] = (m < width && ra < rows) ? src[ra * width + m] : 0.f;
+          vb[kk] = (m < width && rb < rows) ? src[rb * width + m] : 0.f;
         }
-        const uint32_t base =
-            ptx::smem_u32(term + (size_t)ts * kGTermBytes + (op ? kGTermX : 0u)) + boff;
-        // blocks m, h, l
-        sts128(base, pack_bf16(mm[0], mm[1]), pack_bf16(mm[2], mm[3]), pack_bf16(mm[4], mm[5]),
-               pack_bf16(mm[6], mm[7]));
-        sts128(base + kGBlk, pack_bf16(hh[0], hh[1]), pack_bf16(hh[2], hh[3]),
-               pack_bf16(hh[4], hh[5]), pack_bf16(hh[6], hh[7]));
-        sts128(base + 2 * kGBlk, pack_bf16(ll[0], ll[1]), pack_bf16(ll[2], ll[3]),
-               pack_bf16(ll[4], ll[5]), pack_bf16(ll[6], ll[7]));
-        conv_publish(&term_full[ts], lane);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const float* v = h2 ? vb : va;
+          uint32_t hh[8], mm[8], ll[8];
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) split3(v[kk], hh[kk], mm[kk], ll[kk]);
+          const uint32_t base = ptx::smem_u32(term + (size_t)(h2 ? tsb : tsa) * kGTermBytes +
+                                              (op ? kGTermX : 0u)) + boff;
+          // blocks m, h, l
+          sts128(base, pack_bf16(mm[0], mm[1]), pack_bf16(mm[2], mm[3]),
+                 pack_bf16(mm[4], mm[5]), pack_bf16(mm[6], mm[7]));
+          sts128(base + kGBlk, pack_bf16(hh[0], hh[1]), pack_bf16(hh[2], hh[3]),
+                 pack_bf16(hh[4], hh[5]), pack_bf16(hh[6], hh[7]));
+          sts128(base + 2 * kGBlk, pack_bf16(ll[0], ll[1]), pack_bf16(ll[2], ll[3]),
+                 pack_bf16(ll[4], ll[5]), pack_bf16(ll[6], ll[7]));
+        }
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          ptx::mbar_arrive(&term_full[tsa]);
+          ptx::mbar_arrive(&term_full[tsb]);
+        }
       }
       if (!ok) break;
       __syncwarp();
