@@ -383,7 +383,8 @@ typedef struct {
                            (the blocks of one cycle are H-conjugate) with
                            F - H E_0 refreshed between cycles, `recycle`
                            sweeps over them (0, the default: plain restarts;
-                           2 is the tested setting).  A column keeps its E_0
+                           1 and 2 are tested, 1 is the benchmark's setting).
+                           A column keeps its E_0
                            only if that lowers the energy functional
                            e^dagger H e - 2 Re e^dagger f below zero; blocks of
                            iterations that lost rank are not kept; a cycle
