@@ -65,8 +65,12 @@ def parse():
                     help="sweeps of the Galerkin start over the earlier cycles' search blocks "
                          "(0: plain restart; 1, the default: 60 instead of 66 inner "
                          "iterations at 12^4, a net gain with the tensor-core block algebra)")
-    ap.add_argument("--check-every", type=int, default=2,
-                    help="block-CG iterations between convergence checks (one graph chunk)")
+    ap.add_argument("--rhs-offset", type=int, default=0,
+                    help="solve: draw the right-hand sides from the workload's seed plus this offset")
+    ap.add_argument("--check-every", type=int, default=4,
+                    help="block-CG iterations between convergence checks (one graph chunk); "
+                         "4: 56 inner iterations on each of four right-hand-side sets at 12^4 "
+                         "with one recycling sweep")
     ap.add_argument("--fp64-native-iters", type=int, default=3,
                     help="iterations of plain FP64 block CG on the FP64 pipes timed for the "
                          "per-iteration comparison (0: skip)")
@@ -952,7 +956,7 @@ def main():
     op = mrhs.CoarseOp(A, w["L"], disp, precs)
     del A
     torch.cuda.empty_cache()
-    B = sdev.vectors(w["L"], nb, R, w["seed"] + 7919 * rank, device=dev)
+    B = sdev.vectors(w["L"], nb, R, w["seed"] + 7919 * rank + a.rhs_offset, device=dev)
     setup_s = time.time() - t0
     lam = op.lambda_max(a.precond, 40)
     hi = 1.08 * lam
