@@ -1128,6 +1128,7 @@ def main():
                           "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
                                      f"[{hi / a.cheb_ratio:.4g}, {hi:.4g}]",
                           "inner_tol": a.inner_tol, "recycle": a.recycle,
+                          "check_every": a.check_every,
                           "parallelism": f"replicas x{world}",
                           "residuals": f"{a.residual} per cycle, the FP64 operator "
                                        f"({a.fp64_op}) for the one that meets tol",
