@@ -13,7 +13,7 @@ __device__ inline int factor_block(const double2* __restrict__ G, int ldg, int r
                             double2* sA, double2* sS, double2* sW, int* perm, double2* S_out,
                             double2* W_out) {
   const int tid = threadIdx.x, T = blockDim.x;
-  __shared__ double s_dmax, s_piv_d;
+  __shared__ double s_dmax, s_piv_d, s_sjj, s_isjj;
   __shared__ int s_fail, s_piv, s_rank;
   for (int pass = 0; pass < 2; ++pass) {
     const bool pivoting = pass == 1;
@@ -49,6 +49,11 @@ __device__ inline int factor_block(const double2* __restrict__ G, int ldg, int r
         if (!(d > tau * s_dmax) || !isfinite(d)) {
           s_fail = 1;
           s_rank = j;
+        } else {
+          // the pivot's square root and reciprocal, once per column: both
+          // take many instructions on B300's FP64 pipe
+          s_sjj = sqrt(d);
+          s_isjj = 1.0 / s_sjj;
         }
       }
       __syncthreads();
@@ -68,10 +73,10 @@ __device__ inline int factor_block(const double2* __restrict__ G, int ldg, int r
         if (tid == 0) { int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
         __syncthreads();
       }
-      const double sjj = sqrt(s_piv_d);
+      const double sjj = s_sjj, isjj = s_isjj;
       for (int i = j + tid; i < k_in; i += T) {
         const double2 a = sA[j * r + i];
-        sS[j * r + i] = (i == j) ? make_double2(sjj, 0.0) : make_double2(a.x / sjj, a.y / sjj);
+        sS[j * r + i] = (i == j) ? make_double2(sjj, 0.0) : make_double2(a.x * isjj, a.y * isjj);
       }
       __syncthreads();
       const int m = k_in - j - 1;
@@ -91,17 +96,49 @@ __device__ inline int factor_block(const double2* __restrict__ G, int ldg, int r
     __syncthreads();
   }
   const int k = s_rank;
-  // W = (leading k x k of S)^-1, column c by back substitution
-  for (int c = tid; c < r; c += T) {
-    for (int i = 0; i < r; ++i) sW[i * r + c] = make_double2(0.0, 0.0);
-    if (c < k) {
-      const double2 d = sS[c * r + c];
-      sW[c * r + c] = make_double2(1.0 / d.x, 0.0);
-      for (int i = c - 1; i >= 0; --i) {
+  // W = (leading k x k of S)^-1, column c by back substitution, with the
+  // reciprocals of S's real diagonal formed once (in sA's first row, free now)
+  double* inv_d = reinterpret_cast<double*>(sA);
+  for (int i = tid; i < k; i += T) inv_d[i] = 1.0 / sS[i * r + i].x;
+  __syncthreads();
+  for (int e = tid; e < r * r; e += T) sW[e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  if (T >= 8 * r && (T & 31) == 0) {
+    // eight lanes per column c (c = tid / 8): row i of the column is
+    // -(sum_{l = i+1..c} S[i][l] W[l][c]) / S[i][i]; the lanes split the sum
+    // over l and combine it by shuffles in a fixed order, row by row from
+    // the diagonal up (every lane of a warp runs the same r - 1 row steps)
+    const int c = tid >> 3, part = tid & 7;
+    const bool live = c < k;          // c < k <= r: lanes past the last column add zeros
+    if (live && part == 0) sW[c * r + c] = make_double2(inv_d[c], 0.0);
+    __syncwarp();
+    if ((tid >> 5) * 32 < 8 * r) {     // whole warps: the shuffles take every lane
+      for (int i = r - 2; i >= 0; --i) {
         double2 acc = make_double2(0.0, 0.0);
-        for (int l = i + 1; l <= c; ++l) acc = cfma(sS[i * r + l], sW[l * r + c], acc);
-        const double inv = 1.0 / sS[i * r + i].x;
-        sW[i * r + c] = make_double2(-acc.x * inv, -acc.y * inv);
+        if (live && i < c)
+          for (int l = i + 1 + part; l <= c; l += 8) acc = cfma(sS[i * r + l], sW[l * r + c], acc);
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (live && i < c && part == 0) {
+          const double inv = inv_d[i];
+          sW[i * r + c] = make_double2(-acc.x * inv, -acc.y * inv);
+        }
+        __syncwarp();
+      }
+    }
+  } else {
+    for (int c = tid; c < r; c += T) {
+      if (c < k) {
+        sW[c * r + c] = make_double2(inv_d[c], 0.0);
+        for (int i = c - 1; i >= 0; --i) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int l = i + 1; l <= c; ++l) acc = cfma(sS[i * r + l], sW[l * r + c], acc);
+          const double inv = inv_d[i];
+          sW[i * r + c] = make_double2(-acc.x * inv, -acc.y * inv);
+        }
       }
     }
   }
