@@ -731,29 +731,39 @@ __global__ void __launch_bounds__(kBtcThreads, 1) k_update_tc(const __grid_const
       const uint8_t* src = raw + (size_t)rs * kURawBytes + (size_t)r * rin * 8;
       const uint32_t tbase = ptx::smem_u32(term + (size_t)ts * kUTermBytes) +
                              (uint32_t)(r >> 3) * sbo + (uint32_t)(r & 7) * 16u;
-      for (int qq = 0; qq < npc; ++qq) {
-        const int pc = (qq + (lane & 7)) % npc;
-        float v[8];
-        if (r < rows && 8 * pc < kin) {
-          const float4 x0 = *reinterpret_cast<const float4*>(src + pc * 32 + h0 * 16);
-          const float4 x1 = *reinterpret_cast<const float4*>(src + pc * 32 + (h0 ^ 1) * 16);
-          const float4 lo = h0 ? x1 : x0, hi = h0 ? x0 : x1;
-          v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-          v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
-        } else {
+      // two pieces per pass (npc is even): both pieces' loads are issued
+      // before either is split, so their latencies overlap
+      for (int qq = 0; qq < npc; qq += 2) {
+        float v[2][8];
+        int pcs[2];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        for (int u = 0; u < 2; ++u) {
+          const int pc = (qq + u + (lane & 7)) % npc;
+          pcs[u] = pc;
+          if (r < rows && 8 * pc < kin) {
+            const float4 x0 = *reinterpret_cast<const float4*>(src + pc * 32 + h0 * 16);
+            const float4 x1 = *reinterpret_cast<const float4*>(src + pc * 32 + (h0 ^ 1) * 16);
+            const float4 lo = h0 ? x1 : x0, hi = h0 ? x0 : x1;
+            v[u][0] = lo.x; v[u][1] = lo.y; v[u][2] = lo.z; v[u][3] = lo.w;
+            v[u][4] = hi.x; v[u][5] = hi.y; v[u][6] = hi.z; v[u][7] = hi.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[u][e] = 0.f;
+          }
         }
-        uint32_t hh[8], mm[8], ll[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) split3(v[e], hh[e], mm[e], ll[e]);
-        const uint32_t o = tbase + (uint32_t)pc * 128u;
-        sts128(o, pack_bf16(hh[0], hh[1]), pack_bf16(hh[2], hh[3]), pack_bf16(hh[4], hh[5]),
-               pack_bf16(hh[6], hh[7]));
-        sts128(o + kUTermBlk, pack_bf16(mm[0], mm[1]), pack_bf16(mm[2], mm[3]),
-               pack_bf16(mm[4], mm[5]), pack_bf16(mm[6], mm[7]));
-        sts128(o + 2 * kUTermBlk, pack_bf16(ll[0], ll[1]), pack_bf16(ll[2], ll[3]),
-               pack_bf16(ll[4], ll[5]), pack_bf16(ll[6], ll[7]));
+        for (int u = 0; u < 2; ++u) {
+          uint32_t hh[8], mm[8], ll[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) split3(v[u][e], hh[e], mm[e], ll[e]);
+          const uint32_t o = tbase + (uint32_t)pcs[u] * 128u;
+          sts128(o, pack_bf16(hh[0], hh[1]), pack_bf16(hh[2], hh[3]), pack_bf16(hh[4], hh[5]),
+                 pack_bf16(hh[6], hh[7]));
+          sts128(o + kUTermBlk, pack_bf16(mm[0], mm[1]), pack_bf16(mm[2], mm[3]),
+                 pack_bf16(mm[4], mm[5]), pack_bf16(mm[6], mm[7]));
+          sts128(o + 2 * kUTermBlk, pack_bf16(ll[0], ll[1]), pack_bf16(ll[2], ll[3]),
+                 pack_bf16(ll[4], ll[5]), pack_bf16(ll[6], ll[7]));
+        }
       }
       conv_publish(&term_full[ts], lane);
       __syncwarp();
