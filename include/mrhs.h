@@ -286,6 +286,10 @@ int cheby_apply(mrhs_op op, int32_t prec, double lo, double hi, int32_t order, c
  * [n_blocks][v_block][nrhs]; C: device [n_blocks][n_basis][nrhs] (the coarse
  * vector layout [V][nb][nrhs] with V = n_blocks, nb = n_basis).  dtype
  * MRHS_C128 (FP64 arithmetic) or MRHS_C64 (FP32) for all three arrays.
+ * Complex64 with v_block a multiple of 64, n_basis a multiple of 8 up to 64,
+ * nrhs a multiple of 4 up to 32 and 16-byte aligned arrays runs on the
+ * tensor cores (mrhs_block_tc): exact three-term bf16 splits, six products
+ * summed in FP32.
  * 1 <= v_block, 1 <= n_basis <= 256, 1 <= nrhs <= 64 (project also needs
  * nrhs <= 16 * (256 / n_basis)); n_blocks = 0 does nothing.  The output
  * must not overlap the inputs.  Asynchronous on `stream`. */
@@ -489,13 +493,15 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode);
  * TMA producer, 2 the MMA issuer, 4 the epilogue of the BF16 ... TC32 kernel;
  * 8, 16, 32 the same roles in the OZ kernel; 64, 128, 256 the same and 512
  * the operand converters of the tensor-core Gram and block update
- * (mrhs_block_tc)); such a kernel records the
+ * (mrhs_block_tc); 1024 the tensor-core block project / promote); such a
+ * kernel records the
  * bit, drains its own copies, frees its tensor memory and returns, leaving
  * its output undefined.  Synchronises the current device. */
 int32_t mrhs_device_error(void);
 
 /* Which kernels run the complex64 block algebra of blocks of 4..32 columns
- * (block_inner, block_axpy and the updates inside the block-CG solves):
+ * (block_inner, block_axpy and the updates inside the block-CG solves) and
+ * the complex64 block project / promote of the shapes stated there:
  * mode 1 (default) the tcgen05 tensor-core kernels (Fig. 2's Grams and
  * block updates as MMAs on three-term bf16 splits, FP32-class products),
  * mode 0 the FP32 FMA kernels.  Process-wide; returns the previous mode, or

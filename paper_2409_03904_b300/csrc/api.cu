@@ -185,7 +185,7 @@ const char* mrhs_version(void) { return "mrhs 0.1 (sm_103a)"; }
 int32_t mrhs_device_error(void) {
   cudaDeviceSynchronize();
   return (int32_t)(tc_read_and_clear_error() | oz_read_and_clear_error() |
-                   btc_read_and_clear_error());
+                   btc_read_and_clear_error() | bltc_read_and_clear_error());
 }
 
 int32_t mrhs_block_tc(int32_t mode) {

@@ -56,6 +56,7 @@
 // Every mbarrier wait is bounded (1 s); on expiry the kernel records an error
 // bit (mrhs_device_error), drains its own copies and MMAs, frees its tensor
 // memory and returns.
+#include "bf16x3.cuh"
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -71,23 +72,6 @@ constexpr int kConvWarps = 8;
 constexpr int kBtcThreads = (6 + kConvWarps) * 32;   // 448
 constexpr uint32_t kErrProducer = 64u, kErrMma = 128u, kErrEpi = 256u, kErrConv = 512u;
 
-__device__ __forceinline__ void split3(float v, uint32_t& h, uint32_t& m, uint32_t& l) {
-  const uint32_t vb = __float_as_uint(v);
-  h = vb & 0xFFFF0000u;
-  const float r = v - __uint_as_float(h);
-  m = __float_as_uint(r) & 0xFFFF0000u;
-  l = __float_as_uint(r - __uint_as_float(m));
-}
-// the bf16 (upper halves) of a and b packed, a in the low half
-__device__ __forceinline__ uint32_t pack_bf16(uint32_t a, uint32_t b) {
-  return __byte_perm(a, b, 0x7632);
-}
-__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                       uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
-               "r"(d)
-               : "memory");
-}
 // converters' shared-memory stores visible to the MMA (async proxy), then one
 // arrival per warp
 __device__ __forceinline__ void conv_publish(uint64_t* bar, int lane) {

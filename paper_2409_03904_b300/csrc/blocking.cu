@@ -192,6 +192,8 @@ int project_t(const void* basis, const void* F, void* Cc, int64_t nblk, int vb, 
 
 int blocking(bool project, const void* basis, const void* in, void* out, int64_t nblk, int vb,
              int nbasis, int R, int dtype, cudaStream_t s) {
+  if (blocking_tc_applies(basis, in, out, nblk, vb, nbasis, R, dtype))   // blocking_tc.cu
+    return blocking_tc(project, basis, in, out, nblk, vb, nbasis, R, s);
   if (project)
     return dtype == MRHS_C128 ? project_t<double2>(basis, in, out, nblk, vb, nbasis, R, s)
                               : project_t<float2>(basis, in, out, nblk, vb, nbasis, R, s);

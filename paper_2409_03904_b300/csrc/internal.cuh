@@ -207,6 +207,12 @@ int update_tc(void* Out, const void* X, const void* Add, const double2* M, int m
               int64_t N, int rin, int rout, cudaStream_t s);
 int btc_set_wait_limit(unsigned long long ns);
 unsigned btc_read_and_clear_error();
+// blocking_tc.cu: complex64 block project / promote on the tensor cores
+bool blocking_tc_applies(const void* basis, const void* in, const void* out, int64_t nblk,
+                         int vb, int nbasis, int R, int dtype);
+int blocking_tc(bool project, const void* basis, const void* in, void* out, int64_t nblk, int vb,
+                int nbasis, int R, cudaStream_t s);
+unsigned bltc_read_and_clear_error();
 // small.cu
 int factor(const double2* G, double2* S, double2* W, int32_t* rank, int r, double tau,
            cudaStream_t s);
