@@ -1136,9 +1136,11 @@ def main():
                           "block_algebra": "inner block CG on complex64 vectors: Grams and "
                                            "block updates on the tensor cores (tcgen05) from "
                                            "exact three-term bf16 splits, six products summed "
-                                           "in FP32, Grams flushed to FP64 every 512 rows and "
-                                           "summed in a fixed order; Cholesky, inverses and the "
-                                           "outer update in FP64",
+                                           "in FP32; a Gram's FP32 sums (at most 512 rows) "
+                                           "added into double-float pairs (about 2^-48) per "
+                                           "CTA, the CTAs' partials summed in FP64 in a fixed "
+                                           "order; Cholesky, inverses and the outer update in "
+                                           "FP64",
                           "launch_shapes": tuned,
                           "l2": "inputs larger than L2 (coefficients "
                                 f"{op_bytes(w, R, a.precond) / 1e9:.1f} GB per application)"},
