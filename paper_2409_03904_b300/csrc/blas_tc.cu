@@ -47,12 +47,13 @@
 //   and row n of the result is D[n][j] + D[n][Nn+j] + D[n][2Nn+j].
 //
 // Kernels are persistent, one CTA per SM, warp-specialised:
-//   warp 0       bulk copies of raw row tiles into a ring (update)
+//   warp 0       bulk copies of raw row tiles into a ring
 //   warp 1       allocates tensor memory, issues the MMAs (one thread)
 //   warps 2-5    epilogue (tensor-memory lane quarters 2, 3, 0, 1); the
-//                update has a second epilogue group in warps 6-9
-//   the rest     converters: rows -> bf16 term operands (the Gram's read
-//                global memory directly, the update's a bulk-copied tile)
+//                update has a second epilogue group in warps 6-9, the two
+//                taking alternate tiles
+//   the rest     converters: raw rows in shared memory -> bf16 term operands
+//                (eight warps for the Gram, four for the update)
 // Every mbarrier wait is bounded (1 s); on expiry the kernel records an error
 // bit (mrhs_device_error), drains its own copies and MMAs, frees its tensor
 // memory and returns.
@@ -125,7 +126,8 @@ constexpr uint32_t kGSmem = kGOffAcc + 64 * 64 * 8;        // double-float sums 
 // alone with herm), landed by one bulk copy per block.  Converter lanes are
 // real columns, so the reads of a row are conflict-free.  Without herm warps
 // 0-3 convert X and 4-7 Y, every step; with herm warps 0-3 convert the even
-// steps of X and 4-7 the odd ones.
+// steps of X and 4-7 the odd ones; either way a warp converts two of its
+// steps per pass and publishes them after one proxy fence.
 __global__ void __launch_bounds__(kBtcThreads, 1)
     k_gram_tc(const float2* __restrict__ X, const float2* __restrict__ Y,
               double2* __restrict__ part, int64_t N, int rx, int ry, int64_t per, int herm) {
