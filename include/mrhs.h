@@ -361,7 +361,10 @@ typedef struct {
                            improved by 30% over 32 iterations (a low-precision
                            preconditioner is not exactly linear) */
   int32_t max_cycles;   /* MIXED: refinement cycles */
-  int32_t check_every;  /* read the convergence flag every k iterations */
+  int32_t check_every;  /* read the convergence flag every k iterations (MIXED:
+                           at most every 2 in a refinement cycle that needs
+                           less than a tenfold reduction, which is expected
+                           to end the solve) */
   double breakdown_tau; /* relative Cholesky pivot threshold */
   int32_t krylov_prec;  /* MIXED: operator precision inside the inner Krylov loop,
                            MRHS_PREC_FP32 or MRHS_PREC_TC32; -1 (default): TC32

@@ -1225,9 +1225,14 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       }
       const std::vector<double> rnorm_before = rnorm;
       int it = 0;
+      // the cycle expected to end the solve needs few iterations and leaves
+      // no blocks for a later start, so it reads its flags at least every
+      // second iteration (the earlier cycles' extra iterations between
+      // checks deepen their reduction, which the recycled start builds on)
+      const int every_cycle = final_cycle && every > 2 ? 2 : every;
       MRHS_TRY(run_bcg<float2>(cx, sb.b32, p.krylov_prec, sb.f32, sb.e32, target.data(),
                                p.precond != 0, p.precond_prec, lo, hi, p.cheb_order,
-                               p.maxiter - total_iters, every, &it, &flag,
+                               p.maxiter - total_iters, every_cycle, &it, &flag,
                                recycle && keep.avail > keep.used ? &keep : nullptr, projected,
                                !projected));
       if (recycle) MRHS_TRY(recycle_close_cycle(keep, s));
