@@ -59,11 +59,16 @@ __global__ void k_sub(C* out, const C* a, const C* b, int64_t n) {   // out = a 
 // r32[n][j] = complex64(r[n][j] / rho[j]) (0 where rho[j] == 0)
 __global__ void k_scale_to_c64(float2* out, const double2* r, const double* rho, int64_t N,
                                int R) {
+  // the columns' reciprocals once per CTA (an FP64 division is many
+  // instructions on B300's FP64 pipe); 0 for a column with rho <= 0
+  __shared__ double s_inv[MRHS_MAX_RHS];
+  for (int j = threadIdx.x; j < R; j += blockDim.x) s_inv[j] = rho[j] > 0.0 ? 1.0 / rho[j] : 0.0;
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N * R;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double p = rho[i % R];
+    const double ip = s_inv[i % R];
     const double2 v = r[i];
-    out[i] = p > 0.0 ? make_float2((float)(v.x / p), (float)(v.y / p)) : make_float2(0.f, 0.f);
+    out[i] = make_float2((float)(v.x * ip), (float)(v.y * ip));
   }
 }
 
@@ -132,6 +137,24 @@ __global__ void k_colnorm_partial(const C* X, double* part, int64_t N, int R,
   const int64_t n0 = (int64_t)blockIdx.x * rows_per_block;
   int64_t n1 = n0 + rows_per_block;
   if (n1 > N) n1 = N;
+  if (kThreads % R == 0) {
+    // thread t owns column t % R and every (kThreads / R)-th row, so a warp
+    // reads whole rows; the row groups are combined in a fixed order
+    const int j = (int)threadIdx.x % R, g = (int)threadIdx.x / R, G = kThreads / R;
+    double acc = 0.0;
+    for (int64_t n = n0 + g; n < n1; n += G) {
+      const C v = X[n * R + j];
+      acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < R) {
+      double t = 0.0;
+      for (int gg = 0; gg < G; ++gg) t += s[gg * R + threadIdx.x];
+      part[(int64_t)blockIdx.x * R + threadIdx.x] = t;
+    }
+    return;
+  }
   for (int j = 0; j < R; ++j) {
     double acc = 0.0;
     for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
