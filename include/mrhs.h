@@ -456,7 +456,12 @@ typedef struct {
  *   the initial guess X_0; out, the solution.  A zero column of B gives a
  *   zero column of X.  H must be Hermitian positive definite.
  * Returns after termination (synchronises `stream`); on MRHS_ERR_NOT_CONVERGED
- * X and *info hold the last iterate.  Workspace is allocated by the call. */
+ * X and *info hold the last iterate.  A NaN or Inf in B, or in a column of
+ * X_0 whose column of B is not zero, returns MRHS_ERR_NONFINITE before any
+ * iteration: *info is not written and X holds X_0 with the columns of zero B
+ * cleared.  (A column norm that overflows, from entries above about 1e154,
+ * counts as non-finite.)  A NaN or Inf met during the iteration also returns
+ * MRHS_ERR_NONFINITE.  Workspace is allocated by the call. */
 int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
                    const mrhs_solve_params* params, mrhs_solve_info* info, void* stream);
 
@@ -482,8 +487,11 @@ int mrhs_batch_apply(const mrhs_op* ops, int32_t n, int32_t prec, const void* co
  * problems are solved one after another with block_cg_solve.
  *   B, X   host arrays of n device pointers (complex128 [V_i][nb_i][nrhs_i])
  *   info   host array of n records (may be NULL)
- * Returns MRHS_OK if every problem converged, else the first failure code
- * (all X and info are still written).  Synchronises `stream`. */
+ * Returns MRHS_OK if every problem converged.  MRHS_ERR_NOT_CONVERGED means
+ * some problem did not; all X and info are still written.  Non-finite input
+ * in any problem's B or X_0 is refused before any iteration, as in
+ * block_cg_solve.  Any other failure code may leave the X and info of
+ * problems other than the failing one unwritten.  Synchronises `stream`. */
 int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* const* X,
                      const int32_t* nrhs, const mrhs_solve_params* params, mrhs_solve_info* info,
                      void* stream);

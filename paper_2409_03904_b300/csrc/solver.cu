@@ -546,6 +546,18 @@ int grid_for(int64_t n) {
   return (int)g;
 }
 
+// A NaN or Inf in a right-hand side or an initial guess shows as a
+// non-finite column norm (so does an entry above about 1e154, whose square
+// overflows the FP64 sum); the solves refuse such input before iterating
+// instead of treating the column as a zero one.
+int finite_columns(const std::vector<double>& norm, const std::string& what) {
+  for (size_t j = 0; j < norm.size(); ++j)
+    if (!std::isfinite(norm[j]))
+      return fail(MRHS_ERR_NONFINITE,
+                  what + " column " + std::to_string(j) + " is not finite");
+  return MRHS_OK;
+}
+
 // ---------------------------------------------------------- host driver
 struct Ctx {
   mrhs_op_s* op;
@@ -1132,11 +1144,12 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
   if (p.precond && !(lo < hi)) return fail(MRHS_ERR_INVALID_ARG, "cheb_lo must be < cheb_hi");
 
   MRHS_TRY(cx.colnorms<double2>(B, sb.bnorm_d));
-  { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, sb.bnorm_d, cx.N, R); ::mrhs::count_launch(); }
   std::vector<double> bnorm(R), rnorm(R), target(R);
   MRHS_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), sb.bnorm_d, sizeof(double) * R,
                                 cudaMemcpyDeviceToHost, s));
   MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  MRHS_TRY(finite_columns(bnorm, "B"));
+  { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, sb.bnorm_d, cx.N, R); ::mrhs::count_launch(); }
   int total_iters = 0, cycles = 0, status = MRHS_OK, flag = 0;
 
   // r64 = B - H X with the operator of precision `rp` (FP64 or DF32), rnorm
@@ -1173,6 +1186,7 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
     MRHS_CUDA_TRY(cudaMemcpyAsync(xn.data(), sb.rnorm_d, sizeof(double) * R,
                                   cudaMemcpyDeviceToHost, s));
     MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    MRHS_TRY(finite_columns(xn, "X0"));
     bool zero = true;
     for (double v : xn) zero = zero && v == 0.0;
     x0_zero = zero;
@@ -1394,12 +1408,16 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
     }
     b.lo = p.cheb_lo > 0.0 ? p.cheb_lo : b.hi / 400.0;
     MRHS_TRY(cx.colnorms<double2>(B[i], b.sb.bnorm_d));
-    const int g = grid_for(nn);
-    { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X[i], b.sb.bnorm_d, cx.N, cx.R); ::mrhs::count_launch(); }
     MRHS_CUDA_TRY(cudaMemcpyAsync(b.bnorm.data(), b.sb.bnorm_d, sizeof(double) * cx.R,
                                   cudaMemcpyDeviceToHost, s));
   }
   MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i)
+    MRHS_TRY(finite_columns(P[i].bnorm, "problem " + std::to_string(i) + ": B"));
+  for (int i = 0; i < n; ++i) {
+    BatchProb& b = P[i];
+    { k_zero_cols<double2><<<grid_for(b.cx.N * b.cx.R), kThreads, 0, s>>>(X[i], b.sb.bnorm_d, b.cx.N, b.cx.R); ::mrhs::count_launch(); }
+  }
 
   // one side stream per problem: the per-problem block algebra of an
   // iteration forks onto them (event fork / join), so inside a captured graph
@@ -1473,6 +1491,7 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
     MRHS_CUDA_TRY(cudaMemcpyAsync(xn.data(), b.sb.rnorm_d, sizeof(double) * b.cx.R,
                                   cudaMemcpyDeviceToHost, s));
     MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    MRHS_TRY(finite_columns(xn, "problem " + std::to_string(i) + ": X0"));
     bool zero = true;
     for (double v : xn) zero = zero && v == 0.0;
     if (zero) {
@@ -1958,8 +1977,17 @@ int cg5d(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_pa
   const int g = grid_for(n);
   std::vector<double> bnorm(R), rnorm(R);
   MRHS_TRY(cx.colnorms<double2>(B, bnorm_d));
-  { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, bnorm_d, cx.N, R); ::mrhs::count_launch(); }
   MRHS_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), bnorm_d, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+  MRHS_TRY(finite_columns(bnorm, "B"));
+  { k_zero_cols<double2><<<g, kThreads, 0, s>>>(X, bnorm_d, cx.N, R); ::mrhs::count_launch(); }
+  {
+    std::vector<double> xn(R);
+    MRHS_TRY(cx.colnorms<double2>(X, rnorm_d));
+    MRHS_CUDA_TRY(cudaMemcpyAsync(xn.data(), rnorm_d, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA_TRY(cudaStreamSynchronize(s));
+    MRHS_TRY(finite_columns(xn, "X0"));
+  }
   // r = B - H X (X = 0: r = B)
   MRHS_TRY(cx.apply(prec, X, r));
   { k_sub<double2><<<g, kThreads, 0, s>>>(r, B, r, n); ::mrhs::count_launch(); }

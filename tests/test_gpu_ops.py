@@ -292,6 +292,54 @@ def test_solve_edge_cases(mrhs):
     assert i2["iters"] == 0 and max(i2["resid"]) <= 1e-9
 
 
+def test_solve_refuses_nonfinite_input(mrhs):
+    """A NaN or Inf in B, or in a column of X_0 whose B column is not zero,
+    is refused before any iteration with MRHS_ERR_NONFINITE (-5) in every
+    solve mode and in a batch, instead of being taken for a zero column; the
+    operators stay usable."""
+    L, nb, npts = (2, 2, 2, 2), 4, 9
+    disp, _ = stencil(npts)
+    ops = [mrhs.CoarseOp(dev(coarse_op(L, nb, npts, seed, 6.0)), L, disp, ("fp64", "fp16x", "tc32"))
+           for seed in (91, 92)]
+    op = ops[0]
+    B = vectors(L, nb, 4, 93)
+    modes = (("fp64", {}), ("mixed", {}), ("cg5d", {}))
+    for bad in (np.nan, np.inf):
+        Bb = B.copy()
+        Bb[3, 1, 2] = bad
+        for mode, kw in modes:
+            with pytest.raises(mrhs.MrhsError) as e:
+                op.solve(dev(Bb), mode=mode, tol=1e-9, maxiter=500, **kw)
+            assert e.value.code == -5 and "B column 2" in str(e.value), (mode, str(e.value))
+    X0 = np.zeros_like(B)
+    X0[0, 0, 1] = np.nan
+    for mode, kw in modes:
+        with pytest.raises(mrhs.MrhsError) as e:
+            op.solve(dev(B), X0=dev(X0), mode=mode, tol=1e-9, maxiter=500, **kw)
+        assert e.value.code == -5 and "X0 column 1" in str(e.value), (mode, str(e.value))
+    # a NaN guess in a column whose B is zero is cleared: that column's answer is 0
+    Bz = B.copy()
+    Bz[:, :, 1] = 0.0
+    for mode, kw in modes:
+        X, info = op.solve(dev(Bz), X0=dev(X0), mode=mode, tol=1e-9, maxiter=500, **kw)
+        X = X.cpu().numpy()
+        assert np.all(X[:, :, 1] == 0) and np.all(np.isfinite(X)), mode
+        assert max(info["resid"]) <= 1e-9, (mode, info)
+    # a batch (its interval estimates cached by a first, finite call) names
+    # the problem and launches only the column norms; the operators still solve
+    Xs, infos = mrhs.batch_solve(ops, [dev(B), dev(B)], tol=1e-8)
+    assert all(i["status"] == 0 and max(i["resid"]) <= 1e-8 for i in infos), infos
+    Bb = B.copy()
+    Bb[5, 2, 0] = np.nan
+    n0 = mrhs.launch_count()
+    with pytest.raises(mrhs.MrhsError) as e:
+        mrhs.batch_solve(ops, [dev(B), dev(Bb)], tol=1e-8)
+    assert e.value.code == -5 and "problem 1: B column 0" in str(e.value), str(e.value)
+    assert mrhs.launch_count() - n0 <= 8
+    Xs, infos = mrhs.batch_solve(ops, [dev(B), dev(B)], tol=1e-8)
+    assert all(i["status"] == 0 and max(i["resid"]) <= 1e-8 for i in infos), infos
+
+
 def test_invalid_arguments(mrhs):
     L, nb, npts = (2, 2, 2, 2), 4, 9
     disp, _ = stencil(npts)
