@@ -61,9 +61,14 @@ def parse():
     ap.add_argument("--cheb-order", type=int, default=8)
     ap.add_argument("--cheb-ratio", type=float, default=400.0, help="hi / lo")
     ap.add_argument("--inner-tol", type=float, default=3e-4,
-                    help="inner block-CG target per refinement cycle (3e-4: 52 iterations on "
-                         "each of four right-hand-side sets at 12^4, against 56 for 1e-4 .. 5e-4 "
-                         "except 2e-4 once, and 56-60 for 1e-3)")
+                    help="inner block-CG target of the first refinement cycle (3e-4: 24 "
+                         "iterations at 12^4; 1e-4 the same, 1e-3 20 but 4 more in the later "
+                         "cycles)")
+    ap.add_argument("--inner-tol-later", type=float, default=1e-2,
+                    help="inner target of the later refinement cycles, which the Krylov "
+                         "operator's own error limits to 1.5-2%% of their start at 12^4 "
+                         "(1e-2 .. 4e-2: 42 inner iterations on four right-hand-side sets, "
+                         "against 50-54 for 3e-4; 0: --inner-tol)")
     ap.add_argument("--recycle", type=int, default=1,
                     help="sweeps of the Galerkin start over the earlier cycles' search blocks "
                          "(0: plain restart; 1, the default: 60 instead of 66 inner "
@@ -72,8 +77,9 @@ def parse():
                     help="solve: draw the right-hand sides from the workload's seed plus this offset")
     ap.add_argument("--check-every", type=int, default=4,
                     help="block-CG iterations between convergence checks (one graph chunk); "
-                         "4: 56 inner iterations on each of four right-hand-side sets at 12^4 "
-                         "with one recycling sweep")
+                         "4: 42 inner iterations on each of four right-hand-side sets at 12^4 "
+                         "with one recycling sweep and the later-cycle target, against 44 for "
+                         "2 and 47 for 3")
     ap.add_argument("--fp64-native-iters", type=int, default=3,
                     help="iterations of plain FP64 block CG on the FP64 pipes timed for the "
                          "per-iteration comparison (0: skip)")
@@ -966,7 +972,8 @@ def main():
     params = dict(mode="mixed", tol=1e-8, precond=1, precond_prec=a.precond,
                   krylov_prec=a.krylov,
                   cheb_order=a.cheb_order, cheb_hi=hi, cheb_lo=hi / a.cheb_ratio,
-                  inner_tol=a.inner_tol, maxiter=20000, max_cycles=20,
+                  inner_tol=a.inner_tol, inner_tol_later=a.inner_tol_later,
+                  maxiter=20000, max_cycles=20,
                   check_every=a.check_every, residual_prec=a.residual, recycle=a.recycle,
                   fp64_prec=a.fp64_op)
 
@@ -1127,7 +1134,8 @@ def main():
                           "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
                           "precond": f"chebyshev deg {a.cheb_order} {a.precond} on "
                                      f"[{hi / a.cheb_ratio:.4g}, {hi:.4g}]",
-                          "inner_tol": a.inner_tol, "recycle": a.recycle,
+                          "inner_tol": a.inner_tol, "inner_tol_later": a.inner_tol_later,
+                          "recycle": a.recycle,
                           "check_every": a.check_every,
                           "parallelism": f"replicas x{world}",
                           "residuals": f"{a.residual} per cycle, the FP64 operator "

@@ -40,7 +40,7 @@ class SolveParams(ctypes.Structure):
                 ("breakdown_tau", ctypes.c_double), ("krylov_prec", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("residual_prec", ctypes.c_int32),
                 ("recycle", ctypes.c_int32), ("recycle_max_blocks", ctypes.c_int32),
-                ("fp64_prec", ctypes.c_int32)]
+                ("fp64_prec", ctypes.c_int32), ("inner_tol_later", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):

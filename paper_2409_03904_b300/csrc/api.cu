@@ -126,6 +126,16 @@ int check_plain(const mrhs_op_s* op) {
   return MRHS_OK;
 }
 
+// The mixed solve's per-cycle reductions: a target of 1 or more would end
+// every cycle at once, and the solve would restart without progress.
+int check_inner_tols(const mrhs_solve_params& p) {
+  if (p.mode != MRHS_SOLVE_MIXED) return MRHS_OK;
+  if (!(p.inner_tol > 0.0 && p.inner_tol < 1.0) ||
+      !(p.inner_tol_later >= 0.0 && p.inner_tol_later < 1.0))
+    return fail(MRHS_ERR_INVALID_ARG, "inner_tol must be in (0, 1) and inner_tol_later in [0, 1)");
+  return MRHS_OK;
+}
+
 int check_vec(const void* p, const char* name) {
   if (!p) return fail(MRHS_ERR_INVALID_ARG, std::string(name) + " is null");
   if (!aligned16(p)) return fail(MRHS_ERR_INVALID_ARG, std::string(name) + " not 16-byte aligned");
@@ -700,6 +710,7 @@ int block_cg_solve(mrhs_op op, const void* B, void* X, int32_t nrhs,
     return fail(MRHS_ERR_INVALID_ARG, "mode");
   if (p.recycle < 0 || p.recycle_max_blocks < 0)
     return fail(MRHS_ERR_INVALID_ARG, "recycle / recycle_max_blocks must be >= 0");
+  MRHS_TRY(check_inner_tols(p));
   auto built = [&](int pr) { return (op->prec_mask & MRHS_PREC_BIT(pr)) != 0; };
   const bool fp64_ok = built(MRHS_PREC_FP64);
   const bool oz_ok = built(MRHS_PREC_OZ) && oz_supported(op, nrhs);
@@ -868,6 +879,7 @@ int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* 
   if (batched) {
     if (!(q.tol > 0.0) || q.maxiter < 1 || q.cheb_order < 0)
       return fail(MRHS_ERR_INVALID_ARG, "tol / maxiter / cheb_order");
+    MRHS_TRY(check_inner_tols(q));
     for (int i = 0; i < n; ++i)
       if (B[i] == X[i]) return fail(MRHS_ERR_INVALID_ARG, "X and B must differ");
     return solve_batch(const_cast<mrhs_op_s* const*>(ops), n, (const double2* const*)B,
@@ -904,6 +916,7 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->recycle = 0;
   p->recycle_max_blocks = 0;
   p->fp64_prec = -1;
+  p->inner_tol_later = 0.0;
 }
 
 }  // extern "C"

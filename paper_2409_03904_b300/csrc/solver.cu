@@ -550,6 +550,13 @@ int grid_for(int64_t n) {
 // non-finite column norm (so does an entry above about 1e154, whose square
 // overflows the FP64 sum); the solves refuse such input before iterating
 // instead of treating the column as a zero one.
+// Inner tolerance of refinement cycle `cycle` (0: the first).  A later cycle
+// starts from a residual whose low modes dominate, and for those the Krylov
+// operator's own error bounds the reduction the cycle can reach.
+double cycle_inner_tol(const mrhs_solve_params& p, int cycle) {
+  return (cycle > 0 && p.inner_tol_later > 0.0) ? p.inner_tol_later : p.inner_tol;
+}
+
 int finite_columns(const std::vector<double>& norm, const std::string& what) {
   for (size_t j = 0; j < norm.size(); ++j)
     if (!std::isfinite(norm[j]))
@@ -1239,11 +1246,12 @@ int solve(mrhs_op_s* op, const double2* B, double2* X, int R, const mrhs_solve_p
       // expected to finish the solve (TC32 inner solves reach 1/20..1/50 per
       // cycle even at kappa 1e4): its residual goes straight to FP64
       bool final_cycle = true;
+      const double tol_c = cycle_inner_tol(p, cycles);
       for (int j = 0; j < R; ++j) {
         rho[j] = (bnorm[j] > 0 && rnorm[j] > p.tol * bnorm[j]) ? rnorm[j] : 0.0;
         const double want = rho[j] > 0 ? 0.5 * p.tol * bnorm[j] / rho[j] : 1.0;
-        target[j] = std::fmax(p.inner_tol, want);
-        if (rho[j] > 0 && want < std::fmax(p.inner_tol, kFinalCycleTarget)) final_cycle = false;
+        target[j] = std::fmax(tol_c, want);
+        if (rho[j] > 0 && want < std::fmax(tol_c, kFinalCycleTarget)) final_cycle = false;
       }
       MRHS_CUDA_TRY(cudaMemcpyAsync(sb.rho_d, rho.data(), sizeof(double) * R,
                                     cudaMemcpyHostToDevice, s));
@@ -1531,11 +1539,12 @@ int solve_batch(mrhs_op_s* const* ops, int n, const double2* const* B, double2* 
       bR[k] = cx.R;
       std::vector<double> rho(cx.R);
       b.final_cycle = true;      // less than a tenfold reduction left: FP64 residual directly
+      const double tol_c = cycle_inner_tol(p, cycle);
       for (int j = 0; j < cx.R; ++j) {
         rho[j] = (b.bnorm[j] > 0 && b.rnorm[j] > p.tol * b.bnorm[j]) ? b.rnorm[j] : 0.0;
         const double want = rho[j] > 0 ? 0.5 * p.tol * b.bnorm[j] / rho[j] : 1.0;
-        b.target[j] = std::fmax(p.inner_tol, want);
-        if (rho[j] > 0 && want < std::fmax(p.inner_tol, kFinalCycleTarget)) b.final_cycle = false;
+        b.target[j] = std::fmax(tol_c, want);
+        if (rho[j] > 0 && want < std::fmax(tol_c, kFinalCycleTarget)) b.final_cycle = false;
       }
       const int64_t nn = cx.N * cx.R;
       MRHS_CUDA_TRY(cudaMemcpyAsync(b.sb.rho_d, rho.data(), sizeof(double) * cx.R,

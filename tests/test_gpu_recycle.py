@@ -104,3 +104,36 @@ def test_default_is_plain_restart(mrhs, problem):
     op, A, B, disp = problem
     X, info = op.solve(torch.from_numpy(B).cuda(), mode="mixed", tol=1e-8)
     assert info["recycle_blocks"] == 0 and info["recycle_projections"] == 0
+
+
+def test_later_cycle_tolerance(mrhs, problem):
+    """inner_tol_later loosens only the refinement cycles after the first.
+    The first cycle is bit for bit the default one.  The second starts from
+    the same state, so with the looser target it stops at the same flag
+    read or an earlier one.  The solve still meets tol by the C oracle's
+    FP64 residual, and so does a batch.  Tolerances outside their ranges are
+    refused."""
+    op, A, B, disp = problem
+    Bd = torch.from_numpy(B).cuda()
+    kw = dict(mode="mixed", tol=1e-8, inner_tol=3e-4, recycle=1, check_every=4)
+    X0, i0 = op.solve(Bd, **kw)
+    X1, i1 = op.solve(Bd, inner_tol_later=1e-2, **kw)
+    for X, info in ((X0, i0), (X1, i1)):
+        assert info["status"] == 0 and max(info["resid"]) <= 1e-8, info
+        assert oracle_rel(A, X.cpu().numpy(), B, disp) <= 1.5e-8
+    assert i0["cycles"] >= 2 and i1["cycles"] >= 2
+    assert i1["cycle_iters"][0] == i0["cycle_iters"][0]
+    assert i1["cycle_resid"][0] == i0["cycle_resid"][0]
+    assert i1["cycle_iters"][1] <= i0["cycle_iters"][1], (i0["cycle_iters"], i1["cycle_iters"])
+    print("cycle iterations, later-cycle target 3e-4 / 1e-2:", i0["cycle_iters"], i1["cycle_iters"])
+    Xs, infos = mrhs.batch_solve([op], [Bd], tol=1e-8, inner_tol=3e-4, inner_tol_later=1e-2)
+    assert infos[0]["status"] == 0 and max(infos[0]["resid"]) <= 1e-8, infos[0]
+    assert oracle_rel(A, Xs[0].cpu().numpy(), B, disp) <= 1.5e-8
+    for bad in (dict(inner_tol_later=1.0), dict(inner_tol_later=-1e-3), dict(inner_tol=0.0),
+                dict(inner_tol=1.5)):
+        with pytest.raises(mrhs.MrhsError) as e:
+            op.solve(Bd, **{**kw, **bad})
+        assert e.value.code == -1, bad
+        with pytest.raises(mrhs.MrhsError) as e:
+            mrhs.batch_solve([op], [Bd], tol=1e-8, **bad)
+        assert e.value.code == -1, bad
