@@ -916,7 +916,7 @@ void mrhs_solve_params_default(mrhs_solve_params* p, int32_t mode) {
   p->recycle = 0;
   p->recycle_max_blocks = 0;
   p->fp64_prec = -1;
-  p->inner_tol_later = 0.0;
+  p->inner_tol_later = mode == MRHS_SOLVE_MIXED ? 1e-2 : 0.0;
 }
 
 }  // extern "C"

@@ -116,7 +116,7 @@ def test_later_cycle_tolerance(mrhs, problem):
     op, A, B, disp = problem
     Bd = torch.from_numpy(B).cuda()
     kw = dict(mode="mixed", tol=1e-8, inner_tol=3e-4, recycle=1, check_every=4)
-    X0, i0 = op.solve(Bd, **kw)
+    X0, i0 = op.solve(Bd, inner_tol_later=0.0, **kw)
     X1, i1 = op.solve(Bd, inner_tol_later=1e-2, **kw)
     for X, info in ((X0, i0), (X1, i1)):
         assert info["status"] == 0 and max(info["resid"]) <= 1e-8, info
@@ -127,6 +127,9 @@ def test_later_cycle_tolerance(mrhs, problem):
     assert i1["cycle_iters"][1] <= i0["cycle_iters"][1], (i0["cycle_iters"], i1["cycle_iters"])
     print("cycle iterations, later-cycle target 3e-4 / 1e-2:", i0["cycle_iters"], i1["cycle_iters"])
     Xs, infos = mrhs.batch_solve([op], [Bd], tol=1e-8, inner_tol=3e-4, inner_tol_later=1e-2)
+    # the library's default for the mixed solve is the later target 1e-2
+    Xd, idf = op.solve(Bd, mode="mixed", tol=1e-8, inner_tol=3e-4, recycle=1, check_every=4)
+    assert idf["cycle_iters"] == i1["cycle_iters"] and torch.equal(Xd, X1)
     assert infos[0]["status"] == 0 and max(infos[0]["resid"]) <= 1e-8, infos[0]
     assert oracle_rel(A, Xs[0].cpu().numpy(), B, disp) <= 1.5e-8
     for bad in (dict(inner_tol_later=1.0), dict(inner_tol_later=-1e-3), dict(inner_tol=0.0),
