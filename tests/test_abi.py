@@ -87,3 +87,23 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_solve_parameter_defaults(libpath):
+    """mrhs_solve_params_default is host code, checked here without a GPU:
+    the defaults per mode, including the mixed solve's later-cycle inner
+    target (1e-2, 0 elsewhere) and the automatic precision choices (-1)."""
+    import paper_2409_03904_b300 as mrhs
+    l = mrhs._lib.lib()
+    want_common = dict(tol=1e-8, maxiter=5000, precond_prec=-1, krylov_prec=-1, use_graph=1,
+                       residual_prec=-1, cheb_order=8, cheb_lo=0.0, cheb_hi=0.0, inner_tol=1e-3,
+                       max_cycles=12, check_every=4, breakdown_tau=1e-12, recycle=0,
+                       recycle_max_blocks=0, fp64_prec=-1)
+    for mode, precond, later in ((mrhs.SOLVE_FP64, 0, 0.0), (mrhs.SOLVE_MIXED, 1, 1e-2),
+                                 (mrhs.SOLVE_CG5D, 0, 0.0)):
+        p = mrhs._lib.SolveParams()
+        l.mrhs_solve_params_default(ctypes.byref(p), mode)
+        got = {k: getattr(p, k) for k in want_common}
+        assert got == want_common, (mode, got)
+        assert (p.mode, p.precond, p.inner_tol_later) == (mode, precond, later)
+    l.mrhs_solve_params_default(None, mrhs.SOLVE_MIXED)      # a null pointer is ignored
