@@ -321,7 +321,10 @@ def run_reference(a, w, shift):
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "ms/RHS",
            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": val * R,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": w["name"], "nrhs": R, "tol": 1e-8},
+           "data": "synthetic",
+           "config": {"workload": w["name"], "L": list(w["L"]), "nb": w["nb"], "npts": w["npts"],
+                      "nrhs": R, "kappa": w["kappa"], "tol": 1e-8,
+                      "method": "plain FP64 block CG (the oracle's operator on the host cores)"},
            "cpu_baseline": {"value": val, "unit": "ms/RHS", "cores": meta["cores"],
                             "kind": "oracle", "sample": meta["sample"]},
            "e2e": {"value": val, "unit": "ms/RHS", "h2d_bytes_per_step": 0,
