@@ -507,9 +507,11 @@ int mrhs_batch_apply(const mrhs_op* ops, int32_t n, int32_t prec, const void* co
  *   info   host array of n records (may be NULL)
  * Returns MRHS_OK if every problem converged.  MRHS_ERR_NOT_CONVERGED means
  * some problem did not; all X and info are still written.  Non-finite input
- * in any problem's B or X_0 is refused before any iteration, as in
- * block_cg_solve.  Any other failure code may leave the X and info of
- * problems other than the failing one unwritten.  Synchronises `stream`. */
+ * in a problem's B or X_0 returns MRHS_ERR_NONFINITE, as in block_cg_solve:
+ * in the lockstep path before any problem iterates (the message names the
+ * problem), one after another when that problem's turn comes.  Any other
+ * failure code may leave the X and info of problems other than the failing
+ * one unwritten.  Synchronises `stream`. */
 int mrhs_batch_solve(const mrhs_op* ops, int32_t n, const void* const* B, void* const* X,
                      const int32_t* nrhs, const mrhs_solve_params* params, mrhs_solve_info* info,
                      void* stream);
