@@ -339,8 +339,10 @@ int coarse_solve_defl_cheby(mrhs_op op, int32_t prec, const void* U, const doubl
  * few power-method steps): Rayleigh quotient after
  * `iters` applications in precision `prec` to one deterministic start vector.
  * The estimate lies below the true maximum; it is cached on the operator and
- * block_cg_solve uses 1.08 x the cached value when cheb_hi <= 0.  Uses
- * operator-owned workspace; synchronises `stream`. */
+ * block_cg_solve uses 1.08 x the cached value when cheb_hi <= 0.  A
+ * non-finite estimate (NaN or Inf coefficients) returns MRHS_ERR_NONFINITE
+ * and caches nothing.  Uses operator-owned workspace; synchronises
+ * `stream`. */
 int mrhs_op_lambda_max(mrhs_op op, int32_t prec, int32_t iters, double* lam, void* stream);
 
 /* Solver parameters (block_cg_solve). */

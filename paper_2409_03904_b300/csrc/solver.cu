@@ -351,6 +351,15 @@ __global__ void k_small_start(Small* st, int R, double tau) {
 //
 // M step: factor the Gram D^dagger Z (rank checked against the block's), then
 // M = W W^dagger, negM = -M (k_small_WWh) and MC = M C (k_small_mul).
+// A Gram whose diagonal is not finite: a NaN or Inf in either block makes
+// some diagonal entry non-finite (|NaN|^2 and |Inf|^2 are), where the pivoted
+// factorisation would only see rank loss and the loop would run to its cap.
+__device__ bool diag_finite(const double2* G, int R) {
+  for (int j = 0; j < R; ++j)
+    if (!isfinite(G[j * R + j].x)) return false;
+  return true;
+}
+
 __global__ void k_small_Mf(Small* st, int R, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* sA = reinterpret_cast<double2*>(smem_raw);
@@ -359,7 +368,10 @@ __global__ void k_small_Mf(Small* st, int R, double tau) {
   __shared__ int perm[64];
   const int k_in = st->rank;
   const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, nullptr, st->W);
-  if (threadIdx.x == 0 && k < k_in) st->flag |= 2;   // D^dagger H D lost rank
+  if (threadIdx.x == 0) {
+    if (k < k_in) st->flag |= 2;                      // D^dagger H D lost rank
+    if (!diag_finite(st->G, R)) st->flag |= 4;        // a NaN or Inf reached the Gram
+  }
 }
 
 // M = W W^dagger and negM = -M: block i (row), thread j (column)
@@ -403,7 +415,10 @@ __global__ void k_small_Sf(Small* st, int R, double tau) {
   __shared__ int perm[64];
   const int k_in = st->rank;
   const int k = factor_block(st->G, R, R, k_in, tau, sA, sS, sW, perm, st->S, st->W);
-  if (threadIdx.x == 0) st->rank = k;
+  if (threadIdx.x == 0) {
+    st->rank = k;
+    if (!diag_finite(st->G, R)) st->flag |= 4;        // a NaN or Inf reached the Gram
+  }
 }
 
 // C <- S C in place, block j owning column j; unpreconditioned form: est_j =
@@ -1092,6 +1107,11 @@ int power_run(mrhs_op_s* op, int prec, int iters, cudaStream_t s, double* lam) {
     { k_scale_vec<C><<<g, kThreads, 0, s>>>(v, w, 1.0 / std::sqrt(h[1].x), n); ::mrhs::count_launch(); }
   }
   MRHS_CUDA_TRY(cudaGetLastError());
+  // a NaN or Inf in the coefficients reaches the estimate: report it as such
+  // (the Chebyshev interval built from it would only fail as an argument)
+  if (!std::isfinite(est))
+    return fail(MRHS_ERR_NONFINITE, "power-method estimate of lambda_max is not finite "
+                                    "(non-finite operator coefficients?)");
   *lam = est;
   return MRHS_OK;
 }
