@@ -171,3 +171,88 @@ def test_domain_geometry():
     assert np.array_equal(np.sort(owned), np.arange(int(np.prod(L))))
     with pytest.raises(ValueError):
         domain.Domain(L, (1, 2, 1, 1), 0)        # 2 does not divide 3
+
+
+class FailingComm:
+    """A rank that fails between steps: its `fail_at`-th Gram allreduce raises
+    instead of taking part. This is the host-side form of a rank that crashes
+    (no GPU work is in flight at that point)."""
+
+    def __init__(self, inner, fail_at):
+        self.inner, self.calls, self.fail_at = inner, 0, fail_at
+
+    def allreduce(self, t):
+        self.calls += 1
+        if self.calls == self.fail_at:
+            raise RuntimeError("injected rank failure")
+        return self.inner.allreduce(t)
+
+    def sendrecv(self, *args):
+        return self.inner.sendrecv(*args)
+
+
+def _failing_worker(rank, world, port, grid, L, nb, npts, R, shift, q):
+    import datetime
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.set_num_threads(1)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    t0 = time.time()
+    outcome = "finished"
+    try:
+        from paper_2409_03904_b300 import domain
+        disp, _ = stencil(npts)
+        A = coarse_op(L, nb, npts, 4040, shift)
+        B = vectors(L, nb, R, 4041)
+        dom = domain.Domain(L, grid, rank)
+        gs = dom.global_sites
+        be = OracleBackend(dom, A[gs], disp)
+        comm = domain.TorchComm()
+        if rank == 1:
+            comm = FailingComm(comm, fail_at=5)
+        domain.block_cg(dom, be, comm, torch.from_numpy(B[gs].copy()), tol=1e-10, maxiter=400)
+    except Exception as e:  # noqa: BLE001  (every outcome is reported to the parent)
+        outcome = f"{type(e).__name__}: {str(e)[:200]}"
+    q.put((rank, outcome, time.time() - t0))
+    q.close()
+    q.join_thread()
+    if rank == 1:
+        os._exit(0)          # the failed rank leaves without a clean shutdown
+    try:
+        dist.destroy_process_group()
+    except Exception:  # noqa: BLE001
+        pass
+
+
+def test_rank_failure_ends_the_other_ranks_solve():
+    """A rank of the decomposed BlockCGrQ fails between iterations and exits.
+    The other rank must not hang: its next collective raises, within the
+    process group's 20 s timeout. Plain spawned processes report through a
+    queue, so the harness does not kill the survivor before it detects the
+    failure."""
+    import multiprocessing
+    ctx = multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    L, nb, R = (4, 3, 4, 4), 4, 3
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker,
+                         args=(r, 2, port, (1, 1, 1, 2), L, nb, 81, R, 40.0, q))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    res = {}
+    try:
+        for _ in range(2):
+            r, outcome, dt = q.get(timeout=120)
+            res[r] = (outcome, dt)
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
+    assert "injected rank failure" in res[1][0], res
+    assert res[0][0] != "finished", res            # the survivor's collective failed
+    assert res[0][1] < 60, res                     # and it did not wait forever
+    print("survivor:", res[0])
